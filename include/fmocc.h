@@ -1,0 +1,198 @@
+/*
+ * fmocc: FM-index search on one NVIDIA GB300 (sm_103a).
+ *
+ * The operations follow R. Snytsar, "Vectorized Character Counting for Faster Pattern
+ * Matching" (arXiv 1811.06127):
+ *   - Sec. 2 (Eq. 1-3, Fig. 1): suffix array, BWT, C and Occ of a reference R over {A,C,G,T};
+ *   - Listing 1: exact backward search; Listing 2: inexact (bounded-difference) search;
+ *   - Sec. 2 (closing remarks) and Sec. 3.3: one search step consumes eight Occ values,
+ *     Occ(c, k-1) and Occ(c, l) for c in ACGT, which this library computes in one pass over
+ *     one interleaved checkpoint block (two when k and l+1 fall in different blocks).
+ *
+ * Conventions shared by every call:
+ *   - Symbol codes A=0, C=1, G=2, T=3 (the 2-bit code of Fig. 2).  The terminator $ is
+ *     implicit at the end of R and is smaller than every symbol.
+ *   - Rows of the Burrows-Wheeler matrix run 0..n (n+1 rows); row 0 is the suffix "$".
+ *   - Occ(c,k) = occurrences of c in BWT[0..k] inclusive, k in [-1, n]; Occ(c,-1) = 0;
+ *     $ counts for no symbol.  C[c] = symbols of R smaller than c; C[4] = n.
+ *   - An SA interval [k, l] holds the rows whose suffix starts with the searched string;
+ *     k = l + 1 denotes an empty interval (the insertion point).
+ *   - Pointers documented as "device" must point to memory of the index's device (e.g. torch
+ *     CUDA tensors); "host" pointers to ordinary host memory.  The caller owns every buffer
+ *     it passes; the index owns its own device memory (the resident tables and the scratch
+ *     it grows on demand) until fm_free.
+ *   - `stream` is a cudaStream_t (NULL: the legacy default stream).  Compute calls enqueue
+ *     their kernels on it and then synchronise it, so that the returned status covers the
+ *     device work; outputs are complete when the call returns FM_OK.
+ *   - Every call returns a status; fm_last_error() returns a message for the last failure.
+ *   - An index handle is not thread-safe: calls on one handle must not overlap.
+ */
+#ifndef FMOCC_H
+#define FMOCC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum fm_status {
+    FM_OK = 0,
+    FM_EINVAL = 1,   /* an argument or an input symbol is outside the documented domain */
+    FM_ENOMEM = 2,   /* a device or host allocation failed */
+    FM_ECUDA = 3,    /* a CUDA runtime call failed (message in fm_last_error) */
+    FM_ETRUNC = 4,   /* an output buffer is too small; the needed size has been written */
+    FM_ETIMEOUT = 5, /* a bounded wait expired */
+    FM_EIO = 6       /* file I/O or a corrupt index file */
+};
+
+typedef struct fm_index fm_index;
+
+/* Build options. */
+typedef struct fm_params {
+    uint32_t interval; /* checkpoint interval I: 64 (32-byte blocks), 128 (64-byte blocks)
+                          or 256 (96-byte blocks); 0 means 64 */
+    uint32_t flags;    /* FM_BUILD_* bits */
+    int32_t device;    /* CUDA device ordinal; -1 = the calling thread's current device */
+    uint32_t reserved;
+} fm_params;
+
+#define FM_BUILD_CODES 1u        /* ref holds codes 0..3 instead of ASCII ACGTacgt */
+#define FM_BUILD_FORWARD_ONLY 2u /* skip the index of reverse(R): fm_dcalc and fm_inexact
+                                    then return FM_EINVAL */
+
+/* Summary of a built index (fm_info). */
+typedef struct fm_info_t {
+    uint64_t n;              /* reference length |R| */
+    uint32_t interval;       /* checkpoint interval I */
+    uint32_t block_bytes;    /* bytes per checkpoint block: 32, 64 or 96 */
+    uint64_t C[5];           /* C array (Fig. 1) */
+    uint64_t dollar_row;     /* row of the forward BWT holding $ */
+    uint64_t rev_dollar_row; /* the same for reverse(R) (0 without a reverse index) */
+    uint64_t n_blocks;       /* checkpoint blocks per index: (n+1)/I + 1 */
+    uint64_t sa_sample_rate; /* stride of the sampled suffix array kept on the device */
+    uint64_t bytes_device;   /* device bytes held by the resident tables */
+    int32_t has_reverse;
+    int32_t device;
+} fm_info_t;
+
+/* Build the FM-index of R (Sec. 2: Eq. 1 suffix array, Eq. 2 BWT, C, and the checkpointed
+ * Occ table laid out as interleaved blocks, after the bucket layout described in Sec. 2) and,
+ * unless FM_BUILD_FORWARD_ONLY, the same for reverse(R), which the D lower bound of the
+ * inexact search needs.  The tables stay resident in device memory.
+ *   ref   host, n bytes: ASCII ACGTacgt, or codes 0..3 with FM_BUILD_CODES.
+ *   n     1 <= n <= 2,147,483,646.
+ *   p     may be NULL (interval 64, both indexes, current device).
+ *   out   receives the handle.
+ * Errors: FM_EINVAL (bad symbol, n or interval), FM_ENOMEM, FM_ECUDA.  On error *out is
+ * NULL and fm_last_error(NULL) holds the message. */
+int fm_build(const char *ref, uint64_t n, const fm_params *p, fm_index **out);
+
+/* Release the index and all device memory it holds.  NULL is ignored. */
+void fm_free(fm_index *h);
+
+/* Message for the last failure on h, or of the last failed fm_build/fm_load on this thread
+ * when h is NULL.  The string lives until the next call on the same handle/thread. */
+const char *fm_last_error(const fm_index *h);
+
+/* Fill *out with the summary of h.  Errors: FM_EINVAL. */
+int fm_info(const fm_index *h, fm_info_t *out);
+
+/* Copy the forward C array and BWT symbols back (test access).  bwt: host, n+1 bytes, codes
+ * 0..3 with 4 at the $ row.  rev != 0 selects the reverse index.  Errors: FM_EINVAL. */
+int fm_get_bwt(const fm_index *h, int rev, uint8_t *bwt);
+
+/* Save the resident tables to a file (header with n, I, C, $ rows, sizes, then the tables,
+ * then a 64-bit FNV-1a checksum) and load them back on a device.
+ * Errors: FM_EIO (open/write/read, bad magic or checksum), FM_ENOMEM, FM_ECUDA. */
+int fm_save(const fm_index *h, const char *path);
+int fm_load(const char *path, const fm_params *p, fm_index **out);
+
+/* The eight Occ values of one inexact step (Sec. 2, closing remarks of Listing 2; Sec. 3.3),
+ * for N queries:
+ *   out8[8q+c]   = Occ(c, k[q]-1)   c = A,C,G,T
+ *   out8[8q+4+c] = Occ(c, l[q])
+ * k, l: device uint32[N] with 0 <= k[q] <= n+1 and 0 <= l[q] <= n.  out8: device uint32[8N].
+ * N may be 0.  Queries outside the domain write zeros and make the call return FM_EINVAL. */
+int fm_occ8(fm_index *h, const uint32_t *k, const uint32_t *l, uint32_t *out8, uint64_t N,
+            void *stream);
+
+/* Listing 1 (ExactRecur) for each read from the whole range [0, n] (Eq. 3 read as one step
+ * of Listing 1), without early exit: an absent read ends with k_out = l_out + 1.
+ * reads: device uint8, the concatenated codes (0..3) of n_reads reads;
+ * offs:  device uint32[n_reads+1], read r = reads[offs[r] .. offs[r+1]);
+ * k_out, l_out: device uint32[n_reads].
+ * Errors: FM_EINVAL (a code above 3; such reads return k = 0, l = n). */
+int fm_exact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
+             uint32_t *k_out, uint32_t *l_out, void *stream);
+
+/* Inexact search options. */
+typedef struct fm_search_params {
+    uint32_t z;        /* differences allowed, 0..7 */
+    uint32_t max_gaps; /* indel columns allowed among them (0: mismatches only), 0..7 */
+    uint32_t strands;  /* 1: reads as given; 2: each read and its reverse complement, as
+                          queries q = 2r (read) and q = 2r+1 (reverse complement) */
+    uint32_t kernel;   /* FM_KERNEL_* */
+    uint64_t *stats;   /* optional device uint64[4], accumulated by each successful call:
+                          [0] nodes expanded (calls of InexRecur reaching the Occ step),
+                          [1] checkpoint blocks read by those expansions (1 when k and l+1
+                              share a block, else 2), [2] intervals reported before
+                              deduplication, [3] reserved */
+} fm_search_params;
+
+#define FM_KERNEL_AUTO 0u       /* the persistent kernel */
+#define FM_KERNEL_PLAIN 1u      /* one thread per query, depth-first with its own stack */
+#define FM_KERNEL_PERSISTENT 2u /* persistent warps pulling queries from a device work queue,
+                                   expanding pooled frontiers with warp-ballot compaction */
+
+/* The lower bound D of the inexact search (the BWA bound, Li and Durbin 2009, cited with
+ * Listing 2): D(i) = number of disjoint windows, taken greedily from W[0], that do not occur
+ * in R, counted within W[0..i].  Computed by forward extension on the index of reverse(R).
+ * reads/offs as in fm_exact; read lengths at most 255.
+ * D_out: device uint8, strands*offs[n_reads] bytes; query q = r*strands + s has its m_r
+ * values at D_out[strands*offs[r] + s*m_r ...].
+ * Errors: FM_EINVAL (no reverse index, strands not 1/2, a code above 3, a read over 255). */
+int fm_dcalc(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
+             uint32_t strands, uint8_t *D_out, void *stream);
+
+/* Listing 2 (InexRecur) with D pruning, for every query, as sets of SA intervals.
+ * Readings of Listing 2 applied: fresh k', l' per symbol b; the deletion, match and mismatch
+ * recursions run only when k' <= l'; insertions and deletions are single-symbol columns, at
+ * most max_gaps of them; a branch with z < D(i) is cut; intervals reached without reading
+ * any reference symbol are not reported; the search starts from [0, n].
+ * reads/offs as in fm_exact (read lengths 1..255).
+ * counts:  device uint32[nq]   distinct intervals of query q (nq = n_reads * strands);
+ * offsets: device uint64[nq+1] exclusive prefix sum of counts;
+ * pairs:   device uint32[2*pair_capacity]: query q's intervals are
+ *          pairs[2*offsets[q] ...] as (k, l), sorted by k then l;
+ * pairs_needed: host, receives offsets[nq].
+ * When pairs_needed > pair_capacity the call returns FM_ETRUNC after filling counts and
+ * offsets; pairs is then left untouched.
+ * Errors: FM_EINVAL, FM_ETRUNC, FM_ENOMEM, FM_ECUDA. */
+int fm_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
+               const fm_search_params *sp, uint32_t *counts, uint64_t *offsets, uint32_t *pairs,
+               uint64_t pair_capacity, uint64_t *pairs_needed, void *stream);
+
+/* Copy the canonical intervals of the most recent fm_inexact call on h into pairs (device
+ * uint32[2*pair_capacity], laid out as in fm_inexact), e.g. after that call returned
+ * FM_ETRUNC.  Valid until the next fm_inexact call on h.
+ * Errors: FM_EINVAL (no earlier search), FM_ETRUNC (capacity below the count found). */
+int fm_inexact_fetch(fm_index *h, uint32_t *pairs, uint64_t pair_capacity, void *stream);
+
+/* Tuning knobs of the search kernels (the autotuner writes them).  Zero fields keep the
+ * current value.  Errors: FM_EINVAL for out-of-range values. */
+typedef struct fm_tuning {
+    uint32_t warps_per_block;   /* persistent kernel: warps per CTA (1..8) */
+    uint32_t blocks_per_sm;     /* persistent kernel: resident CTAs per SM (occupancy) */
+    uint32_t chunk;             /* queries a warp takes from the work queue at once (1..32) */
+    uint32_t plain_block;       /* plain kernel threads per CTA (a multiple of 32, <= 256) */
+} fm_tuning;
+
+int fm_set_tuning(fm_index *h, const fm_tuning *t);
+int fm_get_tuning(const fm_index *h, fm_tuning *t);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,881 @@
+// Inexact search (Listing 2, InexRecur) with the D lower bound, on the device.
+//
+// A search node is one call of InexRecur: (query q, position i, differences left z, indel
+// columns used g, interval [k, l]), packed in 16 bytes.  Expanding a node costs one eight-Occ
+// step (rank(c, k) and rank(c, l+1) for c in ACGT, from one or two checkpoint blocks) and
+// yields up to nine children, per Listing 2 with these readings:
+//   insertion  (i-1, z-1, g+1, k, l)            when z >= 1 and g < max_gaps
+//   deletion   (i,   z-1, g+1, k'_b, l'_b)      for each b with k'_b <= l'_b, z >= 1, g < max_gaps
+//   match      (i-1, z,   g,   k'_b, l'_b)      for b = W[i], k'_b <= l'_b
+//   mismatch   (i-1, z-1, g,   k'_b, l'_b)      for b != W[i], k'_b <= l'_b, z >= 1
+// with k'_b = C[b] + rank(b, k) + 1 and l'_b = C[b] + rank(b, l+1) computed from the node's
+// own interval.  A child at position i' >= 0 survives only when its z' >= D(i'); a child at
+// i' = -1 is a leaf: its interval is a result unless k = 0 (no reference symbol read).
+//
+// Two schedulers of the same node expansion:
+//   * plain: one thread per query, depth-first with an explicit stack in device memory
+//     (interleaved across threads so that neighbouring lanes touch neighbouring words);
+//   * persistent: a grid of resident warps.  Each warp keeps a pool of nodes of any queries
+//     in shared memory, pops up to 32 of them per step (one per lane), expands them, and
+//     pushes the surviving children back with a warp-ballot/shuffle prefix sum.  When its pool
+//     runs low the warp takes the next chunk of queries from a device work queue (an atomic
+//     counter); when the pool would overflow it spills to a per-warp region of device memory.
+//     A warp leaves when the queue is drained and its pool and spill are empty.
+// Leaves are appended to a raw result buffer (warp-aggregated atomics).  The raw results are
+// then grouped by query, sorted and deduplicated (canonical sets, Listing 2's set union), and
+// compacted into the caller's counts/offsets/pairs.
+#include "fm_internal.cuh"
+
+namespace fm {
+namespace {
+
+constexpr uint32_t FULL = 0xffffffffu;
+
+struct SearchCfg {
+    IndexView ix;
+    const uint8_t *reads;
+    const uint4 *qmeta;
+    uint32_t nq;
+    uint32_t z, max_gaps;
+    uint32_t chunk;
+    uint32_t *next_q;
+    uint4 *raw;
+    unsigned long long *raw_count;
+    uint64_t raw_cap;
+    unsigned long long *stats;   // nodes, blocks, raw
+    uint32_t *err;
+};
+
+__device__ __forceinline__ uint32_t d_at(const uint4 &mt, int i) {
+    if (i < 0) return 0u;
+    const uint32_t ib = (uint32_t)i * 0x01010101u;
+    return __popc(__vcmpleu4(mt.x, ib) & 0x01010101u) + __popc(__vcmpleu4(mt.y, ib) & 0x01010101u);
+}
+
+__device__ __forceinline__ uint32_t w_at(const uint8_t *reads, const uint4 &mt, uint32_t i) {
+    const uint32_t m = mt.w & 255u;
+    if (mt.w >> 8) return 3u - reads[mt.z + m - 1u - i];
+    return reads[mt.z + i];
+}
+
+// One expansion.  Outputs the eight child intervals and two 9-bit masks:
+//   bit 0 insertion, bits 1..4 deletion with b = 0..3, bits 5..8 match/mismatch with b = 0..3;
+// push: child kept as a node; leaf: child is a result.
+template <int I>
+__device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, const uint4 &mt,
+                                       uint32_t k2[4], uint32_t l2[4], uint32_t &push,
+                                       uint32_t &leaf, uint32_t &nblocks, uint32_t &wi_out) {
+    const int i = (int)(nd.y & 255u);
+    const uint32_t z = (nd.y >> 8) & 15u;
+    const uint32_t g = (nd.y >> 12) & 15u;
+    const uint32_t k = nd.z, l = nd.w;
+    const uint32_t wi = w_at(c.reads, mt, (uint32_t)i);
+    wi_out = wi;
+    const uint32_t pk = k, pl = l + 1u;
+    const uint32_t jk = pk / I, jl = pl / I;
+    const uint32_t ok = pk - jk * I, ol = pl - jl * I;
+    Blk<I> Bk, Bl;
+    if (jk == jl) {
+        load_block<I>(c.ix.blocks, jk, ok > ol ? ok : ol, Bk);
+        nblocks = 1;
+    } else {
+        load_block<I>(c.ix.blocks, jk, ok, Bk);
+        load_block<I>(c.ix.blocks, jl, ol, Bl);
+        nblocks = 2;
+    }
+    uint32_t rk[4], rl[4];
+    rank4_in<I>(Bk, jk, pk, c.ix.dollar, rk);
+    rank4_in<I>(jk == jl ? Bk : Bl, jl, pl, c.ix.dollar, rl);
+    const uint32_t d_here = d_at(mt, i);
+    const uint32_t d_next = d_at(mt, i - 1);
+    const bool gap_ok = z >= 1u && g < c.max_gaps;
+    push = 0;
+    leaf = 0;
+    // insertion: W[i] against no reference symbol, interval unchanged
+    if (gap_ok) {
+        if (i == 0) {
+            if (k >= 1u) leaf |= 1u;
+        } else if (z - 1u >= d_next) {
+            push |= 1u;
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        k2[b] = c.ix.C[b] + rk[b] + 1u;
+        l2[b] = c.ix.C[b] + rl[b];
+        if (k2[b] > l2[b]) continue;
+        if (gap_ok && z - 1u >= d_here) push |= 2u << b;           // deletion of b
+        const uint32_t zc = (uint32_t)b == wi ? z : z - 1u;          // match or mismatch
+        if ((uint32_t)b == wi || z >= 1u) {
+            if (i == 0) leaf |= 32u << b;
+            else if (zc >= d_next) push |= 32u << b;
+        }
+    }
+}
+
+// child number t (0 insertion, 1..4 deletion, 5..8 match/mismatch) of node nd
+__device__ __forceinline__ uint4 make_child(const uint4 &nd, int t, const uint32_t k2[4],
+                                            const uint32_t l2[4], uint32_t wi) {
+    const uint32_t i = nd.y & 255u;
+    const uint32_t z = (nd.y >> 8) & 15u;
+    const uint32_t g = (nd.y >> 12) & 15u;
+    uint4 ch;
+    ch.x = nd.x;
+    if (t == 0) {
+        ch.y = (i - 1u) | ((z - 1u) << 8) | ((g + 1u) << 12);
+        ch.z = nd.z;
+        ch.w = nd.w;
+    } else if (t <= 4) {
+        const int b = t - 1;
+        ch.y = i | ((z - 1u) << 8) | ((g + 1u) << 12);
+        ch.z = k2[b];
+        ch.w = l2[b];
+    } else {
+        const int b = t - 5;
+        const uint32_t zc = (uint32_t)b == wi ? z : z - 1u;
+        ch.y = (i - 1u) | (zc << 8) | (g << 12);
+        ch.z = k2[b];
+        ch.w = l2[b];
+    }
+    return ch;
+}
+
+__device__ __forceinline__ uint32_t leaf_k(const uint4 &nd, int t, const uint32_t k2[4]) {
+    return t == 0 ? nd.z : k2[(t - 1) & 3];
+}
+__device__ __forceinline__ uint32_t leaf_l(const uint4 &nd, int t, const uint32_t l2[4]) {
+    return t == 0 ? nd.w : l2[(t - 1) & 3];
+}
+
+__device__ __forceinline__ uint4 root_of(const SearchCfg &c, uint32_t q, const uint4 &mt,
+                                         bool &ok) {
+    const uint32_t m = mt.w & 255u;
+    ok = m >= 1u && c.z >= d_at(mt, (int)m - 1);
+    return make_uint4(q, (m - 1u) | (c.z << 8), 0u, c.ix.n);
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// append this warp's leaves to the raw buffer
+__device__ __forceinline__ void emit_leaves(const SearchCfg &c, int lane, bool act,
+                                            const uint4 &nd, uint32_t leaf, const uint32_t k2[4],
+                                            const uint32_t l2[4]) {
+    const int lc = act ? __popc(leaf) : 0;
+    const int incl = warp_incl_scan(lc, lane);
+    const int tot = __shfl_sync(FULL, incl, 31);
+    if (tot == 0) return;
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(c.raw_count, (unsigned long long)tot);
+    base = __shfl_sync(FULL, base, 31);
+    uint64_t pos = base + (uint64_t)(incl - lc);
+    uint32_t mset = act ? leaf : 0u;
+    while (mset) {
+        const int t = __ffs(mset) - 1;
+        mset &= mset - 1;
+        if (pos < c.raw_cap)
+            c.raw[pos] = make_uint4(nd.x, leaf_k(nd, t, k2), leaf_l(nd, t, l2), 0u);
+        ++pos;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// persistent kernel
+// ------------------------------------------------------------------------------------------
+template <int I>
+__global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk, uint4 *spill_all,
+                                                            uint32_t spill_cap) {
+    extern __shared__ uint4 smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    uint4 *st = smem + (size_t)wib * stk;
+    const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    uint4 *spill = spill_all + gw * spill_cap;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    int top = 0;          // nodes in the shared pool (warp-uniform)
+    uint32_t stop = 0;    // nodes in the spill region (warp-uniform)
+    bool qdone = false;
+    unsigned long long my_nodes = 0, my_blocks = 0;
+
+    for (;;) {
+        if (top < 32) {
+            if (stop > 0) {
+                // drain spilled work before taking new queries
+                uint32_t nmove = stop < (uint32_t)(stk / 2) ? stop : (uint32_t)(stk / 2);
+                if ((uint32_t)top + nmove > (uint32_t)(stk - 288)) nmove = (uint32_t)(stk - 288 - top);
+                for (uint32_t t = lane; t < nmove; t += 32) st[top + t] = spill[stop - nmove + t];
+                stop -= nmove;
+                top += (int)nmove;
+                __syncwarp();
+            } else if (!qdone) {
+                uint32_t q0 = 0;
+                if (lane == 0) q0 = atomicAdd(c.next_q, c.chunk);
+                q0 = __shfl_sync(FULL, q0, 0);
+                if (q0 >= c.nq) {
+                    qdone = true;
+                } else {
+                    const uint32_t q = q0 + lane;
+                    bool ok = false;
+                    uint4 nd;
+                    if ((uint32_t)lane < c.chunk && q < c.nq) nd = root_of(c, q, c.qmeta[q], ok);
+                    const uint32_t bal = __ballot_sync(FULL, ok);
+                    if (ok) st[top + __popc(bal & lt_mask)] = nd;
+                    top += __popc(bal);
+                    __syncwarp();
+                }
+            }
+        }
+        if (top == 0) {
+            if (stop > 0) continue;
+            if (qdone) break;
+            continue;
+        }
+        const int take = top < 32 ? top : 32;
+        const bool act = lane < take;
+        uint4 nd = make_uint4(0, 0, 0, 0), mt = make_uint4(0, 0, 0, 0);
+        if (act) nd = st[top - 1 - lane];
+        top -= take;
+        __syncwarp();
+        uint32_t k2[4] = {0, 0, 0, 0}, l2[4] = {0, 0, 0, 0}, push = 0, leaf = 0, nb = 0, wi = 0;
+        if (act) {
+            mt = c.qmeta[nd.x];
+            expand<I>(c, nd, mt, k2, l2, push, leaf, nb, wi);
+            my_nodes += 1;
+            my_blocks += nb;
+        }
+        // compaction of the surviving children
+        const int pc = __popc(push);
+        const int incl = warp_incl_scan(pc, lane);
+        const int total = __shfl_sync(FULL, incl, 31);
+        if (top + total > stk) {
+            // pool full: move it to the spill region
+            if (stop + (uint32_t)top > spill_cap) {
+                if (lane == 0) atomicOr(c.err, kErrSpill);
+                top = 0;   // work dropped: the host grows the spill region and reruns
+            } else {
+                for (int t = lane; t < top; t += 32) spill[stop + t] = st[t];
+                stop += (uint32_t)top;
+                top = 0;
+            }
+            __syncwarp();
+        }
+        {
+            int pos = top + incl - pc;
+            uint32_t mset = push;
+            while (mset) {
+                const int t = __ffs(mset) - 1;
+                mset &= mset - 1;
+                st[pos++] = make_child(nd, t, k2, l2, wi);
+            }
+        }
+        top += total;
+        emit_leaves(c, lane, act, nd, leaf, k2, l2);
+        __syncwarp();
+    }
+    if (c.stats) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            my_nodes += __shfl_down_sync(FULL, my_nodes, o);
+            my_blocks += __shfl_down_sync(FULL, my_blocks, o);
+        }
+        if (lane == 0) {
+            atomicAdd(c.stats + 0, my_nodes);
+            atomicAdd(c.stats + 1, my_blocks);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// plain kernel: one thread per query, depth-first
+// ------------------------------------------------------------------------------------------
+template <int I>
+__global__ void __launch_bounds__(256) k_inexact_plain(SearchCfg c, uint4 *stacks, uint32_t cap,
+                                                       uint32_t T) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= T) return;   // T is a multiple of 32: whole warps leave
+    const int lane = threadIdx.x & 31;
+    unsigned long long my_nodes = 0, my_blocks = 0;
+    // every lane of a warp iterates until the whole warp is done (warp-synchronous leaves)
+    uint32_t q = tid;
+    uint32_t sp = 0;
+    bool have = false;
+    for (;;) {
+        // fetch the next query when the stack is empty
+        while (!have && q < c.nq) {
+            bool ok;
+            uint4 mt = c.qmeta[q];
+            uint4 r = root_of(c, q, mt, ok);
+            if (ok) {
+                stacks[(size_t)tid] = r;
+                sp = 1;
+                have = true;
+            }
+            q += T;
+        }
+        const bool act = have;
+        if (!__any_sync(FULL, act)) break;
+        uint4 nd = make_uint4(0, 0, 0, 0);
+        uint32_t k2[4] = {0, 0, 0, 0}, l2[4] = {0, 0, 0, 0}, push = 0, leaf = 0, nb = 0, wi = 0;
+        if (act) {
+            nd = stacks[(size_t)(sp - 1) * T + tid];
+            --sp;
+            const uint4 mt = c.qmeta[nd.x];
+            expand<I>(c, nd, mt, k2, l2, push, leaf, nb, wi);
+            my_nodes += 1;
+            my_blocks += nb;
+            uint32_t mset = push;
+            while (mset) {
+                const int t = __ffs(mset) - 1;
+                mset &= mset - 1;
+                if (sp < cap) {
+                    stacks[(size_t)sp * T + tid] = make_child(nd, t, k2, l2, wi);
+                    ++sp;
+                } else {
+                    atomicOr(c.err, kErrStack);
+                }
+            }
+            if (sp == 0) have = false;
+        }
+        emit_leaves(c, lane, act, nd, leaf, k2, l2);
+    }
+    if (c.stats) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            my_nodes += __shfl_down_sync(FULL, my_nodes, o);
+            my_blocks += __shfl_down_sync(FULL, my_blocks, o);
+        }
+        if (lane == 0) {
+            atomicAdd(c.stats + 0, my_nodes);
+            atomicAdd(c.stats + 1, my_blocks);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// canonical result sets
+// ------------------------------------------------------------------------------------------
+__global__ void k_hist(const uint4 *__restrict__ raw, uint64_t R, uint32_t *__restrict__ cnt) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < R;
+         e += (uint64_t)gridDim.x * blockDim.x)
+        atomicAdd(cnt + raw[e].x, 1u);
+}
+
+__global__ void k_scatter(const uint4 *__restrict__ raw, uint64_t R, const uint64_t *__restrict__ start,
+                          uint32_t *__restrict__ cursor, uint64_t *__restrict__ grouped) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < R;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 v = raw[e];
+        const uint32_t at = atomicAdd(cursor + v.x, 1u);
+        grouped[start[v.x] + at] = ((uint64_t)v.y << 32) | v.z;
+    }
+}
+
+// warp per query: segments of up to 32 sorted in registers (bitonic over shuffles) and
+// deduplicated with a ballot; larger segments are listed for the CTA kernel
+__global__ void k_sort_small(uint32_t nq, const uint32_t *__restrict__ cnt,
+                             const uint64_t *__restrict__ start, uint64_t *__restrict__ grouped,
+                             uint32_t *__restrict__ ucnt, uint32_t *__restrict__ large,
+                             uint32_t *__restrict__ nlarge) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += warps) {
+        const uint32_t n = cnt[q];
+        if (n > 32) {
+            if (lane == 0) large[atomicAdd(nlarge, 1u)] = q;
+            continue;
+        }
+        uint64_t *seg = grouped + start[q];
+        uint64_t key = (uint32_t)lane < n ? seg[lane] : ~0ull;
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const uint64_t o = __shfl_xor_sync(FULL, key, j);
+                const bool up = (lane & k) == 0;
+                const bool low = (lane & j) == 0;
+                key = (low == up) ? (key < o ? key : o) : (key > o ? key : o);
+            }
+        }
+        const uint64_t prev = __shfl_up_sync(FULL, key, 1);
+        const bool keep = (uint32_t)lane < n && (lane == 0 || key != prev);
+        const uint32_t bal = __ballot_sync(FULL, keep);
+        if (keep) seg[__popc(bal & ((1u << lane) - 1u))] = key;
+        if (lane == 0) ucnt[q] = __popc(bal);
+    }
+}
+
+// CTA per large segment: bitonic sort in shared memory up to 8192 keys; above that, each key's
+// final position is its rank (keys smaller, plus equal keys before it), written to tmp
+__global__ void k_sort_large(const uint32_t *__restrict__ large, const uint32_t *__restrict__ nlarge,
+                             const uint32_t *__restrict__ cnt, const uint64_t *__restrict__ start,
+                             uint64_t *__restrict__ grouped, uint64_t *__restrict__ tmp,
+                             uint32_t *__restrict__ ucnt) {
+    extern __shared__ uint64_t sk[];
+    __shared__ uint32_t s_wsum[32];
+    const uint32_t L = *nlarge;
+    for (uint32_t li = blockIdx.x; li < L; li += gridDim.x) {
+        const uint32_t q = large[li];
+        const uint32_t n = cnt[q];
+        uint64_t *seg = grouped + start[q];
+        if (n <= 8192) {
+            uint32_t P = 64;
+            while (P < n) P <<= 1;
+            for (uint32_t t = threadIdx.x; t < P; t += blockDim.x) sk[t] = t < n ? seg[t] : ~0ull;
+            __syncthreads();
+            for (uint32_t k = 2; k <= P; k <<= 1) {
+                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                    for (uint32_t t = threadIdx.x; t < P; t += blockDim.x) {
+                        const uint32_t o = t ^ j;
+                        if (o > t) {
+                            const bool up = (t & k) == 0;
+                            const uint64_t a = sk[t], b = sk[o];
+                            if ((a > b) == up) {
+                                sk[t] = b;
+                                sk[o] = a;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) seg[t] = sk[t];
+            __syncthreads();
+        } else {
+            uint64_t *tq = tmp + start[q];
+            for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
+                const uint64_t x = seg[t];
+                uint32_t r = 0;
+                for (uint32_t u = 0; u < n; ++u) {
+                    const uint64_t y = seg[u];
+                    r += (y < x) || (y == x && u < t);
+                }
+                tq[r] = x;
+            }
+            __syncthreads();
+            for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) seg[t] = tq[t];
+            __syncthreads();
+        }
+        // deduplicate the sorted segment in place, in tiles of blockDim keys
+        uint32_t written = 0;
+        for (uint32_t base = 0; base < n; base += blockDim.x) {
+            const uint32_t t = base + threadIdx.x;
+            bool keep = false;
+            uint64_t x = 0;
+            if (t < n) {
+                x = seg[t];
+                keep = (t == 0) || seg[t - 1] != x;
+            }
+            __syncthreads();   // all reads of this tile precede the writes below
+            const uint32_t bal = __ballot_sync(FULL, keep);
+            const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+            if (ln == 0) s_wsum[w] = __popc(bal);
+            __syncthreads();
+            uint32_t before = 0, tile = 0;
+            for (int v = 0; v < (int)(blockDim.x >> 5); ++v) {
+                if (v < w) before += s_wsum[v];
+                tile += s_wsum[v];
+            }
+            if (keep) seg[written + before + __popc(bal & ((1u << ln) - 1u))] = x;
+            written += tile;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) ucnt[q] = written;
+        __syncthreads();
+    }
+}
+
+__global__ void k_compact(uint32_t nq, const uint32_t *__restrict__ ucnt,
+                          const uint64_t *__restrict__ start, const uint64_t *__restrict__ offsets,
+                          const uint64_t *__restrict__ grouped, uint32_t *__restrict__ pairs) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += warps) {
+        const uint32_t u = ucnt[q];
+        const uint64_t *seg = grouped + start[q];
+        uint32_t *dst = pairs + 2 * offsets[q];
+        for (uint32_t t = lane; t < u; t += 32) {
+            const uint64_t x = seg[t];
+            dst[2 * t] = (uint32_t)(x >> 32);
+            dst[2 * t + 1] = (uint32_t)x;
+        }
+    }
+}
+
+__global__ void k_add_stats(const unsigned long long *__restrict__ in,
+                            const unsigned long long *__restrict__ raw,
+                            unsigned long long *__restrict__ out) {
+    if (threadIdx.x == 0) {
+        out[0] += in[0];
+        out[1] += in[1];
+        out[2] += *raw;
+    }
+}
+
+__global__ void k_copy_counts(uint32_t nq, const uint32_t *__restrict__ ucnt,
+                              uint32_t *__restrict__ counts) {
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x)
+        counts[q] = ucnt[q];
+}
+
+// exclusive scan uint32 -> uint64 of n values, out has n+1 entries (out[n] = total).
+// Three passes: tile sums, scan of the tile sums in one CTA, tile-local scans.
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t *ws, uint64_t &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t t = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint64_t y = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t t = __shfl_up_sync(FULL, y, o);
+            if (lane >= o) y += t;
+        }
+        ws[lane] = y;
+    }
+    __syncthreads();
+    const uint64_t before = w > 0 ? ws[w - 1] : 0;
+    total = ws[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const uint32_t *__restrict__ in, uint64_t n,
+                                                             uint64_t *__restrict__ tile_sum) {
+    __shared__ uint64_t ws[32];
+    const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+    uint64_t s = 0;
+#pragma unroll
+    for (int t = 0; t < kScanItems; ++t) {
+        const uint64_t i = base + (uint64_t)threadIdx.x * kScanItems + t;
+        if (i < n) s += in[i];
+    }
+    uint64_t total;
+    block_excl_scan(s, ws, total);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(uint64_t *__restrict__ tile_sum, uint64_t ntiles) {
+    __shared__ uint64_t ws[32];
+    uint64_t carry = 0;
+    for (uint64_t b = 0; b < ntiles; b += blockDim.x) {
+        const uint64_t i = b + threadIdx.x;
+        const uint64_t v = i < ntiles ? tile_sum[i] : 0;
+        uint64_t total;
+        const uint64_t ex = block_excl_scan(v, ws, total);
+        if (i < ntiles) tile_sum[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) tile_sum[ntiles] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t *__restrict__ in, uint64_t n,
+                                                             const uint64_t *__restrict__ tile_off,
+                                                             uint64_t *__restrict__ out) {
+    __shared__ uint64_t ws[32];
+    const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+    uint32_t v[kScanItems];
+    uint64_t s = 0;
+#pragma unroll
+    for (int t = 0; t < kScanItems; ++t) {
+        const uint64_t i = base + (uint64_t)threadIdx.x * kScanItems + t;
+        v[t] = i < n ? in[i] : 0u;
+        s += v[t];
+    }
+    uint64_t total;
+    uint64_t run = tile_off[blockIdx.x] + block_excl_scan(s, ws, total);
+#pragma unroll
+    for (int t = 0; t < kScanItems; ++t) {
+        const uint64_t i = base + (uint64_t)threadIdx.x * kScanItems + t;
+        if (i < n) out[i] = run;
+        run += v[t];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        const uint64_t ntiles = gridDim.x;
+        out[n] = tile_off[ntiles];
+    }
+}
+
+int grid_cap(fm_index *h, uint64_t work, int block) {
+    uint64_t g = (work + block - 1) / block;
+    uint64_t cap = (uint64_t)h->sms * (2048 / block) * 2;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+// exclusive scan of n uint32 into out[0..n] (out[n] = total); tile_sum needs
+// ceil(n / kScanTile) + 1 entries
+static int scan_u32(fm_index *h, const uint32_t *in, uint64_t n, uint64_t *out, uint64_t *tile_sum,
+                    cudaStream_t st) {
+    const uint64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    if (ntiles == 0) {
+        FM_CUDA_TRY(h, cudaMemsetAsync(out, 0, 8, st));
+        return FM_OK;
+    }
+    k_scan_tiles<<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, tile_sum);
+    k_scan_sums<<<1, kScanThreads, 0, st>>>(tile_sum, ntiles);
+    k_scan_apply<<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, tile_sum, out);
+    FM_CUDA_TRY(h, cudaGetLastError());
+    return FM_OK;
+}
+
+int ensure_scratch(fm_index *h, Scratch &s, size_t bytes) {
+    if (s.bytes >= bytes && s.ptr) return FM_OK;
+    if (s.ptr) {
+        cudaFree(s.ptr);
+        s.ptr = nullptr;
+        s.bytes = 0;
+    }
+    size_t want = bytes < 256 ? 256 : bytes;
+    cudaError_t e = cudaMalloc(&s.ptr, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(h, FM_ENOMEM, "device allocation of " + std::to_string(want) +
+                                           " bytes of search scratch failed");
+    }
+    s.bytes = want;
+    return FM_OK;
+}
+
+template <int I>
+static int launch_search(fm_index *h, const SearchCfg &c, uint32_t kernel, uint4 *spill,
+                         uint32_t spill_cap, int grid, int block, int stk, uint4 *stacks,
+                         uint32_t cap, uint32_t T, cudaStream_t st) {
+    if (kernel == FM_KERNEL_PLAIN) {
+        const int pb = (int)h->tune.plain_block;
+        k_inexact_plain<I><<<(T + pb - 1) / pb, pb, 0, st>>>(c, stacks, cap, T);
+    } else {
+        const size_t smem = (size_t)(block / 32) * stk * sizeof(uint4);
+        k_inexact_persistent<I><<<grid, block, smem, st>>>(c, stk, spill, spill_cap);
+    }
+    FM_CUDA_TRY(h, cudaGetLastError());
+    return FM_OK;
+}
+
+template <int I>
+static cudaError_t set_smem_attr(size_t smem) {
+    return cudaFuncSetAttribute(k_inexact_persistent<I>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
+template <int I>
+static int occupancy_blocks(int block, size_t smem) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_inexact_persistent<I>, block, smem);
+    return nb;
+}
+
+int fetch_inexact(fm_index *h, uint32_t *pairs, uint64_t pair_capacity, cudaStream_t st) {
+    if (!h->last_valid) return set_error(h, FM_EINVAL, "no search results to fetch");
+    if (h->last_total > pair_capacity)
+        return set_error(h, FM_ETRUNC, "pair capacity below the intervals found");
+    if (h->last_total == 0) return FM_OK;
+    if (!pairs) return set_error(h, FM_EINVAL, "pairs is NULL");
+    char *gb = (char *)h->s_group.ptr;
+    const uint32_t nq = h->last_nq;
+    k_compact<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, st>>>(
+        nq, (const uint32_t *)(gb + h->last_off_ucnt), (const uint64_t *)(gb + h->last_off_start),
+        (const uint64_t *)(gb + h->last_off_uoff), (const uint64_t *)(gb + h->last_off_grp), pairs);
+    FM_CUDA_TRY(h, cudaGetLastError());
+    FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+    return FM_OK;
+}
+
+int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
+                const fm_search_params *sp, uint32_t *counts, uint64_t *offsets, uint32_t *pairs,
+                uint64_t pair_capacity, uint64_t *pairs_needed, cudaStream_t st) {
+    const uint32_t strands = sp->strands;
+    const uint64_t nq64 = (uint64_t)n_reads * strands;
+    if (nq64 > 0xffffffffull) return set_error(h, FM_EINVAL, "too many queries");
+    const uint32_t nq = (uint32_t)nq64;
+    int rc;
+
+    // scratch layout in s_misc: counters
+    //   [0] raw_count (u64) [1] next_q (u32) [2] nlarge (u32) [3..] spare
+    if ((rc = ensure_scratch(h, h->s_misc, 256))) return rc;
+    unsigned long long *d_raw_count = (unsigned long long *)h->s_misc.ptr;
+    uint32_t *d_next_q = (uint32_t *)((char *)h->s_misc.ptr + 8);
+    uint32_t *d_nlarge = (uint32_t *)((char *)h->s_misc.ptr + 12);
+    unsigned long long *d_stats = (unsigned long long *)((char *)h->s_misc.ptr + 32);
+
+    if (nq == 0) {
+        if (pairs_needed) *pairs_needed = 0;
+        FM_CUDA_TRY(h, cudaMemsetAsync(offsets, 0, 8, st));
+        FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+        return FM_OK;
+    }
+
+    // D lower bound and per-query metadata
+    if ((rc = ensure_scratch(h, h->s_qmeta, (size_t)nq * sizeof(uint4)))) return rc;
+    uint4 *qmeta = (uint4 *)h->s_qmeta.ptr;
+    if ((rc = launch_dcalc(h, reads, offs, n_reads, strands, qmeta, nullptr, st))) return rc;
+
+    const uint32_t I = h->interval;
+    const Tuning &tu = h->tune;
+    const int block = (int)tu.warps_per_block * 32;
+    const int stk = 352;   // pool entries per warp: >= 288 (children of 32 nodes) + 32
+    const size_t smem = (size_t)(block / 32) * stk * sizeof(uint4);
+    cudaError_t e = I == 64 ? set_smem_attr<64>(smem) : (I == 128 ? set_smem_attr<128>(smem)
+                                                                  : set_smem_attr<256>(smem));
+    if (e != cudaSuccess) return cuda_status(h, e, "cudaFuncSetAttribute");
+    int bps = (int)tu.blocks_per_sm;
+    const int occ = I == 64 ? occupancy_blocks<64>(block, smem)
+                            : (I == 128 ? occupancy_blocks<128>(block, smem)
+                                        : occupancy_blocks<256>(block, smem));
+    if (bps <= 0 || bps > occ) bps = occ;
+    if (bps <= 0) return set_error(h, FM_ECUDA, "persistent kernel does not fit on an SM");
+    int grid = h->sms * bps;
+    const uint64_t nwarps = (uint64_t)grid * (block / 32);
+
+    // plain-kernel stacks: depth-first eager pushes keep at most 8 siblings per level over at
+    // most (read length + z) levels
+    const uint32_t cap = 8u * ((uint32_t)kMaxReadLen + sp->z) + 16u;
+    uint32_t T = 0;
+    if (sp->kernel == FM_KERNEL_PLAIN) {
+        uint64_t tmax = (uint64_t)h->sms * 1024;
+        T = (uint32_t)(nq < tmax ? nq : tmax);
+        T = (T + 31) / 32 * 32;
+        if ((rc = ensure_scratch(h, h->s_plain, (size_t)T * cap * sizeof(uint4)))) return rc;
+    }
+
+    // raw result buffer and spill region, grown on overflow (the search is then rerun)
+    uint64_t raw_cap = h->s_raw.bytes / sizeof(uint4);
+    if (raw_cap < (uint64_t)nq * 4 + (1u << 20)) raw_cap = (uint64_t)nq * 4 + (1u << 20);
+    uint32_t spill_cap = (uint32_t)(h->s_spill.bytes / sizeof(uint4) / (nwarps ? nwarps : 1));
+    if (spill_cap < 4096) spill_cap = 4096;
+
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        if ((rc = ensure_scratch(h, h->s_raw, raw_cap * sizeof(uint4)))) return rc;
+        if (sp->kernel != FM_KERNEL_PLAIN)
+            if ((rc = ensure_scratch(h, h->s_spill, nwarps * spill_cap * sizeof(uint4)))) return rc;
+        FM_CUDA_TRY(h, cudaMemsetAsync(h->s_misc.ptr, 0, 64, st));
+        FM_CUDA_TRY(h, cudaMemsetAsync(h->d_err + kErrSearch, 0, 4, st));
+        SearchCfg c;
+        c.ix = view_fwd(h);
+        c.reads = reads;
+        c.qmeta = qmeta;
+        c.nq = nq;
+        c.z = sp->z;
+        c.max_gaps = sp->max_gaps;
+        c.chunk = tu.chunk;
+        c.next_q = d_next_q;
+        c.raw = (uint4 *)h->s_raw.ptr;
+        c.raw_count = d_raw_count;
+        c.raw_cap = raw_cap;
+        c.stats = d_stats;
+        c.err = h->d_err + kErrSearch;
+        switch (I) {
+            case 64: rc = launch_search<64>(h, c, sp->kernel, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, (uint4 *)h->s_plain.ptr, cap, T, st); break;
+            case 128: rc = launch_search<128>(h, c, sp->kernel, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, (uint4 *)h->s_plain.ptr, cap, T, st); break;
+            default: rc = launch_search<256>(h, c, sp->kernel, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, (uint4 *)h->s_plain.ptr, cap, T, st); break;
+        }
+        if (rc) return rc;
+        unsigned long long rawn = 0;
+        uint32_t errw = 0;
+        FM_CUDA_TRY(h, cudaMemcpyAsync(&rawn, d_raw_count, 8, cudaMemcpyDeviceToHost, st));
+        FM_CUDA_TRY(h, cudaMemcpyAsync(&errw, h->d_err + kErrSearch, 4, cudaMemcpyDeviceToHost, st));
+        FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+        if (errw & kErrStack) return set_error(h, FM_ENOMEM, "plain search stack overflow");
+        bool again = false;
+        if (errw & kErrSpill) {
+            spill_cap *= 4;
+            again = true;
+        }
+        if (rawn > raw_cap) {
+            raw_cap = rawn + rawn / 4 + 1024;
+            again = true;
+        }
+        if (!again) {
+            // canonical sets
+            const uint64_t R = rawn;
+            // group scratch: cnt, cursor, ucnt, large (4 x nq u32), start and uoff (nq+1 u64
+            // each), tile sums, grouped and tmp (R u64 each)
+            const uint64_t ntiles = (nq + kScanTile - 1) / kScanTile + 2;
+            const size_t off_cnt = 0, off_cur = off_cnt + (size_t)nq * 4,
+                         off_ucnt = off_cur + (size_t)nq * 4, off_large = off_ucnt + (size_t)nq * 4,
+                         off_start = (off_large + (size_t)nq * 4 + 15) / 16 * 16,
+                         off_uoff = off_start + ((size_t)nq + 1) * 8,
+                         off_tiles = off_uoff + ((size_t)nq + 1) * 8, off_grp = off_tiles + ntiles * 8,
+                         off_tmp = off_grp + (R ? R : 1) * 8, total = off_tmp + (R ? R : 1) * 8;
+            h->last_valid = false;
+            if ((rc = ensure_scratch(h, h->s_group, total))) return rc;
+            char *gb = (char *)h->s_group.ptr;
+            uint32_t *cnt = (uint32_t *)(gb + off_cnt), *cursor = (uint32_t *)(gb + off_cur),
+                     *ucnt = (uint32_t *)(gb + off_ucnt), *large = (uint32_t *)(gb + off_large);
+            uint64_t *start = (uint64_t *)(gb + off_start), *uoff = (uint64_t *)(gb + off_uoff),
+                     *tiles = (uint64_t *)(gb + off_tiles), *grouped = (uint64_t *)(gb + off_grp),
+                     *tmp = (uint64_t *)(gb + off_tmp);
+            FM_CUDA_TRY(h, cudaMemsetAsync(cnt, 0, (size_t)nq * 8, st));   // cnt and cursor
+            const uint4 *raw = (const uint4 *)h->s_raw.ptr;
+            if (R) k_hist<<<grid_cap(h, R, 256), 256, 0, st>>>(raw, R, cnt);
+            if ((rc = scan_u32(h, cnt, nq, start, tiles, st))) return rc;
+            if (R) k_scatter<<<grid_cap(h, R, 256), 256, 0, st>>>(raw, R, start, cursor, grouped);
+            k_sort_small<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, st>>>(nq, cnt, start, grouped, ucnt, large, d_nlarge);
+            FM_CUDA_TRY(h, cudaGetLastError());
+            uint32_t nlarge = 0;
+            FM_CUDA_TRY(h, cudaMemcpyAsync(&nlarge, d_nlarge, 4, cudaMemcpyDeviceToHost, st));
+            FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+            if (nlarge) {
+                const size_t lsm = 8192 * sizeof(uint64_t);
+                FM_CUDA_TRY(h, cudaFuncSetAttribute(k_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
+                unsigned lg = nlarge < (uint32_t)h->sms * 4 ? nlarge : (uint32_t)h->sms * 4;
+                k_sort_large<<<lg, 512, lsm, st>>>(large, d_nlarge, cnt, start, grouped, tmp, ucnt);
+                FM_CUDA_TRY(h, cudaGetLastError());
+            }
+            if ((rc = scan_u32(h, ucnt, nq, uoff, tiles, st))) return rc;
+            FM_CUDA_TRY(h, cudaMemcpyAsync(offsets, uoff, ((size_t)nq + 1) * 8, cudaMemcpyDeviceToDevice, st));
+            k_copy_counts<<<grid_cap(h, nq, 256), 256, 0, st>>>(nq, ucnt, counts);
+            FM_CUDA_TRY(h, cudaGetLastError());
+            uint64_t need = 0;
+            FM_CUDA_TRY(h, cudaMemcpyAsync(&need, uoff + nq, 8, cudaMemcpyDeviceToHost, st));
+            FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+            if (pairs_needed) *pairs_needed = need;
+            h->last_nq = nq;
+            h->last_total = need;
+            h->last_off_ucnt = off_ucnt;
+            h->last_off_start = off_start;
+            h->last_off_uoff = off_uoff;
+            h->last_off_grp = off_grp;
+            h->last_valid = true;
+            if (sp->stats) {
+                k_add_stats<<<1, 32, 0, st>>>(d_stats, d_raw_count, (unsigned long long *)sp->stats);
+                FM_CUDA_TRY(h, cudaGetLastError());
+            }
+            if (need > pair_capacity) {
+                FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+                return set_error(h, FM_ETRUNC, "pair capacity " + std::to_string(pair_capacity) +
+                                                   " below the " + std::to_string(need) + " intervals found");
+            }
+            if (need) {
+                k_compact<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, st>>>(nq, ucnt, start, uoff, grouped, pairs);
+                FM_CUDA_TRY(h, cudaGetLastError());
+            }
+            uint32_t derr = 0;
+            FM_CUDA_TRY(h, cudaMemcpyAsync(&derr, h->d_err + kErrDcalc, 4, cudaMemcpyDeviceToHost, st));
+            FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+            if (derr & kErrReadLen) return set_error(h, FM_EINVAL, "a read is longer than 255 symbols");
+            if (derr & kErrDomain) return set_error(h, FM_EINVAL, "a read holds a code above 3");
+            return FM_OK;
+        }
+    }
+    return set_error(h, FM_ENOMEM, "search scratch did not converge after 8 regrowths");
+}
+
+}  // namespace fm

@@ -1,0 +1,231 @@
+// Internal declarations of the fmocc CUDA library (sm_103a).
+//
+// Resident layout (per index, forward and reverse): an array of checkpoint blocks.  Block j
+// covers BWT rows [j*I, (j+1)*I):
+//   bytes  0..15  uint32 cnt[4]: rank(c, j*I) for c = A,C,G,T ($ excluded)
+//   bytes 16..    the I BWT symbols of the block, 2 bits each, symbol t of the block at bits
+//                 2(t%32)..2(t%32)+1 of 64-bit word t/32 (the little-endian 2-bit code of
+//                 Fig. 2); $ is stored as A and corrected for through dollar_row
+//   I = 64: 32-byte blocks (one DRAM sector); I = 128: 64 bytes; I = 256: 96 bytes (80 used).
+// One extra final block holds the totals, so rank(c, n+1) needs no special case.
+// This interleaving of counters and symbols in one block follows the bucket layout the paper
+// describes in Sec. 2 (128 symbols with 4 x 64-bit counters); here the counters are uint32
+// and the block is sized to the 32-byte sector.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/fmocc.h"
+
+namespace fm {
+
+constexpr int kMaxReadLen = 255;   // read length limit of the search kernels (8-bit position)
+constexpr int kMaxZ = 7;
+constexpr int kMaxGaps = 7;
+
+__host__ __device__ constexpr uint32_t block_bytes(uint32_t I) {
+    return I == 64 ? 32u : (I == 128 ? 64u : 96u);
+}
+
+// Device view of one resident index.
+struct IndexView {
+    const uint8_t *blocks;   // n_blocks * block_bytes(I)
+    uint32_t n;              // reference length
+    uint32_t dollar;         // row holding $
+    uint32_t C[5];
+};
+
+// Per-search device pointers (scratch owned by the handle).
+struct Scratch {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct Tuning {
+    uint32_t warps_per_block = 8;
+    uint32_t blocks_per_sm = 0;     // 0: from the occupancy calculator
+    uint32_t chunk = 16;
+    uint32_t plain_block = 128;
+};
+
+}  // namespace fm
+
+struct fm_index {
+    int device = 0;
+    int sms = 0;
+    uint64_t n = 0;
+    uint32_t interval = 64;
+    uint32_t bbytes = 32;
+    uint64_t n_blocks = 0;
+    uint64_t C[5] = {0, 0, 0, 0, 0};
+    uint64_t dollar = 0, rev_dollar = 0;
+    bool has_rev = false;
+    uint8_t *d_fwd = nullptr;        // forward checkpoint blocks
+    uint8_t *d_rev = nullptr;        // reverse(R) checkpoint blocks
+    uint32_t *d_sa_sample = nullptr; // SA[j * sa_rate]
+    uint64_t sa_rate = 32;
+    uint64_t n_sa_sample = 0;
+    uint32_t *d_err = nullptr;       // device error word (1 word per call kind)
+    // grow-on-demand scratch of the search calls
+    fm::Scratch s_qmeta, s_raw, s_spill, s_group, s_scan, s_plain, s_misc;
+    fm::Tuning tune;
+    std::string err;
+    // canonical results of the last search (in s_group), for fm_inexact_fetch
+    uint32_t last_nq = 0;
+    uint64_t last_total = 0;
+    bool last_valid = false;
+    size_t last_off_ucnt = 0, last_off_start = 0, last_off_uoff = 0, last_off_grp = 0;
+};
+
+namespace fm {
+
+// error plumbing -------------------------------------------------------------------------
+int set_error(fm_index *h, int code, const std::string &msg);
+int set_global_error(int code, const std::string &msg);
+int cuda_status(fm_index *h, cudaError_t e, const char *what);
+int ensure_scratch(fm_index *h, Scratch &s, size_t bytes);
+int device_sms(int device);
+
+#define FM_CUDA_TRY(h, call)                                   \
+    do {                                                       \
+        cudaError_t _e = (call);                               \
+        if (_e != cudaSuccess) return fm::cuda_status(h, _e, #call); \
+    } while (0)
+
+// build entry (fm_build.cu) ----------------------------------------------------------------
+int build_index(fm_index *h, const uint8_t *d_codes, uint64_t n, bool reverse, uint8_t **out_blocks,
+                uint64_t *out_dollar, uint64_t C[5], uint32_t **out_sa_sample, cudaStream_t st);
+
+// search entries (fm_search.cu, fm_inexact.cu) ------------------------------------------
+IndexView view_fwd(const fm_index *h);
+IndexView view_rev(const fm_index *h);
+
+int launch_occ8(fm_index *h, const uint32_t *k, const uint32_t *l, uint32_t *out8, uint64_t N,
+                cudaStream_t st);
+int launch_exact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
+                 uint32_t *k_out, uint32_t *l_out, cudaStream_t st);
+// D lower bound per query; qmeta (uint4 per query) and/or D_out (uint8 per position)
+int launch_dcalc(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
+                 uint32_t strands, uint4 *qmeta, uint8_t *D_out, cudaStream_t st);
+int fetch_inexact(fm_index *h, uint32_t *pairs, uint64_t pair_capacity, cudaStream_t st);
+int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
+                const fm_search_params *sp, uint32_t *counts, uint64_t *offsets, uint32_t *pairs,
+                uint64_t pair_capacity, uint64_t *pairs_needed, cudaStream_t st);
+
+// error word slots
+enum ErrSlot { kErrOcc = 0, kErrExact = 1, kErrDcalc = 2, kErrSearch = 3, kErrBuild = 4,
+               kErrSlots = 8 };
+// error bits
+enum ErrBits : uint32_t {
+    kErrDomain = 1u,      // a query or symbol outside the domain
+    kErrSpill = 2u,       // frontier spill capacity exceeded
+    kErrStack = 4u,       // plain-kernel stack capacity exceeded
+    kErrReadLen = 8u,     // read longer than kMaxReadLen
+};
+
+// -----------------------------------------------------------------------------------------
+// device helpers
+// -----------------------------------------------------------------------------------------
+
+// 256-bit read-only load of one 32-byte sector (sm_100+ PTX).
+__device__ __forceinline__ void ldg256(const void *p, uint4 &a, uint4 &b) {
+    asm volatile("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z),
+                   "=r"(b.w)
+                 : "l"(p));
+}
+
+__device__ __forceinline__ uint64_t u64of(uint32_t lo, uint32_t hi) {
+    return (uint64_t)lo | ((uint64_t)hi << 32);
+}
+
+// Symbols A,C,G,T counted among the first t symbols (t in [0,32]) of a 64-bit word of 2-bit
+// codes: lo bit set for C(01) and T(11), hi bit set for G(10) and T(11).
+__device__ __forceinline__ void count_word(uint64_t w, uint32_t t, uint32_t &c, uint32_t &g,
+                                           uint32_t &tt) {
+    const uint64_t m55 = 0x5555555555555555ull;
+    uint64_t mask = t >= 32 ? ~0ull : ((1ull << (2 * t)) - 1ull);
+    uint64_t lo = w & m55 & mask;
+    uint64_t hi = (w >> 1) & m55 & mask;
+    uint32_t both = __popcll(lo & hi);
+    tt += both;
+    c += __popcll(lo) - both;
+    g += __popcll(hi) - both;
+}
+
+// Loaded checkpoint block: counters plus up to 8 words (I <= 256).
+template <int I>
+struct Blk {
+    uint4 cnt;
+    uint64_t w[I / 32];
+};
+
+// Load the block of rank position p (only the sectors the offsets up to `upto` need are
+// read for I >= 128).
+template <int I>
+__device__ __forceinline__ void load_block(const uint8_t *blocks, uint32_t j, uint32_t upto,
+                                           Blk<I> &B) {
+    const uint8_t *p = blocks + (size_t)j * block_bytes(I);
+    uint4 a, b;
+    ldg256(p, a, b);
+    B.cnt = a;
+    B.w[0] = u64of(b.x, b.y);
+    B.w[1] = u64of(b.z, b.w);
+    if constexpr (I >= 128) {
+        if (upto > 64) {
+            uint4 c, d;
+            ldg256(p + 32, c, d);
+            B.w[2] = u64of(c.x, c.y);
+            B.w[3] = u64of(c.z, c.w);
+            if constexpr (I == 256) {
+                B.w[4] = u64of(d.x, d.y);
+                B.w[5] = u64of(d.z, d.w);
+                if (upto > 192) {
+                    uint4 e, f;
+                    ldg256(p + 64, e, f);
+                    B.w[6] = u64of(e.x, e.y);
+                    B.w[7] = u64of(e.z, e.w);
+                } else {
+                    B.w[6] = B.w[7] = 0;
+                }
+            }
+        } else {
+            B.w[2] = B.w[3] = 0;
+            if constexpr (I == 256) B.w[4] = B.w[5] = B.w[6] = B.w[7] = 0;
+        }
+    }
+}
+
+// rank(c, p) for c = A,C,G,T given the loaded block of p (block index j = p / I).
+template <int I>
+__device__ __forceinline__ void rank4_in(const Blk<I> &B, uint32_t j, uint32_t p, uint32_t dollar,
+                                         uint32_t r[4]) {
+    uint32_t o = p - j * (uint32_t)I;
+    uint32_t c = 0, g = 0, t = 0;
+#pragma unroll
+    for (int wi = 0; wi < I / 32; ++wi) {
+        int32_t left = (int32_t)o - 32 * wi;
+        if (left > 0) count_word(B.w[wi], (uint32_t)(left > 32 ? 32 : left), c, g, t);
+    }
+    uint32_t a = o - c - g - t;
+    uint32_t base = j * (uint32_t)I;
+    a -= (dollar >= base && dollar < p) ? 1u : 0u;
+    r[0] = B.cnt.x + a;
+    r[1] = B.cnt.y + c;
+    r[2] = B.cnt.z + g;
+    r[3] = B.cnt.w + t;
+}
+
+// rank(b, p) for one symbol b.
+template <int I>
+__device__ __forceinline__ uint32_t rank1_in(const Blk<I> &B, uint32_t j, uint32_t p,
+                                             uint32_t dollar, uint32_t b) {
+    uint32_t r[4];
+    rank4_in<I>(B, j, p, dollar, r);
+    return b == 0 ? r[0] : (b == 1 ? r[1] : (b == 2 ? r[2] : r[3]));
+}
+
+}  // namespace fm

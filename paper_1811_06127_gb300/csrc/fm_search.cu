@@ -1,0 +1,260 @@
+// Hot-path kernels of the exact search: the eight-Occ query (Sec. 2 closing remarks, Sec. 3.3),
+// Listing 1 (ExactRecur) and the D lower bound of the inexact search (forward extension on the
+// index of reverse(R)).
+//
+// All three read the resident checkpoint blocks with 256-bit read-only gathers and count
+// symbols with mask-and-popcount on the 2-bit words (fm_internal.cuh, rank4_in).  The role of
+// the paper's half-byte lookup / SAD extraction (Sec. 3.1-3.2) is taken by that popcount:
+// per 64-bit word, lo = w & 0x55.., hi = (w >> 1) & 0x55.., T = popc(lo & hi),
+// C = popc(lo) - T, G = popc(hi) - T, and A is the remainder minus the $ correction.
+#include "fm_internal.cuh"
+
+namespace fm {
+
+IndexView view_fwd(const fm_index *h) {
+    IndexView v;
+    v.blocks = h->d_fwd;
+    v.n = (uint32_t)h->n;
+    v.dollar = (uint32_t)h->dollar;
+    for (int i = 0; i < 5; ++i) v.C[i] = (uint32_t)h->C[i];
+    return v;
+}
+
+IndexView view_rev(const fm_index *h) {
+    IndexView v = view_fwd(h);
+    v.blocks = h->d_rev;
+    v.dollar = (uint32_t)h->rev_dollar;
+    return v;
+}
+
+namespace {
+
+// -------------------------------------------------------------------------------------------
+// eight Occ values per query
+// -------------------------------------------------------------------------------------------
+// Each thread takes Q queries (q, q + S, ..., S = grid size) and issues all their block loads
+// before counting, so that 1..2*Q independent gathers per thread are in flight.
+template <int I, int Q>
+__global__ void __launch_bounds__(256) k_occ8(IndexView ix, const uint32_t *__restrict__ kq,
+                                              const uint32_t *__restrict__ lq,
+                                              uint32_t *__restrict__ out, uint64_t N,
+                                              uint32_t *__restrict__ err) {
+    const uint64_t S = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t q0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q0 < N; q0 += S * Q) {
+        uint32_t p1[Q], p2[Q], j1[Q], j2[Q];
+        bool ok[Q];
+        Blk<I> B1[Q], B2[Q];
+#pragma unroll
+        for (int t = 0; t < Q; ++t) {
+            uint64_t q = q0 + (uint64_t)t * S;
+            ok[t] = false;
+            p1[t] = p2[t] = 0;
+            if (q < N) {
+                uint32_t k = __ldcs(kq + q), l = __ldcs(lq + q);
+                ok[t] = (k <= ix.n + 1u) && (l <= ix.n);
+                if (ok[t]) {
+                    p1[t] = k;       // Occ(c, k-1) = rank(c, k)
+                    p2[t] = l + 1u;  // Occ(c, l)   = rank(c, l+1)
+                }
+            }
+            j1[t] = p1[t] / I;
+            j2[t] = p2[t] / I;
+        }
+#pragma unroll
+        for (int t = 0; t < Q; ++t) {
+            if (ok[t]) {
+                uint32_t o1 = p1[t] - j1[t] * I, o2 = p2[t] - j2[t] * I;
+                if (j1[t] == j2[t]) {
+                    load_block<I>(ix.blocks, j1[t], o1 > o2 ? o1 : o2, B1[t]);
+                } else {
+                    load_block<I>(ix.blocks, j1[t], o1, B1[t]);
+                    load_block<I>(ix.blocks, j2[t], o2, B2[t]);
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < Q; ++t) {
+            uint64_t q = q0 + (uint64_t)t * S;
+            if (q >= N) continue;
+            uint32_t a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
+            if (ok[t]) {
+                rank4_in<I>(B1[t], j1[t], p1[t], ix.dollar, a);
+                rank4_in<I>(j1[t] == j2[t] ? B1[t] : B2[t], j2[t], p2[t], ix.dollar, b);
+            } else {
+                atomicOr(err, kErrDomain);
+            }
+            uint4 *o = reinterpret_cast<uint4 *>(out + 8 * q);
+            __stcs(o, make_uint4(a[0], a[1], a[2], a[3]));
+            __stcs(o + 1, make_uint4(b[0], b[1], b[2], b[3]));
+        }
+    }
+}
+
+// -------------------------------------------------------------------------------------------
+// Listing 1, one thread per read
+// -------------------------------------------------------------------------------------------
+template <int I>
+__global__ void __launch_bounds__(128) k_exact(IndexView ix, const uint8_t *__restrict__ reads,
+                                               const uint32_t *__restrict__ offs, uint32_t nr,
+                                               uint32_t *__restrict__ kout,
+                                               uint32_t *__restrict__ lout,
+                                               uint32_t *__restrict__ err) {
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
+        const uint32_t s = offs[r], e = offs[r + 1];
+        uint32_t k = 0, l = ix.n;
+        for (uint32_t i = e; i > s; --i) {
+            const uint32_t b = reads[i - 1];
+            if (b > 3u) {
+                atomicOr(err, kErrDomain);
+                k = 0;
+                l = ix.n;
+                break;
+            }
+            const uint32_t pk = k, pl = l + 1u;
+            const uint32_t jk = pk / I, jl = pl / I;
+            Blk<I> Bk, Bl;
+            const uint32_t ok = pk - jk * I, ol = pl - jl * I;
+            if (jk == jl) {
+                load_block<I>(ix.blocks, jk, ok > ol ? ok : ol, Bk);
+            } else {
+                load_block<I>(ix.blocks, jk, ok, Bk);
+                load_block<I>(ix.blocks, jl, ol, Bl);
+            }
+            const uint32_t rk = rank1_in<I>(Bk, jk, pk, ix.dollar, b);
+            const uint32_t rl = rank1_in<I>(jk == jl ? Bk : Bl, jl, pl, ix.dollar, b);
+            k = ix.C[b] + rk + 1u;
+            l = ix.C[b] + rl;
+        }
+        kout[r] = k;
+        lout[r] = l;
+    }
+}
+
+// -------------------------------------------------------------------------------------------
+// D lower bound by forward extension on the index of reverse(R), one thread per query.
+// qmeta[q] = { D breakpoints 0..3, D breakpoints 4..7, read start, m | strand << 8 }, with
+// breakpoint j = first position i at which D(i) >= j+1 (255: never), so that
+// D(i) = #{j : bp_j <= i}.
+// -------------------------------------------------------------------------------------------
+template <int I>
+__global__ void __launch_bounds__(128) k_dcalc(IndexView rv, const uint8_t *__restrict__ reads,
+                                               const uint32_t *__restrict__ offs, uint32_t nr,
+                                               uint32_t strands, uint4 *__restrict__ qmeta,
+                                               uint8_t *__restrict__ D_out,
+                                               uint32_t *__restrict__ err) {
+    const uint32_t nq = nr * strands;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        const uint32_t r = strands == 2 ? q >> 1 : q;
+        const uint32_t strand = strands == 2 ? (q & 1u) : 0u;
+        const uint32_t s = offs[r];
+        const uint32_t m = offs[r + 1] - s;
+        uint8_t bp[8] = {255, 255, 255, 255, 255, 255, 255, 255};
+        bool bad = m > (uint32_t)kMaxReadLen;
+        if (bad) atomicOr(err, kErrReadLen);
+        uint32_t k = 0, l = rv.n, z = 0;
+        uint8_t *Dq = D_out ? D_out + (size_t)strands * s + (size_t)strand * m : nullptr;
+        for (uint32_t i = 0; i < m && !bad; ++i) {
+            uint32_t b = strand ? reads[s + m - 1 - i] : reads[s + i];
+            if (b > 3u) {
+                atomicOr(err, kErrDomain);
+                bad = true;
+                break;
+            }
+            if (strand) b = 3u - b;
+            const uint32_t pk = k, pl = l + 1u;
+            const uint32_t jk = pk / I, jl = pl / I;
+            Blk<I> Bk, Bl;
+            const uint32_t ok = pk - jk * I, ol = pl - jl * I;
+            if (jk == jl) {
+                load_block<I>(rv.blocks, jk, ok > ol ? ok : ol, Bk);
+            } else {
+                load_block<I>(rv.blocks, jk, ok, Bk);
+                load_block<I>(rv.blocks, jl, ol, Bl);
+            }
+            const uint32_t k2 = rv.C[b] + rank1_in<I>(Bk, jk, pk, rv.dollar, b) + 1u;
+            const uint32_t l2 = rv.C[b] + rank1_in<I>(jk == jl ? Bk : Bl, jl, pl, rv.dollar, b);
+            if (k2 > l2) {   // W[j..i] does not occur: close the window, restart after i
+                if (z < 8) bp[z] = (uint8_t)i;
+                ++z;
+                k = 0;
+                l = rv.n;
+            } else {
+                k = k2;
+                l = l2;
+            }
+            if (Dq) Dq[i] = (uint8_t)(z > 255 ? 255 : z);
+        }
+        if (qmeta) {
+            uint4 mt;
+            mt.x = (uint32_t)bp[0] | ((uint32_t)bp[1] << 8) | ((uint32_t)bp[2] << 16) |
+                   ((uint32_t)bp[3] << 24);
+            mt.y = (uint32_t)bp[4] | ((uint32_t)bp[5] << 8) | ((uint32_t)bp[6] << 16) |
+                   ((uint32_t)bp[7] << 24);
+            mt.z = s;
+            // a bad query is given length 0: the search then reports nothing for it
+            mt.w = (bad ? 0u : m) | (strand << 8);
+            qmeta[q] = mt;
+        }
+    }
+}
+
+int grid_occ(fm_index *h, uint64_t work, int block) {
+    uint64_t g = (work + block - 1) / block;
+    uint64_t cap = (uint64_t)h->sms * (2048 / block) * 4;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+int launch_occ8(fm_index *h, const uint32_t *k, const uint32_t *l, uint32_t *out8, uint64_t N,
+                cudaStream_t st) {
+    if (N == 0) return FM_OK;
+    IndexView ix = view_fwd(h);
+    uint32_t *err = h->d_err + kErrOcc;
+    constexpr int Q = 2;
+    const int block = 256;
+    int grid = grid_occ(h, (N + Q - 1) / Q, block);
+    switch (h->interval) {
+        case 64: k_occ8<64, Q><<<grid, block, 0, st>>>(ix, k, l, out8, N, err); break;
+        case 128: k_occ8<128, Q><<<grid, block, 0, st>>>(ix, k, l, out8, N, err); break;
+        default: k_occ8<256, Q><<<grid, block, 0, st>>>(ix, k, l, out8, N, err); break;
+    }
+    FM_CUDA_TRY(h, cudaGetLastError());
+    return FM_OK;
+}
+
+int launch_exact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
+                 uint32_t *k_out, uint32_t *l_out, cudaStream_t st) {
+    if (n_reads == 0) return FM_OK;
+    IndexView ix = view_fwd(h);
+    uint32_t *err = h->d_err + kErrExact;
+    const int block = 128;
+    int grid = grid_occ(h, n_reads, block);
+    switch (h->interval) {
+        case 64: k_exact<64><<<grid, block, 0, st>>>(ix, reads, offs, n_reads, k_out, l_out, err); break;
+        case 128: k_exact<128><<<grid, block, 0, st>>>(ix, reads, offs, n_reads, k_out, l_out, err); break;
+        default: k_exact<256><<<grid, block, 0, st>>>(ix, reads, offs, n_reads, k_out, l_out, err); break;
+    }
+    FM_CUDA_TRY(h, cudaGetLastError());
+    return FM_OK;
+}
+
+int launch_dcalc(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
+                 uint32_t strands, uint4 *qmeta, uint8_t *D_out, cudaStream_t st) {
+    uint64_t nq = (uint64_t)n_reads * strands;
+    if (nq == 0) return FM_OK;
+    IndexView rv = view_rev(h);
+    uint32_t *err = h->d_err + kErrDcalc;
+    const int block = 128;
+    int grid = grid_occ(h, nq, block);
+    switch (h->interval) {
+        case 64: k_dcalc<64><<<grid, block, 0, st>>>(rv, reads, offs, n_reads, strands, qmeta, D_out, err); break;
+        case 128: k_dcalc<128><<<grid, block, 0, st>>>(rv, reads, offs, n_reads, strands, qmeta, D_out, err); break;
+        default: k_dcalc<256><<<grid, block, 0, st>>>(rv, reads, offs, n_reads, strands, qmeta, D_out, err); break;
+    }
+    FM_CUDA_TRY(h, cudaGetLastError());
+    return FM_OK;
+}
+
+}  // namespace fm

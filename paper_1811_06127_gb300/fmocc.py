@@ -1,0 +1,325 @@
+"""Python binding of the fmocc C ABI (include/fmocc.h).
+
+Argument marshalling only: every step of the search runs in libfmocc.so's kernels.  Device
+buffers are torch CUDA tensors (uint32 values travel in int32 tensors, bit for bit; uint64 in
+int64), streams are torch streams.  There is no CPU path: without the built library every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libfmocc.so")
+
+FM_OK, FM_EINVAL, FM_ENOMEM, FM_ECUDA, FM_ETRUNC, FM_ETIMEOUT, FM_EIO = range(7)
+FM_BUILD_CODES = 1
+FM_BUILD_FORWARD_ONLY = 2
+FM_KERNEL_AUTO, FM_KERNEL_PLAIN, FM_KERNEL_PERSISTENT = 0, 1, 2
+KERNELS = {"auto": FM_KERNEL_AUTO, "plain": FM_KERNEL_PLAIN, "persistent": FM_KERNEL_PERSISTENT}
+
+
+class FmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fmocc status {code}: {msg}")
+        self.code = code
+
+
+class fm_params(C.Structure):
+    _fields_ = [("interval", C.c_uint32), ("flags", C.c_uint32), ("device", C.c_int32),
+                ("reserved", C.c_uint32)]
+
+
+class fm_info_t(C.Structure):
+    _fields_ = [("n", C.c_uint64), ("interval", C.c_uint32), ("block_bytes", C.c_uint32),
+                ("C", C.c_uint64 * 5), ("dollar_row", C.c_uint64), ("rev_dollar_row", C.c_uint64),
+                ("n_blocks", C.c_uint64), ("sa_sample_rate", C.c_uint64),
+                ("bytes_device", C.c_uint64), ("has_reverse", C.c_int32), ("device", C.c_int32)]
+
+
+class fm_search_params(C.Structure):
+    _fields_ = [("z", C.c_uint32), ("max_gaps", C.c_uint32), ("strands", C.c_uint32),
+                ("kernel", C.c_uint32), ("stats", C.c_void_p)]
+
+
+class fm_tuning(C.Structure):
+    _fields_ = [("warps_per_block", C.c_uint32), ("blocks_per_sm", C.c_uint32),
+                ("chunk", C.c_uint32), ("plain_block", C.c_uint32)]
+
+
+# every symbol include/fmocc.h declares
+EXPORTS = ["fm_build", "fm_free", "fm_last_error", "fm_info", "fm_get_bwt", "fm_save", "fm_load",
+           "fm_occ8", "fm_exact", "fm_dcalc", "fm_inexact", "fm_inexact_fetch", "fm_set_tuning",
+           "fm_get_tuning"]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libfmocc.so (raises when it has not been built)."""
+    global _lib
+    if _lib is not None and path == LIB_PATH:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built: run __graft_entry__.build() (needs nvcc)")
+    lib = C.CDLL(path)
+    P, u32, u64 = C.c_void_p, C.c_uint32, C.c_uint64
+    lib.fm_build.argtypes = [P, u64, C.POINTER(fm_params), C.POINTER(P)]
+    lib.fm_free.argtypes = [P]
+    lib.fm_free.restype = None
+    lib.fm_last_error.argtypes = [P]
+    lib.fm_last_error.restype = C.c_char_p
+    lib.fm_info.argtypes = [P, C.POINTER(fm_info_t)]
+    lib.fm_get_bwt.argtypes = [P, C.c_int, P]
+    lib.fm_save.argtypes = [P, C.c_char_p]
+    lib.fm_load.argtypes = [C.c_char_p, C.POINTER(fm_params), C.POINTER(P)]
+    lib.fm_occ8.argtypes = [P, P, P, P, u64, P]
+    lib.fm_exact.argtypes = [P, P, P, u32, P, P, P]
+    lib.fm_dcalc.argtypes = [P, P, P, u32, u32, P, P]
+    lib.fm_inexact.argtypes = [P, P, P, u32, C.POINTER(fm_search_params), P, P, P, u64,
+                               C.POINTER(C.c_uint64), P]
+    lib.fm_inexact_fetch.argtypes = [P, P, u64, P]
+    lib.fm_set_tuning.argtypes = [P, C.POINTER(fm_tuning)]
+    lib.fm_get_tuning.argtypes = [P, C.POINTER(fm_tuning)]
+    for name in EXPORTS:
+        f = getattr(lib, name)
+        if name not in ("fm_free", "fm_last_error"):
+            f.restype = C.c_int
+    if path == LIB_PATH:
+        _lib = lib
+    return lib
+
+
+def _check(rc: int, h=None):
+    if rc != FM_OK:
+        msg = load_library().fm_last_error(h.ptr if h is not None else None)
+        raise FmError(rc, (msg or b"").decode(errors="replace"))
+
+
+def _dptr(t: torch.Tensor | None, dtypes, what: str):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype not in dtypes:
+        raise TypeError(f"{what} must have dtype in {dtypes}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+_U32 = (torch.int32,) + ((torch.uint32,) if hasattr(torch, "uint32") else ())
+_U64 = (torch.int64,) + ((torch.uint64,) if hasattr(torch, "uint64") else ())
+_U8 = (torch.uint8,)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Index:
+    """Handle of a resident index (fm_index*)."""
+
+    def __init__(self, ptr: int):
+        self.ptr = C.c_void_p(ptr)
+
+    def close(self):
+        if self.ptr and self.ptr.value:
+            load_library().fm_free(self.ptr)
+            self.ptr = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # convenience forwards
+    def info(self):
+        return fm_info(self)
+
+    def occ8(self, k, l, out=None, stream=None):
+        return fm_occ8(self, k, l, out, stream)
+
+    def exact(self, reads, offs, stream=None):
+        return fm_exact(self, reads, offs, stream=stream)
+
+    def dcalc(self, reads, offs, strands=1, stream=None):
+        return fm_dcalc(self, reads, offs, strands, stream=stream)
+
+    def inexact(self, reads, offs, z, max_gaps=0, strands=1, kernel="auto", **kw):
+        return fm_inexact(self, reads, offs, z, max_gaps, strands, kernel, **kw)
+
+
+def fm_build(ref, interval: int = 64, flags: int = 0, device: int = -1,
+             forward_only: bool = False) -> Index:
+    """Build the index of ``ref`` (bytes/str over ACGTacgt, or a uint8 numpy array of codes)."""
+    lib = load_library()
+    if isinstance(ref, np.ndarray):
+        buf = np.ascontiguousarray(ref, dtype=np.uint8)
+        flags |= FM_BUILD_CODES
+        ptr, n = buf.ctypes.data_as(C.c_void_p), buf.size
+    else:
+        if isinstance(ref, str):
+            ref = ref.encode()
+        buf = ref
+        ptr, n = C.c_char_p(buf), len(buf)
+    if forward_only:
+        flags |= FM_BUILD_FORWARD_ONLY
+    p = fm_params(interval, flags, device, 0)
+    out = C.c_void_p()
+    rc = lib.fm_build(C.cast(ptr, C.c_void_p), n, C.byref(p), C.byref(out))
+    _check(rc)
+    return Index(out.value)
+
+
+def fm_free(h: Index):
+    h.close()
+
+
+def fm_last_error(h: Index | None = None) -> str:
+    return (load_library().fm_last_error(h.ptr if h is not None else None) or b"").decode()
+
+
+def fm_info(h: Index) -> dict:
+    inf = fm_info_t()
+    _check(load_library().fm_info(h.ptr, C.byref(inf)), h)
+    return {"n": inf.n, "interval": inf.interval, "block_bytes": inf.block_bytes,
+            "C": list(inf.C), "dollar_row": inf.dollar_row, "rev_dollar_row": inf.rev_dollar_row,
+            "n_blocks": inf.n_blocks, "sa_sample_rate": inf.sa_sample_rate,
+            "bytes_device": inf.bytes_device, "has_reverse": bool(inf.has_reverse),
+            "device": inf.device}
+
+
+def fm_get_bwt(h: Index, rev: bool = False) -> np.ndarray:
+    n = fm_info(h)["n"]
+    out = np.empty(n + 1, dtype=np.uint8)
+    _check(load_library().fm_get_bwt(h.ptr, 1 if rev else 0, out.ctypes.data_as(C.c_void_p)), h)
+    return out
+
+
+def fm_save(h: Index, path: str):
+    _check(load_library().fm_save(h.ptr, path.encode()), h)
+
+
+def fm_load(path: str, device: int = -1) -> Index:
+    p = fm_params(0, 0, device, 0)
+    out = C.c_void_p()
+    _check(load_library().fm_load(path.encode(), C.byref(p), C.byref(out)))
+    return Index(out.value)
+
+
+def fm_occ8(h: Index, k: torch.Tensor, l: torch.Tensor, out: torch.Tensor | None = None,
+            stream=None) -> torch.Tensor:
+    """out[q] = [Occ(A..T, k[q]-1), Occ(A..T, l[q])] as an int32 [N, 8] CUDA tensor."""
+    N = k.numel()
+    if l.numel() != N:
+        raise ValueError("k and l differ in length")
+    if out is None:
+        out = torch.empty((N, 8), dtype=torch.int32, device=k.device)
+    rc = load_library().fm_occ8(h.ptr, _dptr(k, _U32, "k"), _dptr(l, _U32, "l"),
+                                _dptr(out, _U32, "out"), N, _stream(stream))
+    _check(rc, h)
+    return out
+
+
+def fm_exact(h: Index, reads: torch.Tensor, offs: torch.Tensor, k_out=None, l_out=None,
+             stream=None):
+    """Listing 1 intervals (k, l) per read, int32 CUDA tensors."""
+    nr = offs.numel() - 1
+    dev = offs.device
+    if k_out is None:
+        k_out = torch.empty(nr, dtype=torch.int32, device=dev)
+    if l_out is None:
+        l_out = torch.empty(nr, dtype=torch.int32, device=dev)
+    rc = load_library().fm_exact(h.ptr, _dptr(reads, _U8, "reads"), _dptr(offs, _U32, "offs"), nr,
+                                 _dptr(k_out, _U32, "k_out"), _dptr(l_out, _U32, "l_out"),
+                                 _stream(stream))
+    _check(rc, h)
+    return k_out, l_out
+
+
+def fm_dcalc(h: Index, reads: torch.Tensor, offs: torch.Tensor, strands: int = 1, D_out=None,
+             stream=None) -> torch.Tensor:
+    nr = offs.numel() - 1
+    total = int(reads.numel()) * strands
+    if D_out is None:
+        D_out = torch.empty(max(total, 1), dtype=torch.uint8, device=offs.device)
+    rc = load_library().fm_dcalc(h.ptr, _dptr(reads, _U8, "reads"), _dptr(offs, _U32, "offs"), nr,
+                                 strands, _dptr(D_out, _U8, "D_out"), _stream(stream))
+    _check(rc, h)
+    return D_out[:total]
+
+
+def fm_inexact(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int, max_gaps: int = 0,
+               strands: int = 1, kernel="auto", stats: torch.Tensor | None = None,
+               pair_capacity: int | None = None, counts=None, offsets=None, pairs=None,
+               stream=None):
+    """Listing 2 interval sets.  Returns (counts int32[nq], offsets int64[nq+1],
+    pairs int32[total, 2]); on FM_ETRUNC the pairs buffer is regrown and fetched again."""
+    lib = load_library()
+    nr = offs.numel() - 1
+    nq = nr * strands
+    dev = offs.device
+    kern = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    if counts is None:
+        counts = torch.empty(max(nq, 1), dtype=torch.int32, device=dev)
+    if offsets is None:
+        offsets = torch.empty(nq + 1, dtype=torch.int64, device=dev)
+    if pairs is None:
+        cap = pair_capacity if pair_capacity is not None else 4 * nq + 1024
+        pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=dev)
+    cap = pairs.shape[0]
+    sp = fm_search_params(z, max_gaps, strands, kern,
+                          _dptr(stats, _U64, "stats") if stats is not None else None)
+    need = C.c_uint64(0)
+    rc = lib.fm_inexact(h.ptr, _dptr(reads, _U8, "reads"), _dptr(offs, _U32, "offs"), nr,
+                        C.byref(sp), _dptr(counts, _U32, "counts"),
+                        _dptr(offsets, _U64, "offsets"), _dptr(pairs, _U32, "pairs"), cap,
+                        C.byref(need), _stream(stream))
+    if rc == FM_ETRUNC:
+        pairs = torch.empty((max(int(need.value), 1), 2), dtype=torch.int32, device=dev)
+        rc = lib.fm_inexact_fetch(h.ptr, _dptr(pairs, _U32, "pairs"), pairs.shape[0],
+                                  _stream(stream))
+    _check(rc, h)
+    return counts[:nq], offsets, pairs[:int(need.value)]
+
+
+def fm_inexact_fetch(h: Index, pairs: torch.Tensor, stream=None):
+    _check(load_library().fm_inexact_fetch(h.ptr, _dptr(pairs, _U32, "pairs"), pairs.shape[0],
+                                           _stream(stream)), h)
+    return pairs
+
+
+def fm_set_tuning(h: Index, warps_per_block=0, blocks_per_sm=0, chunk=0, plain_block=0):
+    t = fm_tuning(warps_per_block, blocks_per_sm, chunk, plain_block)
+    _check(load_library().fm_set_tuning(h.ptr, C.byref(t)), h)
+
+
+def fm_get_tuning(h: Index) -> dict:
+    t = fm_tuning()
+    _check(load_library().fm_get_tuning(h.ptr, C.byref(t)), h)
+    return {"warps_per_block": t.warps_per_block, "blocks_per_sm": t.blocks_per_sm,
+            "chunk": t.chunk, "plain_block": t.plain_block}
+
+
+# ---------------------------------------------------------------------------------------------
+# host-side helpers (marshalling of read batches)
+# ---------------------------------------------------------------------------------------------
+
+def to_device_reads(reads, device="cuda"):
+    """(codes uint8, offs int32) CUDA tensors from a synth.Reads batch."""
+    codes = torch.from_numpy(np.ascontiguousarray(reads.codes)).to(device)
+    offs = torch.from_numpy(np.ascontiguousarray(reads.offs).view(np.int32)).to(device)
+    return codes, offs

@@ -1,0 +1,287 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element.
+
+Every result here is integer and must be bit-exact (tolerance 0).  Sizes span several
+checkpoint blocks and leave ragged tails; the full-size configurations have their own file.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1811_06127_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fm():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1811_06127_gb300 import _build, fmocc
+    _build.build()
+    fmocc.load_library()
+    return fmocc
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def test_fig1_acag(fm):
+    h = fm.fm_build("ACAG")
+    inf = fm.fm_info(h)
+    assert inf["C"] == [0, 2, 3, 4, 4]
+    assert inf["dollar_row"] == 1
+    assert "".join("ACGT$"[c] for c in fm.fm_get_bwt(h)) == "G$CAA"
+    k = torch.tensor([0, 1, 2, 3, 4, 5], dtype=torch.int32, device="cuda")
+    l = torch.tensor([0, 1, 2, 3, 4, 4], dtype=torch.int32, device="cuda")
+    out = _u32(fm.fm_occ8(h, k, l))
+    fig1 = np.array([[0, 0, 1, 0], [0, 0, 1, 0], [0, 1, 1, 0], [1, 1, 1, 0], [2, 1, 1, 0]])
+    for q in range(6):
+        kk, ll = int(k[q]), int(l[q])
+        want_k = fig1[kk - 1] if kk >= 1 else np.zeros(4)
+        assert out[q, :4].tolist() == want_k.tolist()
+        assert out[q, 4:].tolist() == fig1[ll].tolist()
+    for w, exp in (("A", (1, 2)), ("G", (4, 4)), ("CA", (3, 3)), ("AG", (2, 2)), ("T", (5, 4))):
+        codes = torch.from_numpy(synth.from_ascii(w)).cuda()
+        offs = torch.tensor([0, len(w)], dtype=torch.int32, device="cuda")
+        kk, ll = fm.fm_exact(h, codes, offs)
+        assert (int(kk[0]), int(ll[0])) == exp
+    h.close()
+
+
+TEXTS = [("uniform", 1), ("uniform", 2), ("uniform", 31), ("uniform", 63), ("uniform", 64),
+         ("uniform", 65), ("uniform", 127), ("uniform", 128), ("uniform", 255), ("uniform", 256),
+         ("uniform", 257), ("uniform", 1000), ("periodic", 3000), ("homopolymer", 777),
+         ("repeat", 100_000), ("uniform", 1_000_000)]
+
+
+def _text(kind, n):
+    if kind == "uniform":
+        return synth.uniform_text(1000 + n, n)
+    if kind == "periodic":
+        return synth.from_ascii(("ACGTTGCA" * (n // 8 + 1))[:n])
+    if kind == "homopolymer":
+        return synth.from_ascii(("A" * 300 + "C" + "A" * 300 + "GT" * 100)[:n])
+    return synth.repeat_text(77, n, families=20, min_len=300, max_len=3000)
+
+
+@pytest.mark.parametrize("interval", [64, 128, 256])
+@pytest.mark.parametrize("kind,n", TEXTS)
+def test_bwt_c_dollar(fm, kind, n, interval):
+    R = _text(kind, n)
+    h = fm.fm_build(R, interval=interval)
+    ix = oracle.Index(R, "sais")
+    inf = fm.fm_info(h)
+    assert inf["C"] == ix.C.tolist()
+    assert inf["dollar_row"] == ix.dollar_row
+    assert np.array_equal(fm.fm_get_bwt(h), ix.bwt)
+    # the reverse index is the index of reverse(R)
+    ixr = oracle.Index(R[::-1].copy(), "sais")
+    assert inf["rev_dollar_row"] == ixr.dollar_row
+    assert np.array_equal(fm.fm_get_bwt(h, rev=True), ixr.bwt)
+    h.close()
+
+
+def _edge_queries(n, I):
+    ks, ls = [], []
+    cand = sorted({0, 1, n, n + 1, *[j * I + d for j in range(0, (n + 1) // I + 1)
+                                     for d in (-1, 0, 1, I - 1) if 0 <= j * I + d <= n + 1]})
+    cand = cand[:400]
+    for k in cand:
+        for l in (k - 1, k, k + 1, n, 0):
+            if 0 <= l <= n and 0 <= k <= n + 1:
+                ks.append(k)
+                ls.append(l)
+    return np.array(ks, np.uint32), np.array(ls, np.uint32)
+
+
+@pytest.mark.parametrize("interval", [64, 128, 256])
+@pytest.mark.parametrize("kind,n", [("uniform", 1), ("uniform", 65), ("uniform", 1000),
+                                    ("repeat", 100_000), ("uniform", 1_000_000)])
+def test_occ8_matches_oracle(fm, kind, n, interval):
+    R = _text(kind, n)
+    h = fm.fm_build(R, interval=interval, forward_only=True)
+    ix = oracle.Index(R, "sais")
+    k1, l1 = synth.occ_queries_uniform(5, n, 200_000)
+    k2, l2 = synth.occ_queries_mixed(6, n, 200_000, interval)
+    k3, l3 = _edge_queries(n, interval)
+    k = np.concatenate([k1, k2, k3])
+    l = np.concatenate([l1, l2, l3])
+    got = _u32(fm.fm_occ8(h, torch.from_numpy(k.view(np.int32)).cuda(),
+                          torch.from_numpy(l.view(np.int32)).cuda()))
+    want = ix.occ8(k, l)
+    assert np.array_equal(got, want)
+    h.close()
+
+
+def test_occ8_domain_error_and_empty(fm):
+    R = _text("uniform", 1000)
+    h = fm.fm_build(R)
+    e = torch.empty(0, dtype=torch.int32, device="cuda")
+    assert fm.fm_occ8(h, e, e).shape == (0, 8)
+    k = torch.tensor([0, 1002], dtype=torch.int32, device="cuda")
+    l = torch.tensor([5, 5], dtype=torch.int32, device="cuda")
+    with pytest.raises(fm.FmError) as ei:
+        fm.fm_occ8(h, k, l)
+    assert ei.value.code == fm.FM_EINVAL
+    # the handle stays usable
+    k = torch.tensor([0, 1001], dtype=torch.int32, device="cuda")
+    out = _u32(fm.fm_occ8(h, k, l))
+    assert np.array_equal(out, oracle.Index(R).occ8(np.array([0, 1001], np.uint32),
+                                                    np.array([5, 5], np.uint32)))
+    h.close()
+
+
+@pytest.mark.parametrize("interval", [64, 128, 256])
+def test_exact_matches_oracle(fm, interval):
+    R = synth.uniform_text(1811061271, 1_000_000)
+    h = fm.fm_build(R, interval=interval)
+    ix = oracle.Index(R, "sais")
+    reads = synth.exact_reads(1811061271, R, 10_000, 32)
+    ragged = synth.sample_reads(3, R, 3000, 0, 200, sub_rate=0.01, random_frac=0.2)
+    for rd in (reads, ragged):
+        codes, offs = fm.to_device_reads(rd)
+        k, l = fm.fm_exact(h, codes, offs)
+        kw, lw = ix.exact(rd.codes, rd.offs)
+        assert np.array_equal(_u32(k), kw)
+        assert np.array_equal(_u32(l), lw)
+    h.close()
+
+
+def test_exact_bad_code(fm):
+    h = fm.fm_build(_text("uniform", 1000))
+    codes = torch.tensor([0, 1, 7, 2], dtype=torch.uint8, device="cuda")
+    offs = torch.tensor([0, 2, 4], dtype=torch.int32, device="cuda")
+    with pytest.raises(fm.FmError):
+        fm.fm_exact(h, codes, offs)
+    h.close()
+
+
+@pytest.mark.parametrize("interval", [64, 256])
+def test_dcalc_matches_oracle(fm, interval):
+    R = synth.repeat_text(5, 300_000, families=30, min_len=300, max_len=3000)
+    h = fm.fm_build(R, interval=interval)
+    ix = oracle.Index(R, "sais")
+    reads = synth.sample_reads(9, R, 1500, 1, 255, sub_rate=0.03, indel_rate=0.01,
+                               both_strands=True, random_frac=0.1)
+    codes, offs = fm.to_device_reads(reads)
+    D = fm.fm_dcalc(h, codes, offs, strands=2).cpu().numpy()
+    for r in range(len(reads)):
+        W = reads.read(r)
+        m = W.size
+        s = 2 * int(reads.offs[r])
+        assert np.array_equal(D[s:s + m], ix.dcalc(W)), r
+        assert np.array_equal(D[s + m:s + 2 * m], ix.dcalc(synth.revcomp(W))), r
+    h.close()
+
+
+def _inexact_case(fm, R, reads, z, gaps, interval, kernels=("plain", "persistent")):
+    h = fm.fm_build(R, interval=interval)
+    ix = oracle.Index(R, "sais")
+    want = ix.inexact(reads.codes, reads.offs, z, gaps, strands=2, interval=interval)
+    codes, offs = fm.to_device_reads(reads)
+    for kern in kernels:
+        stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+        counts, offsets, pairs = fm.fm_inexact(h, codes, offs, z, gaps, strands=2, kernel=kern,
+                                               stats=stats)
+        assert np.array_equal(_u32(counts), want["counts"]), kern
+        assert np.array_equal(offsets.cpu().numpy().astype(np.uint64), want["offsets"]), kern
+        assert np.array_equal(_u32(pairs), want["pairs"]), kern
+        st = stats.cpu().numpy()
+        assert st[0] == want["nodes"].sum(), kern
+        assert st[1] == want["blocks"].sum(), kern
+    h.close()
+
+
+@pytest.mark.parametrize("z,gaps", [(0, 0), (1, 0), (2, 0), (1, 1), (2, 1), (2, 2), (3, 1)])
+def test_inexact_matches_oracle(fm, z, gaps):
+    R = synth.repeat_text(1811061273, 400_000, families=40, min_len=300, max_len=4000)
+    n_reads = 400 if z < 3 else 80
+    reads = synth.sample_reads(31 + z, R, n_reads, 20, 150, sub_rate=0.01, indel_rate=0.003,
+                               both_strands=True, random_frac=0.05)
+    _inexact_case(fm, R, reads, z, gaps, 64)
+
+
+@pytest.mark.parametrize("interval", [128, 256])
+def test_inexact_intervals(fm, interval):
+    R = synth.repeat_text(11, 200_000, families=20, min_len=300, max_len=3000)
+    reads = synth.sample_reads(12, R, 300, 30, 100, sub_rate=0.02, both_strands=True)
+    _inexact_case(fm, R, reads, 2, 1, interval)
+
+
+def test_inexact_edge_reads(fm):
+    """Length-0, length-1, length-255 reads, all-A reads and reads over a homopolymer text.
+    (Over a homopolymer the literal recursion of Listing 2 reaches the same state by very many
+    indel placements, so the gap budget is kept small for the long reads.)"""
+    R = _text("homopolymer", 777)
+    short = [np.zeros(0, np.uint8), np.array([0], np.uint8), np.array([3], np.uint8),
+             np.zeros(12, np.uint8), np.array([0, 1], np.uint8), synth.uniform_text(4, 20)]
+    long_ = [np.zeros(40, np.uint8), synth.uniform_text(4, 255), np.zeros(255, np.uint8),
+             np.concatenate([np.zeros(120, np.uint8), [1], np.zeros(100, np.uint8)]).astype(np.uint8)]
+
+    def batch(parts):
+        codes = np.concatenate(parts).astype(np.uint8)
+        offs = np.concatenate([[0], np.cumsum([p.size for p in parts])]).astype(np.uint32)
+        return synth.Reads(codes, offs)
+
+    for z, g in ((0, 0), (2, 0), (2, 1)):
+        _inexact_case(fm, R, batch(short + long_), z, g, 64)
+    _inexact_case(fm, R, batch(short), 3, 3, 64)
+
+
+def test_inexact_truncation_and_fetch(fm):
+    R = synth.repeat_text(21, 100_000, families=10, min_len=300, max_len=2000)
+    reads = synth.sample_reads(22, R, 200, 30, 80, sub_rate=0.02, both_strands=True)
+    h = fm.fm_build(R)
+    codes, offs = fm.to_device_reads(reads)
+    c0, o0, p0 = fm.fm_inexact(h, codes, offs, 2, 1, strands=2)
+    total = int(o0[-1])
+    assert total > 10
+    # a capacity below the total: FM_ETRUNC, then the binding fetches into a larger buffer
+    c1, o1, p1 = fm.fm_inexact(h, codes, offs, 2, 1, strands=2, pair_capacity=3)
+    assert torch.equal(c0, c1) and torch.equal(o0, o1) and torch.equal(p0, p1)
+    h.close()
+
+
+def test_inexact_too_long_read(fm):
+    h = fm.fm_build(_text("uniform", 5000))
+    codes = torch.zeros(300, dtype=torch.uint8, device="cuda")
+    offs = torch.tensor([0, 300], dtype=torch.int32, device="cuda")
+    with pytest.raises(fm.FmError) as ei:
+        fm.fm_inexact(h, codes, offs, 1, 0)
+    assert ei.value.code == fm.FM_EINVAL
+    h.close()
+
+
+def test_save_load_roundtrip(fm):
+    R = synth.repeat_text(8, 50_000, families=5, min_len=300, max_len=1000)
+    h = fm.fm_build(R, interval=128)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ix.fm")
+        fm.fm_save(h, path)
+        h2 = fm.fm_load(path)
+        assert fm.fm_info(h2) == fm.fm_info(h)
+        assert np.array_equal(fm.fm_get_bwt(h2), fm.fm_get_bwt(h))
+        assert np.array_equal(fm.fm_get_bwt(h2, rev=True), fm.fm_get_bwt(h, rev=True))
+        raw = bytearray(open(path, "rb").read())
+        raw[200] ^= 1
+        open(path, "wb").write(bytes(raw))
+        with pytest.raises(fm.FmError) as ei:
+            fm.fm_load(path)
+        assert ei.value.code == fm.FM_EIO
+        h2.close()
+    h.close()
+
+
+def test_invalid_reference(fm):
+    with pytest.raises(fm.FmError) as ei:
+        fm.fm_build("ACGTN")
+    assert ei.value.code == fm.FM_EINVAL
+    h = fm.fm_build("acgtACGT")
+    assert fm.fm_info(h)["n"] == 8
+    h.close()
