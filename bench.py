@@ -1,0 +1,489 @@
+#!/usr/bin/env python
+"""Benchmark of the FM-index search path on GB300 (one JSON line on rank 0).
+
+Main line (the step): one batched inexact search (D lower bound, persistent search kernel,
+canonical interval sets) of 10,000,000 reads of 50-250 bp (1% substitutions, 0.05% single-base
+indels, drawn from both strands) against a 2,000,000,000-base repeat-structured reference,
+z = 2 differences with at most 1 gap, each read searched on both strands.  Metric: reads/s.
+Beside it, in the same line:
+  * the plain per-read kernel on the same batch (bit-exact comparison of the two);
+  * e2e: the same step through the C ABI with the reads in pinned host memory, the
+    host->device copy of the reads and the device->host copy of the interval sets timed;
+  * occ8: the Occ micro-benchmark, 2^28 eight-Occ queries on a 2 Gbp i.i.d. 41% GC index
+    (half in one checkpoint block, half at a geometric gap of mean 1000), against the
+    random-gather roofline;
+  * exact: plain exact search of 10,000 32 bp reads on a 1 Mbp uniform reference;
+  * cpu_baseline: the CPU oracle on a bounded sample of the main workload.
+With --impl reference the CPU oracle itself is timed on a bounded sample per step.
+Launch: python bench.py [--gpus N --steps K --warmup W]; under torchrun one replica per GPU,
+each with its own read batch (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("reads/s at z<=2 (batched vs plain kernel, bit-exact); 8-Occ Gq/s vs gather "
+          "roofline")
+SEED_EXACT, SEED_OCC, SEED_SEARCH = 1811061271, 1811061272, 1811061274
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--ref-n", type=int, default=2_000_000_000)
+    ap.add_argument("--reads", type=int, default=10_000_000)
+    ap.add_argument("--occ-n", type=int, default=2_000_000_000)
+    ap.add_argument("--occ-queries", type=int, default=1 << 28)
+    ap.add_argument("--interval", type=int, default=64)
+    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--skip-occ8", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-reads", type=int, default=200_000)
+    ap.add_argument("--cpu-sample-ref", type=int, default=32_000_000)
+    ap.add_argument("--log", default=None, help="also append the JSON line to this file")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------------------------
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------------------------
+# reference arm / CPU baseline: the oracle as it stands
+# ---------------------------------------------------------------------------------------------
+
+def oracle_sample(args, nreads, seed_off=0):
+    import oracle
+    from paper_1811_06127_gb300 import synth
+    R = synth.repeat_text(SEED_SEARCH, args.cpu_sample_ref)
+    ix = oracle.Index(R, "sais")
+    reads = synth.sample_reads(SEED_SEARCH + 7 + seed_off, R, nreads, 50, 250, sub_rate=0.01,
+                               indel_rate=0.0005, both_strands=True)
+    return ix, reads
+
+
+def cpu_baseline(args):
+    import oracle
+    ix, reads = oracle_sample(args, args.cpu_sample_reads)
+    thr = oracle.default_threads()
+    t0 = time.perf_counter()
+    res = ix.inexact(reads.codes, reads.offs, 2, 1, strands=2, threads=thr)
+    dt = time.perf_counter() - t0
+    return {"value": len(reads) / dt, "unit": "reads/s", "cores": thr, "kind": "oracle",
+            "sample": (f"{len(reads)} reads of the same read model (50-250 bp, 1% subst, 0.05% "
+                       f"indel, both strands, z=2, 1 gap) against a {args.cpu_sample_ref} bp "
+                       "reference from the same repeat generator; the oracle's own index of the "
+                       "2 Gbp reference is not built (its SA-IS takes over ten minutes); index "
+                       "build not timed"),
+            "seconds": dt, "nodes_per_read": float(res["nodes"].sum()) / len(reads)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    import oracle
+    n_step = max(2000, args.cpu_sample_reads // 10)
+    ix, reads = oracle_sample(args, n_step * (args.warmup + args.steps))
+    thr = oracle.default_threads()
+    times = []
+    for s in range(args.warmup + args.steps):
+        sub = reads.subset(np.arange(s * n_step, (s + 1) * n_step))
+        t0 = time.perf_counter()
+        ix.inexact(sub.codes, sub.offs, 2, 1, strands=2, threads=thr)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = n_step * args.steps / total
+    line = {"metric": METRIC, "value": value, "unit": "reads/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8/u32 (integer)",
+            "data": "synthetic",
+            "config": {"workload": "inexact search z=2 (1 gap), 50-250 bp reads, both strands, "
+                                   f"oracle sample on a {args.cpu_sample_ref} bp reference",
+                       "reads_per_step": n_step},
+            "cpu_baseline": {"value": value, "unit": "reads/s", "cores": thr, "kind": "oracle",
+                             "sample": f"{n_step} reads per step against a {args.cpu_sample_ref}"
+                                       " bp reference from the same generator"},
+            "e2e": {"value": value, "unit": "reads/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_1811_06127_gb300 import fmocc, synth
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    fmocc.load_library()
+    dev = torch.device("cuda", local)
+    hbm_peak, peak_kind = peaks()
+    notes = {}
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    l2_flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB L2
+
+    def flush():
+        l2_flush.add_(1)
+
+    # ---- main workload: index and reads -------------------------------------------------
+    t0 = time.time()
+    R = synth.repeat_text(SEED_SEARCH, args.ref_n)
+    notes["ref_gen_s"] = time.time() - t0
+    t0 = time.time()
+    h = fmocc.fm_build(R, interval=args.interval, device=local)
+    torch.cuda.synchronize()
+    notes["build_s"] = time.time() - t0
+    t0 = time.time()
+    reads = synth.sample_reads(SEED_SEARCH + 1000 * rank, R, args.reads, 50, 250, sub_rate=0.01,
+                               indel_rate=0.0005, both_strands=True)
+    notes["reads_gen_s"] = time.time() - t0
+    del R
+    codes_h = torch.from_numpy(reads.codes).pin_memory()
+    offs_h = torch.from_numpy(reads.offs.view(np.int32)).pin_memory()
+    codes = codes_h.to(dev)
+    offs = offs_h.to(dev)
+    nq = 2 * args.reads
+    counts = torch.empty(nq, dtype=torch.int32, device=dev)
+    offsets = torch.empty(nq + 1, dtype=torch.int64, device=dev)
+    stats = torch.zeros(4, dtype=torch.int64, device=dev)
+    prof = fmocc.fm_profile()
+
+    def search(kernel, pairs_buf, st=None):
+        return fmocc.fm_inexact(h, codes, offs, 2, 1, strands=2, kernel=kernel, stats=st,
+                                counts=counts, offsets=offsets, pairs=pairs_buf, profile=prof)
+
+    # size the pairs buffer with one untimed call
+    c0, o0, p0 = search("persistent", None)
+    pairs_cap = int(p0.shape[0]) + 1024
+    pairs = torch.empty((pairs_cap, 2), dtype=torch.int32, device=dev)
+    ref_pairs = p0.clone()
+    ref_offsets = o0.clone()
+
+    # warm-up, then K timed steps (events per step on the launching stream, L2 flushed between)
+    for _ in range(args.warmup):
+        search("persistent", pairs)
+    barrier()
+    stats.zero_()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clk = Clocks(local)
+    clk.start()
+    search_ms, launches = [], 0
+    for s in range(args.steps):
+        flush()
+        ev[s][0].record()
+        _, o1, p1 = search("persistent", pairs, stats)
+        ev[s][1].record()
+        search_ms.append(prof.ms_search)
+        launches += prof.launches
+    barrier()
+    clocks = clk.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = max_over_ranks(sum(step_ms) / 1000.0)
+    st = stats.cpu().numpy()
+    nodes_per_step = st[0] / args.steps
+    blocks_per_step = st[1] / args.steps
+    bbytes = {64: 32, 128: 64, 256: 96}[args.interval]
+    value = args.reads * args.steps * world / total_s
+    # dominant kernel: the persistent search kernel, its own event-timed duration per launch
+    k_ms = float(np.mean(search_ms))
+    alg_bytes = blocks_per_step * bbytes
+    achieved = alg_bytes / (k_ms / 1000.0) / 1e9
+    same = bool(torch.equal(p1, ref_pairs) and torch.equal(o1, ref_offsets))
+
+    # ---- plain per-read kernel on the same batch ----------------------------------------
+    plain = None
+    if not args.skip_plain:
+        search("plain", pairs)
+        barrier()
+        pms = []
+        for _ in range(args.plain_steps):
+            flush()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            _, op, pp = search("plain", pairs)
+            b.record()
+            torch.cuda.synchronize()
+            pms.append(a.elapsed_time(b))
+        same_plain = bool(torch.equal(pp, ref_pairs) and torch.equal(op, ref_offsets))
+        ptot = max_over_ranks(sum(pms) / 1000.0)
+        plain = {"value": args.reads * len(pms) * world / ptot, "unit": "reads/s",
+                 "ms_per_step": 1000 * ptot / len(pms), "steps": len(pms),
+                 "kernel_ms": prof.ms_search, "bit_exact_vs_persistent": same_plain}
+
+    # ---- e2e through the C ABI with host buffers ----------------------------------------
+    e2e = None
+    if not args.skip_e2e:
+        counts_h = torch.empty(nq, dtype=torch.int32).pin_memory()
+        offsets_h = torch.empty(nq + 1, dtype=torch.int64).pin_memory()
+        pairs_h = torch.empty((pairs_cap, 2), dtype=torch.int32).pin_memory()
+        d2h = 0
+        barrier()
+        t0 = time.perf_counter()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record()
+        for _ in range(args.steps):
+            codes.copy_(codes_h, non_blocking=True)
+            offs.copy_(offs_h, non_blocking=True)
+            c2, o2, p2 = search("persistent", pairs)
+            counts_h.copy_(c2, non_blocking=True)
+            offsets_h.copy_(o2, non_blocking=True)
+            npairs = p2.shape[0]
+            pairs_h[:npairs].copy_(p2, non_blocking=True)
+            d2h = counts_h.numel() * 4 + offsets_h.numel() * 8 + npairs * 8
+        eb.record()
+        torch.cuda.synchronize()
+        e_s = max_over_ranks(ea.elapsed_time(eb) / 1000.0)
+        e2e = {"value": args.reads * args.steps * world / e_s, "unit": "reads/s",
+               "h2d_bytes_per_step": codes_h.numel() + offs_h.numel() * 4,
+               "d2h_bytes_per_step": int(d2h), "wall_s": time.perf_counter() - t0}
+    h.close()
+    del codes, offs, pairs
+
+    # ---- Occ micro-benchmark -----------------------------------------------------------
+    occ8 = None
+    if not args.skip_occ8:
+        occ8 = bench_occ8(args, torch, fmocc, synth, dev, hbm_peak, peak_kind, flush, barrier,
+                          max_over_ranks, world)
+    exact = bench_exact(args, torch, fmocc, synth, dev, flush, barrier)
+
+    cpu = None
+    if not args.skip_cpu and rank == 0 and world == 1:
+        cpu = cpu_baseline(args)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "reads/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8/u32 (integer)",
+        "data": "synthetic (seeded genome-shaped reference and reads; no dataset)",
+        "config": {"workload": ("batched uneven inexact search: 2 Gbp repeat-structured reference "
+                                "(41% GC, 20% copies of 500 families), 10M reads 50-250 bp, 1% "
+                                "subst + 0.05% indel, z=2 with <=1 gap, both strands, persistent "
+                                "kernel"),
+                   "reference_bp": args.ref_n, "reads_per_step": args.reads,
+                   "queries_per_step": nq, "interval": args.interval,
+                   "parallelism": f"replicas x{world} (read sharding)",
+                   "l2": "flushed between timed steps (256 MB write); index 2x1 GB > L2"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None,
+                     "kernel": "k_inexact_persistent", "kernel_ms": k_ms,
+                     "algorithmic_bytes": alg_bytes, "peak_kind": peak_kind,
+                     "per_unit": f"{bbytes} B per checkpoint block read, "
+                                 f"{blocks_per_step / max(nodes_per_step, 1):.3f} blocks per node, "
+                                 f"{nodes_per_step / nq:.1f} nodes per query"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "search": {"nodes_per_step": nodes_per_step, "blocks_per_step": blocks_per_step,
+                   "intervals_per_step": int(ref_offsets[-1].item()),
+                   "bit_exact_repeat": same, "step_ms": step_ms,
+                   "profile_last": prof.as_dict()},
+        "plain": plain,
+        "e2e": e2e,
+        "occ8": occ8,
+        "exact": exact,
+        "cpu_baseline": cpu,
+        "setup": notes,
+    }
+    if rank == 0:
+        s = json.dumps(line)
+        print(s, flush=True)
+        if args.log:
+            with open(args.log, "a") as f:
+                f.write(s + "\n")
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def bench_occ8(args, torch, fmocc, synth, dev, hbm_peak, peak_kind, flush, barrier,
+               max_over_ranks, world):
+    t0 = time.time()
+    R = synth.gc_text(SEED_OCC, args.occ_n, 0.41)
+    h = fmocc.fm_build(R, interval=args.interval, device=dev.index, forward_only=True)
+    del R
+    n = args.occ_n
+    k, l = synth.occ_queries_mixed(SEED_OCC, n, args.occ_queries, args.interval)
+    I = args.interval
+    same = (k // I) == ((l.astype(np.int64) + 1) // I)
+    blocks = float(np.where(same, 1, 2).sum())
+    kd = torch.from_numpy(k.view(np.int32)).to(dev)
+    ld = torch.from_numpy(l.view(np.int32)).to(dev)
+    del k, l
+    out = torch.empty((args.occ_queries, 8), dtype=torch.int32, device=dev)
+    setup_s = time.time() - t0
+    for _ in range(3):
+        fmocc.fm_occ8(h, kd, ld, out)
+    barrier()
+    ms = []
+    for _ in range(max(args.steps, 3)):
+        flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fmocc.fm_occ8(h, kd, ld, out)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = max_over_ranks(float(np.mean(ms)) / 1000.0)
+    bb = {64: 32, 128: 64, 256: 96}[I]
+    gather = blocks * bb
+    io = args.occ_queries * 40.0
+    h.close()
+    return {"value": args.occ_queries * world / t / 1e9, "unit": "G 8-Occ/s",
+            "config": {"reference_bp": n, "gc": 0.41, "queries": args.occ_queries,
+                       "interval": I, "block_bytes": bb, "same_block_frac": float(same.mean())},
+            "ms_per_launch": t * 1000,
+            "roofline": {"bound": "hbm", "achieved": gather / t / 1e9, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": gather / t / 1e9 / hbm_peak,
+                         "peak_kind": peak_kind,
+                         "gather_roofline_gq_s": hbm_peak * 1e9 / (gather / args.occ_queries) / 1e9,
+                         "total_traffic_frac": (gather + io) / t / 1e9 / hbm_peak,
+                         "blocks_per_query": blocks / args.occ_queries},
+            "setup_s": setup_s}
+
+
+def bench_exact(args, torch, fmocc, synth, dev, flush, barrier):
+    R = synth.uniform_text(SEED_EXACT, 1_000_000)
+    h = fmocc.fm_build(R, interval=args.interval, device=dev.index)
+    reads = synth.exact_reads(SEED_EXACT, R, 10_000, 32)
+    codes, offs = fmocc.to_device_reads(reads, dev)
+    k1, l1 = synth.occ_queries_uniform(SEED_EXACT, R.size, 1_000_000)
+    kd = torch.from_numpy(k1.view(np.int32)).to(dev)
+    ld = torch.from_numpy(l1.view(np.int32)).to(dev)
+    out = torch.empty((kd.numel(), 8), dtype=torch.int32, device=dev)
+    for _ in range(3):
+        fmocc.fm_exact(h, codes, offs)
+        fmocc.fm_occ8(h, kd, ld, out)
+    barrier()
+    ms_e, ms_o = [], []
+    for _ in range(max(args.steps, 3)):
+        for fn, acc in ((lambda: fmocc.fm_exact(h, codes, offs), ms_e),
+                        (lambda: fmocc.fm_occ8(h, kd, ld, out), ms_o)):
+            flush()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            acc.append(a.elapsed_time(b))
+    h.close()
+    te, to = float(np.mean(ms_e)), float(np.mean(ms_o))
+    return {"config": "1 Mbp uniform reference, 10,000 reads of 32 bp (90% copied), I=64; "
+                      "1,000,000 fm_occ8 queries",
+            "reads_per_s": 10_000 / (te / 1000), "ms_per_call": te,
+            "occ8_gq_s": 1e6 / (to / 1000) / 1e9, "occ8_ms": to,
+            "note": "index L2-resident (0.5 MB): latency-bound, no roofline claim"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -127,6 +127,17 @@ int fm_occ8(fm_index *h, const uint32_t *k, const uint32_t *l, uint32_t *out8, u
 int fm_exact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
              uint32_t *k_out, uint32_t *l_out, void *stream);
 
+/* Per-call profile of fm_inexact (optional): phase times from CUDA events recorded on the
+ * call's stream around the library's own launches, and the number of kernels launched. */
+typedef struct fm_profile {
+    float ms_dcalc;    /* D lower bound (one launch) */
+    float ms_search;   /* the search kernel (last pass when scratch had to be regrown) */
+    float ms_canon;    /* grouping, sorting, deduplication and compaction of the intervals */
+    float ms_total;    /* whole call, first launch to last */
+    uint32_t launches; /* kernels launched by the call */
+    uint32_t passes;   /* search passes (1 unless scratch was regrown) */
+} fm_profile;
+
 /* Inexact search options. */
 typedef struct fm_search_params {
     uint32_t z;        /* differences allowed, 0..7 */
@@ -139,6 +150,7 @@ typedef struct fm_search_params {
                           [1] checkpoint blocks read by those expansions (1 when k and l+1
                               share a block, else 2), [2] intervals reported before
                               deduplication, [3] reserved */
+    fm_profile *profile; /* optional host pointer, filled by a successful call */
 } fm_search_params;
 
 #define FM_KERNEL_AUTO 0u       /* the persistent kernel */

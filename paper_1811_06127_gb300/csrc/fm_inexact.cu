@@ -24,6 +24,8 @@
 // Leaves are appended to a raw result buffer (warp-aggregated atomics).  The raw results are
 // then grouped by query, sorted and deduplicated (canonical sets, Listing 2's set union), and
 // compacted into the caller's counts/offsets/pairs.
+#include <string.h>
+
 #include "fm_internal.cuh"
 
 namespace fm {
@@ -682,6 +684,26 @@ static int occupancy_blocks(int block, size_t smem) {
     return nb;
 }
 
+// fills the profile from the phase events: ev[0] start, ev[1] before the (last) search pass,
+// ev[2] after it, ev[3] end of the canonical sets
+static int finish_profile(fm_index *h, fm_profile *prof, cudaEvent_t *ev, uint32_t launches,
+                          cudaStream_t st) {
+    if (!prof) return FM_OK;
+    FM_CUDA_TRY(h, cudaEventRecord(ev[3], st));
+    FM_CUDA_TRY(h, cudaEventSynchronize(ev[3]));
+    float a = 0, b = 0, c = 0, d = 0;
+    FM_CUDA_TRY(h, cudaEventElapsedTime(&a, ev[0], ev[4] ? ev[4] : ev[1]));
+    FM_CUDA_TRY(h, cudaEventElapsedTime(&b, ev[1], ev[2]));
+    FM_CUDA_TRY(h, cudaEventElapsedTime(&c, ev[2], ev[3]));
+    FM_CUDA_TRY(h, cudaEventElapsedTime(&d, ev[0], ev[3]));
+    prof->ms_dcalc = a;
+    prof->ms_search = b;
+    prof->ms_canon = c;
+    prof->ms_total = d;
+    prof->launches = launches;
+    return FM_OK;
+}
+
 int fetch_inexact(fm_index *h, uint32_t *pairs, uint64_t pair_capacity, cudaStream_t st) {
     if (!h->last_valid) return set_error(h, FM_EINVAL, "no search results to fetch");
     if (h->last_total > pair_capacity)
@@ -722,10 +744,29 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
         return FM_OK;
     }
 
+    // phase events on the call's stream (profile requested)
+    fm_profile *prof = sp->profile;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    struct EvGuard {
+        cudaEvent_t *e;
+        ~EvGuard() {
+            for (int i = 0; i < 5; ++i)
+                if (e[i]) cudaEventDestroy(e[i]);
+        }
+    } evg{ev};
+    if (prof) {
+        memset(prof, 0, sizeof(*prof));
+        for (int i = 0; i < 5; ++i) FM_CUDA_TRY(h, cudaEventCreate(&ev[i]));
+        FM_CUDA_TRY(h, cudaEventRecord(ev[0], st));
+    }
+    uint32_t launches = 0;
+
     // D lower bound and per-query metadata
     if ((rc = ensure_scratch(h, h->s_qmeta, (size_t)nq * sizeof(uint4)))) return rc;
     uint4 *qmeta = (uint4 *)h->s_qmeta.ptr;
     if ((rc = launch_dcalc(h, reads, offs, n_reads, strands, qmeta, nullptr, st))) return rc;
+    ++launches;
+    if (prof) FM_CUDA_TRY(h, cudaEventRecord(ev[4], st));   // end of the D pass
 
     const uint32_t I = h->interval;
     const Tuning &tu = h->tune;
@@ -781,12 +822,18 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
         c.raw_cap = raw_cap;
         c.stats = d_stats;
         c.err = h->d_err + kErrSearch;
+        if (prof) FM_CUDA_TRY(h, cudaEventRecord(ev[1], st));
         switch (I) {
             case 64: rc = launch_search<64>(h, c, sp->kernel, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, (uint4 *)h->s_plain.ptr, cap, T, st); break;
             case 128: rc = launch_search<128>(h, c, sp->kernel, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, (uint4 *)h->s_plain.ptr, cap, T, st); break;
             default: rc = launch_search<256>(h, c, sp->kernel, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, (uint4 *)h->s_plain.ptr, cap, T, st); break;
         }
         if (rc) return rc;
+        ++launches;
+        if (prof) {
+            FM_CUDA_TRY(h, cudaEventRecord(ev[2], st));
+            prof->passes += 1;
+        }
         unsigned long long rawn = 0;
         uint32_t errw = 0;
         FM_CUDA_TRY(h, cudaMemcpyAsync(&rawn, d_raw_count, 8, cudaMemcpyDeviceToHost, st));
@@ -829,6 +876,7 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
             if (R) k_scatter<<<grid_cap(h, R, 256), 256, 0, st>>>(raw, R, start, cursor, grouped);
             k_sort_small<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, st>>>(nq, cnt, start, grouped, ucnt, large, d_nlarge);
             FM_CUDA_TRY(h, cudaGetLastError());
+            launches += (R ? 2u : 0u) + 3u + 1u;
             uint32_t nlarge = 0;
             FM_CUDA_TRY(h, cudaMemcpyAsync(&nlarge, d_nlarge, 4, cudaMemcpyDeviceToHost, st));
             FM_CUDA_TRY(h, cudaStreamSynchronize(st));
@@ -838,11 +886,13 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
                 unsigned lg = nlarge < (uint32_t)h->sms * 4 ? nlarge : (uint32_t)h->sms * 4;
                 k_sort_large<<<lg, 512, lsm, st>>>(large, d_nlarge, cnt, start, grouped, tmp, ucnt);
                 FM_CUDA_TRY(h, cudaGetLastError());
+                ++launches;
             }
             if ((rc = scan_u32(h, ucnt, nq, uoff, tiles, st))) return rc;
             FM_CUDA_TRY(h, cudaMemcpyAsync(offsets, uoff, ((size_t)nq + 1) * 8, cudaMemcpyDeviceToDevice, st));
             k_copy_counts<<<grid_cap(h, nq, 256), 256, 0, st>>>(nq, ucnt, counts);
             FM_CUDA_TRY(h, cudaGetLastError());
+            launches += 3u + 1u;
             uint64_t need = 0;
             FM_CUDA_TRY(h, cudaMemcpyAsync(&need, uoff + nq, 8, cudaMemcpyDeviceToHost, st));
             FM_CUDA_TRY(h, cudaStreamSynchronize(st));
@@ -857,16 +907,19 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
             if (sp->stats) {
                 k_add_stats<<<1, 32, 0, st>>>(d_stats, d_raw_count, (unsigned long long *)sp->stats);
                 FM_CUDA_TRY(h, cudaGetLastError());
+                ++launches;
             }
             if (need > pair_capacity) {
-                FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+                if ((rc = finish_profile(h, prof, ev, launches, st))) return rc;
                 return set_error(h, FM_ETRUNC, "pair capacity " + std::to_string(pair_capacity) +
                                                    " below the " + std::to_string(need) + " intervals found");
             }
             if (need) {
                 k_compact<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, st>>>(nq, ucnt, start, uoff, grouped, pairs);
                 FM_CUDA_TRY(h, cudaGetLastError());
+                ++launches;
             }
+            if ((rc = finish_profile(h, prof, ev, launches, st))) return rc;
             uint32_t derr = 0;
             FM_CUDA_TRY(h, cudaMemcpyAsync(&derr, h->d_err + kErrDcalc, 4, cudaMemcpyDeviceToHost, st));
             FM_CUDA_TRY(h, cudaStreamSynchronize(st));

@@ -41,9 +41,18 @@ class fm_info_t(C.Structure):
                 ("bytes_device", C.c_uint64), ("has_reverse", C.c_int32), ("device", C.c_int32)]
 
 
+class fm_profile(C.Structure):
+    _fields_ = [("ms_dcalc", C.c_float), ("ms_search", C.c_float), ("ms_canon", C.c_float),
+                ("ms_total", C.c_float), ("launches", C.c_uint32), ("passes", C.c_uint32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class fm_search_params(C.Structure):
     _fields_ = [("z", C.c_uint32), ("max_gaps", C.c_uint32), ("strands", C.c_uint32),
-                ("kernel", C.c_uint32), ("stats", C.c_void_p)]
+                ("kernel", C.c_uint32), ("stats", C.c_void_p),
+                ("profile", C.POINTER(fm_profile))]
 
 
 class fm_tuning(C.Structure):
@@ -265,7 +274,7 @@ def fm_dcalc(h: Index, reads: torch.Tensor, offs: torch.Tensor, strands: int = 1
 def fm_inexact(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int, max_gaps: int = 0,
                strands: int = 1, kernel="auto", stats: torch.Tensor | None = None,
                pair_capacity: int | None = None, counts=None, offsets=None, pairs=None,
-               stream=None):
+               profile: fm_profile | None = None, stream=None):
     """Listing 2 interval sets.  Returns (counts int32[nq], offsets int64[nq+1],
     pairs int32[total, 2]); on FM_ETRUNC the pairs buffer is regrown and fetched again."""
     lib = load_library()
@@ -282,7 +291,8 @@ def fm_inexact(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int, max_ga
         pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=dev)
     cap = pairs.shape[0]
     sp = fm_search_params(z, max_gaps, strands, kern,
-                          _dptr(stats, _U64, "stats") if stats is not None else None)
+                          _dptr(stats, _U64, "stats") if stats is not None else None,
+                          C.pointer(profile) if profile is not None else None)
     need = C.c_uint64(0)
     rc = lib.fm_inexact(h.ptr, _dptr(reads, _U8, "reads"), _dptr(offs, _U32, "offs"), nr,
                         C.byref(sp), _dptr(counts, _U32, "counts"),

@@ -28,6 +28,9 @@ these genome-shaped stand-ins take their shapes from the configurations below):
 """
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
@@ -37,6 +40,19 @@ _MIX2 = np.uint64(0x94D049BB133111EB)
 
 # chunk of hashes evaluated at once (bounds host memory for 2 Gbp texts)
 _CHUNK = 1 << 24
+
+
+def _pmap(fn, starts):
+    """Run fn(start) for every chunk start on a thread pool (numpy releases the GIL); every
+    draw is keyed by absolute position, so the result does not depend on the schedule."""
+    starts = list(starts)
+    if len(starts) <= 1:
+        for st in starts:
+            fn(st)
+        return
+    workers = min(len(starts), os.cpu_count() or 1, 32)
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        list(ex.map(fn, starts))
 
 
 def splitmix64(seed: int, idx) -> np.ndarray:
@@ -56,9 +72,12 @@ def substream(seed: int, tag: int) -> int:
 
 def hashes(seed: int, count: int, start: int = 0) -> np.ndarray:
     out = np.empty(count, dtype=np.uint64)
-    for s in range(0, count, _CHUNK):
+
+    def one(s):
         e = min(count, s + _CHUNK)
         out[s:e] = splitmix64(seed, np.arange(start + s, start + e, dtype=np.uint64))
+
+    _pmap(one, range(0, count, _CHUNK))
     return out
 
 
@@ -86,10 +105,13 @@ def uniform_text(seed: int, n: int) -> np.ndarray:
     nh = (n + 31) // 32
     out = np.empty(nh * 32, dtype=np.uint8)
     shifts = np.array([0, 2, 4, 6], dtype=np.uint8)
-    for s in range(0, nh, _CHUNK):
+
+    def one(s):
         e = min(nh, s + _CHUNK)
         b = splitmix64(seed, np.arange(s, e, dtype=np.uint64)).view(np.uint8)
         out[s * 32:e * 32] = ((b[:, None] >> shifts) & 3).reshape(-1)
+
+    _pmap(one, range(0, nh, _CHUNK))
     return out[:n].copy()
 
 
@@ -107,13 +129,16 @@ def gc_text(seed: int, n: int, gc: float = 0.41) -> np.ndarray:
     t1, t2, t3 = _gc_thresholds(gc)
     nh = (n + 3) // 4
     out = np.empty(nh * 4, dtype=np.uint8)
-    for s in range(0, nh, _CHUNK):
+
+    def one(s):
         e = min(nh, s + _CHUNK)
         u = splitmix64(seed, np.arange(s, e, dtype=np.uint64)).view(np.uint16)
         c = (u >= t1).astype(np.uint8)
         c += (u >= t2)
         c += (u >= t3)
         out[s * 4:e * 4] = c
+
+    _pmap(one, range(0, nh, _CHUNK))
     return out[:n].copy()
 
 
@@ -219,63 +244,76 @@ class Reads:
 
 def sample_reads(seed: int, text: np.ndarray, n_reads: int, min_len: int, max_len: int,
                  sub_rate: float = 0.0, indel_rate: float = 0.0, both_strands: bool = False,
-                 random_frac: float = 0.0, chunk: int = 1 << 20) -> Reads:
+                 random_frac: float = 0.0, chunk: int = 1 << 17) -> Reads:
     """Reads sampled from ``text`` with sequencing-like errors.
 
     Read r: length uniform in [min_len, max_len]; with probability ``random_frac`` a uniform
     random string, otherwise copied from a uniform start position.  Along the read each output
     base is, with probability indel_rate/2 each, an inserted random base (consumes no
     reference) or preceded by one deleted reference base; every copied base is substituted
-    with probability ``sub_rate``.  With ``both_strands`` half of the copied reads (chosen by
-    hash) are reverse-complemented.
+    with probability ``sub_rate`` by one of the three other bases.  With ``both_strands`` half
+    of the copied reads (chosen by hash) are reverse-complemented.
+
+    Per output position one hash h supplies every draw: bits 0..31 the substitution test,
+    bits 32..47 the substituted base, bits 48..49 a random base, bits 50..63 the indel test.
     """
     n = int(text.size)
     lens = randint(substream(seed, 11), n_reads, min_len, max_len)
     offs = np.zeros(n_reads + 1, dtype=np.int64)
     np.cumsum(lens, out=offs[1:])
-    total = int(offs[-1])
     is_rand = uniform01(substream(seed, 12), n_reads) < random_frac
     flip = (uniform01(substream(seed, 13), n_reads) < 0.5) & both_strands
     # reference span needed: len plus room for a few deletions (clipped at the text end)
     maxspan = np.minimum(lens + (16 if indel_rate > 0 else 0), n)
     starts = randint(substream(seed, 14), n_reads, 0, n - maxspan)
+    total = int(offs[-1])
     codes = np.empty(total, dtype=np.uint8)
-    s_ev, s_sub, s_rnd = substream(seed, 15), substream(seed, 16), substream(seed, 17)
-    for r0 in range(0, n_reads, chunk):
+    s_pos = substream(seed, 15)
+    sub_thr = np.uint64(int(sub_rate * 2.0 ** 32))
+    ins_thr = np.uint64(int(indel_rate / 2 * 2.0 ** 14))
+    del_thr = np.uint64(int(indel_rate * 2.0 ** 14))
+    def one(r0):
         r1 = min(n_reads, r0 + chunk)
         a, b = int(offs[r0]), int(offs[r1])
         m = b - a
-        rid = np.repeat(np.arange(r0, r1), lens[r0:r1])
-        tpos = np.arange(a, b, dtype=np.int64) - offs[rid]          # position within read
-        if indel_rate > 0:
-            u = (hashes(s_ev, m, a) >> np.uint64(11)).astype(np.float64) * (1.0 / 2 ** 53)
-            ins = u < indel_rate / 2
-            dele = (u >= indel_rate / 2) & (u < indel_rate)
-        else:
-            ins = np.zeros(m, dtype=bool)
-            dele = np.zeros(m, dtype=bool)
-        # reference offset consumed: t - (#ins up to t) + (#del up to t)
-        step = dele.astype(np.int64) - ins.astype(np.int64)
-        cs = np.cumsum(step)
+        L = lens[r0:r1]
+        rid = np.repeat(np.arange(r0, r1), L)
         seg0 = offs[r0:r1] - a
-        base = np.repeat(cs[seg0] - step[seg0], lens[r0:r1])
-        refoff = tpos + (cs - base)
+        tpos = np.arange(m, dtype=np.int64) - np.repeat(seg0, L)    # position within read
+        h = splitmix64(s_pos, np.arange(a, b, dtype=np.uint64))
+        if indel_rate > 0:
+            ev = h >> np.uint64(50)
+            ins = ev < ins_thr
+            dele = (ev >= ins_thr) & (ev < del_thr)
+            # reference offset consumed: t - (#ins up to t) + (#del up to t)
+            step = dele.astype(np.int64) - ins.astype(np.int64)
+            cs = np.cumsum(step)
+            base = np.repeat(cs[seg0] - step[seg0], L)
+            refoff = tpos + (cs - base)
+        else:
+            ins = None
+            refoff = tpos
         src = starts[rid] + refoff
         np.clip(src, 0, n - 1, out=src)
         seq = text[src]
-        rnd = (hashes(s_rnd, m, a) & np.uint64(3)).astype(np.uint8)
-        seq = np.where(ins, rnd, seq)
-        seq = _substitute(substream(s_sub, r0), seq, sub_rate)
-        rr = is_rand[rid]
+        rnd = ((h >> np.uint64(48)) & np.uint64(3)).astype(np.uint8)
+        if ins is not None:
+            seq[ins] = rnd[ins]
+        if sub_rate > 0:
+            hit = (h & np.uint64(0xFFFFFFFF)) < sub_thr
+            shift = ((((h >> np.uint64(32)) & np.uint64(0xFFFF)) * np.uint64(3)) >> np.uint64(16)
+                     ).astype(np.uint8) + 1
+            seq[hit] = (seq[hit] + shift[hit]) & 3
+        rr = np.repeat(is_rand[r0:r1], L)
         seq[rr] = rnd[rr]
         # reverse-complement flipped reads inside their segments
-        fl = flip[rid] & ~rr
+        fl = np.repeat(flip[r0:r1] & ~is_rand[r0:r1], L)
         if fl.any():
-            idx = np.arange(m, dtype=np.int64)
-            rev = seg0[rid - r0] + (lens[rid] - 1 - tpos)
-            idx = np.where(fl, rev, idx)
-            seq = np.where(fl, 3 - seq[idx], seq).astype(np.uint8)
+            rev = np.repeat(seg0 + L - 1, L) - tpos
+            seq[fl] = 3 - seq[rev[fl]]
         codes[a:b] = seq
+
+    _pmap(one, range(0, n_reads, chunk))
     return Reads(codes, offs.astype(np.uint32))
 
 
@@ -298,50 +336,59 @@ def occ_queries_uniform(seed: int, n: int, count: int):
 
 
 def occ_queries_mixed(seed: int, n: int, count: int, interval: int, same_frac: float = 0.5,
-                      gap_mean: float = 1000.0, chunk: int = 1 << 24):
+                      gap_mean: float = 1000.0, chunk: int = 1 << 22):
     """Occ micro-benchmark queries.
 
     With probability ``same_frac`` the pair lies in one checkpoint block: block j uniform,
     then two distinct rank positions p1 < p2 uniform in that block (clipped to [0, n+1]),
     k = p1, l = p2 - 1, so k/I == (l+1)/I.  Otherwise k is uniform in [0, n] and
     l = k + g with g geometric (mean ``gap_mean``, support >= 1), redrawn while l > n.
+    Query q draws from two hashes, 2q and 2q+1 of the seed.
     """
     I = interval
-    nblk_full = (n + 1) // I          # blocks with at least two rank positions inside [0,n+1]
+    nblk = max((n + 1) // I, 1)       # blocks with at least two rank positions in [0, n+1]
     k_out = np.empty(count, dtype=np.uint32)
     l_out = np.empty(count, dtype=np.uint32)
-    p = 1.0 / gap_mean
-    lq = np.log1p(-p)
-    for c0 in range(0, count, chunk):
+    lq = np.log1p(-1.0 / gap_mean)
+    sthr = np.uint64(int(same_frac * 2.0 ** 16))
+    M32 = np.uint64(0xFFFFFFFF)
+
+    def one(c0):
         c1 = min(count, c0 + chunk)
         m = c1 - c0
-        sd = substream(seed, 1000 + c0 // chunk)
-        same = uniform01(substream(sd, 1), m) < same_frac
-        j = randint(substream(sd, 2), m, 0, max(nblk_full - 1, 0))
+        h = splitmix64(seed, np.arange(2 * c0, 2 * c1, dtype=np.uint64))
+        h1, h2 = h[0::2], h[1::2]
+        same = (h1 >> np.uint64(48)) < sthr
+        # same block: j from the low 32 bits of h1, the two positions from h2
+        j = (((h1 & M32) * np.uint64(nblk)) >> np.uint64(32)).astype(np.int64)
         lo = j * I
-        hi = np.minimum(lo + I - 1, n + 1)                           # inclusive last position
-        a = randint(substream(sd, 3), m, lo, hi - 1)
-        b = randint(substream(sd, 4), m, 0, np.maximum(hi - a - 1, 0))
-        p1, p2 = a, a + 1 + b
-        ks = p1
-        ls = p2 - 1
-        k = randint(substream(sd, 5), m, 0, n)
-        u = uniform01(substream(sd, 6), m)
-        g = 1 + np.floor(np.log1p(-u) / lq).astype(np.int64)
-        l = k + g
-        tries = 7
-        bad = l > n
-        while bad.any():
-            u2 = uniform01(substream(sd, tries), m)
-            g2 = 1 + np.floor(np.log1p(-u2) / lq).astype(np.int64)
-            l = np.where(bad, k + g2, l)
-            bad = l > n
+        hi = np.minimum(lo + I - 1, n + 1)                          # inclusive last position
+        span_a = (hi - lo).astype(np.uint64)                        # a in [lo, hi-1]
+        a = lo + (((h2 & M32) * span_a) >> np.uint64(32)).astype(np.int64)
+        span_b = np.maximum(hi - a, 1).astype(np.uint64)            # b in [0, hi-a-1]
+        b = (((h2 >> np.uint64(32)) * span_b) >> np.uint64(32)).astype(np.int64)
+        ks = a
+        ls = a + b                                                  # p2 - 1 with p2 = a + 1 + b
+        # geometric gap: k from h1's bits 16..47, u from h2's top 53 bits
+        k = ((((h1 >> np.uint64(16)) & M32) * np.uint64(n + 1)) >> np.uint64(32)).astype(np.int64)
+        u = (h2 >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+        l = k + 1 + np.floor(np.log1p(-u) / lq).astype(np.int64)
+        bad = np.flatnonzero(~same & (l > n))
+        tries = 0
+        while bad.size:
+            hb = splitmix64(substream(seed, 1_000_003 + tries),
+                            np.arange(c0, c0 + bad.size, dtype=np.uint64))
+            ub = (hb >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+            l[bad] = k[bad] + 1 + np.floor(np.log1p(-ub) / lq).astype(np.int64)
+            bad = bad[l[bad] > n]
             tries += 1
             if tries > 200:
-                l = np.where(bad, n, l)
+                l[bad] = n
                 break
         k_out[c0:c1] = np.where(same, ks, k)
         l_out[c0:c1] = np.where(same, ls, l)
+
+    _pmap(one, range(0, count, chunk))
     return k_out, l_out
 
 
