@@ -192,6 +192,29 @@ int fm_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t
  * Errors: FM_EINVAL (no earlier search), FM_ETRUNC (capacity below the count found). */
 int fm_inexact_fetch(fm_index *h, uint32_t *pairs, uint64_t pair_capacity, void *stream);
 
+/* fm_inexact without any device allocation.  The paper has no counterpart: this entry point
+ * exists for callers that cannot let a library call cudaMalloc, such as a serving process whose
+ * memory manager has reserved the device's memory up front (a library allocation would fail or
+ * fragment its pool), or a latency-critical loop that must not pay for cudaMalloc/cudaFree and
+ * the device synchronisation cudaFree implies.  fm_inexact grows its search scratch on demand;
+ * this variant takes all of it from one fixed 64 MiB array in the library's device memory,
+ * which every GPU that loads the library holds until the process exits.  It runs the
+ * depth-first search kernel on a fixed 1536 threads (sp->kernel and sp->profile are ignored),
+ * so it is slower than fm_inexact; its results are the same.
+ * Arguments, results and errors are those of fm_inexact, with these limits:
+ *   - at most 32,768 queries (n_reads * strands) per call, else FM_EINVAL;
+ *   - at most 262,144 intervals before deduplication, else FM_ENOMEM (nothing is grown: split
+ *     the batch and call again).
+ * The index handle itself must already exist (fm_build/fm_load allocate).  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress, once per device, with
+ * that device current); make that first call before any stream capture.  Every call shares the
+ * one array and leaves its contents behind; calls that overlap on the GPU, from any thread,
+ * stream or handle, race on it and must not be issued. */
+int fm_inexact_noalloc(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
+                       const fm_search_params *sp, uint32_t *counts, uint64_t *offsets,
+                       uint32_t *pairs, uint64_t pair_capacity, uint64_t *pairs_needed,
+                       void *stream);
+
 /* Tuning knobs of the search kernels (the autotuner writes them).  Zero fields keep the
  * current value.  Errors: FM_EINVAL for out-of-range values. */
 typedef struct fm_tuning {

@@ -932,3 +932,231 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
 }
 
 }  // namespace fm
+
+// ============================================================================================
+// Allocation-free inexact search.
+//
+// fm_inexact grows its scratch (query metadata, raw intervals, frontier spill, grouping
+// buffers) with cudaMalloc on demand.  fm_inexact_noalloc runs the same search with all of
+// that scratch carved out of one fixed, file-scope device array, so a call allocates nothing.
+// The array is 64 MiB; every device that loads this library holds it until the process exits.
+// It runs the depth-first kernel (k_inexact_plain), whose per-thread stack has a proven bound
+// (at most 8 siblings wait per level over at most read length + z levels), on a fixed number
+// of threads, so the search itself cannot run out of space.  Limits that follow from the
+// array's size: at most kNoAllocMaxQueries queries (reads x strands) per call and at most
+// kNoAllocMaxRaw intervals before deduplication; a call beyond them returns an error instead
+// of growing anything.  All calls share the one array: calls that overlap on the GPU (from any
+// thread, stream or index handle) race on it and must not be issued.
+// ============================================================================================
+#include <mutex>
+
+namespace fm {
+namespace {
+
+constexpr uint32_t kNoAllocMaxQueries = 32768;
+constexpr uint64_t kNoAllocMaxRaw = 8ull * kNoAllocMaxQueries;
+constexpr uint32_t kNoAllocThreads = 1536;                           // multiple of 32
+constexpr uint32_t kNoAllocStackCap = 8u * ((uint32_t)kMaxReadLen + (uint32_t)kMaxZ) + 16u;
+
+constexpr size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
+// byte offsets inside the array
+constexpr size_t kNaMisc = 0;                                            // counters, 256 B
+constexpr size_t kNaQmeta = kNaMisc + 256;                               // uint4 per query
+constexpr size_t kNaRaw = na_align(kNaQmeta + (size_t)kNoAllocMaxQueries * 16);
+constexpr size_t kNaStacks = na_align(kNaRaw + kNoAllocMaxRaw * 16);
+constexpr size_t kNaCnt = na_align(kNaStacks + (size_t)kNoAllocThreads * kNoAllocStackCap * 16);
+constexpr size_t kNaCursor = kNaCnt + (size_t)kNoAllocMaxQueries * 4;    // contiguous with cnt
+constexpr size_t kNaUcnt = na_align(kNaCursor + (size_t)kNoAllocMaxQueries * 4);
+constexpr size_t kNaLarge = na_align(kNaUcnt + (size_t)kNoAllocMaxQueries * 4);
+constexpr size_t kNaStart = na_align(kNaLarge + (size_t)kNoAllocMaxQueries * 4);
+constexpr size_t kNaUoff = na_align(kNaStart + ((size_t)kNoAllocMaxQueries + 1) * 8);
+constexpr size_t kNaTiles = na_align(kNaUoff + ((size_t)kNoAllocMaxQueries + 1) * 8);
+constexpr size_t kNaGrouped = na_align(kNaTiles + ((size_t)kNoAllocMaxQueries / kScanTile + 4) * 8);
+constexpr size_t kNaTmp = na_align(kNaGrouped + kNoAllocMaxRaw * 8);
+constexpr size_t kNaEnd = na_align(kNaTmp + kNoAllocMaxRaw * 8);
+constexpr size_t kNoAllocBytes = (size_t)64 << 20;
+static_assert(kNaEnd <= kNoAllocBytes, "no-alloc scratch layout exceeds its array");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch per device.  In host code the array's name is only a
+// host-side stand-in, so its device address is taken once per device, with that device
+// current, by cudaGetSymbolAddress.
+std::mutex g_na_mu;
+constexpr int kNaMaxDevices = 64;
+unsigned char *g_na_base[kNaMaxDevices] = {};
+
+int noalloc_base(fm_index *h, unsigned char **out) {
+    if (h->device < 0 || h->device >= kNaMaxDevices)
+        return set_error(h, FM_EINVAL, "device ordinal out of range for the static scratch");
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_base[h->device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_status(h, e, "cudaGetSymbolAddress(static scratch)");
+        g_na_base[h->device] = (unsigned char *)p;
+    }
+    *out = g_na_base[h->device];
+    return FM_OK;
+}
+
+template <int I>
+int noalloc_launch(fm_index *h, const SearchCfg &c, uint4 *stacks, cudaStream_t st) {
+    const int pb = 128;
+    k_inexact_plain<I><<<(kNoAllocThreads + pb - 1) / pb, pb, 0, st>>>(c, stacks, kNoAllocStackCap,
+                                                                        kNoAllocThreads);
+    FM_CUDA_TRY(h, cudaGetLastError());
+    return FM_OK;
+}
+
+int run_inexact_noalloc(fm_index *h, const uint8_t *reads, const uint32_t *offs,
+                        uint32_t n_reads, const fm_search_params *sp, uint32_t *counts,
+                        uint64_t *offsets, uint32_t *pairs, uint64_t pair_capacity,
+                        uint64_t *pairs_needed, cudaStream_t st) {
+    const uint64_t nq64 = (uint64_t)n_reads * sp->strands;
+    if (nq64 > kNoAllocMaxQueries)
+        return set_error(h, FM_EINVAL, "fm_inexact_noalloc: " + std::to_string(nq64) +
+                                           " queries exceed the static scratch limit of " +
+                                           std::to_string(kNoAllocMaxQueries));
+    const uint32_t nq = (uint32_t)nq64;
+    int rc;
+    unsigned char *base = nullptr;
+    if ((rc = noalloc_base(h, &base))) return rc;
+    unsigned long long *d_raw_count = (unsigned long long *)(base + kNaMisc);
+    uint32_t *d_next_q = (uint32_t *)(base + kNaMisc + 8);
+    uint32_t *d_nlarge = (uint32_t *)(base + kNaMisc + 12);
+    unsigned long long *d_stats = (unsigned long long *)(base + kNaMisc + 32);
+    uint4 *qmeta = (uint4 *)(base + kNaQmeta);
+    uint4 *raw = (uint4 *)(base + kNaRaw);
+    uint4 *stacks = (uint4 *)(base + kNaStacks);
+    uint32_t *cnt = (uint32_t *)(base + kNaCnt), *cursor = (uint32_t *)(base + kNaCursor);
+    uint32_t *ucnt = (uint32_t *)(base + kNaUcnt), *large = (uint32_t *)(base + kNaLarge);
+    uint64_t *start = (uint64_t *)(base + kNaStart), *uoff = (uint64_t *)(base + kNaUoff);
+    uint64_t *tiles = (uint64_t *)(base + kNaTiles), *grouped = (uint64_t *)(base + kNaGrouped);
+    uint64_t *tmp = (uint64_t *)(base + kNaTmp);
+
+    // the array keeps the previous call's contents: counters start from zero
+    FM_CUDA_TRY(h, cudaMemsetAsync(base + kNaMisc, 0, 64, st));
+    if (nq == 0) {
+        FM_CUDA_TRY(h, cudaMemsetAsync(offsets, 0, 8, st));
+        FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+        if (pairs_needed) *pairs_needed = 0;
+        return FM_OK;
+    }
+    FM_CUDA_TRY(h, cudaMemsetAsync(h->d_err + kErrSearch, 0, 4, st));
+    if ((rc = launch_dcalc(h, reads, offs, n_reads, sp->strands, qmeta, nullptr, st))) return rc;
+
+    SearchCfg c;
+    c.ix = view_fwd(h);
+    c.reads = reads;
+    c.qmeta = qmeta;
+    c.nq = nq;
+    c.z = sp->z;
+    c.max_gaps = sp->max_gaps;
+    c.chunk = h->tune.chunk;
+    c.next_q = d_next_q;
+    c.raw = raw;
+    c.raw_count = d_raw_count;
+    c.raw_cap = kNoAllocMaxRaw;
+    c.stats = d_stats;
+    c.err = h->d_err + kErrSearch;
+    switch (h->interval) {
+        case 64: rc = noalloc_launch<64>(h, c, stacks, st); break;
+        case 128: rc = noalloc_launch<128>(h, c, stacks, st); break;
+        default: rc = noalloc_launch<256>(h, c, stacks, st); break;
+    }
+    if (rc) return rc;
+    unsigned long long rawn = 0;
+    uint32_t errw = 0;
+    FM_CUDA_TRY(h, cudaMemcpyAsync(&rawn, d_raw_count, 8, cudaMemcpyDeviceToHost, st));
+    FM_CUDA_TRY(h, cudaMemcpyAsync(&errw, h->d_err + kErrSearch, 4, cudaMemcpyDeviceToHost, st));
+    FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+    if (errw & kErrStack)   // cannot happen: the stack capacity is the proven bound
+        return set_error(h, FM_ENOMEM, "fm_inexact_noalloc: depth-first stack overflow");
+    if (rawn > kNoAllocMaxRaw)
+        return set_error(h, FM_ENOMEM, "fm_inexact_noalloc: " + std::to_string(rawn) +
+                                           " intervals before deduplication exceed the static "
+                                           "limit of " + std::to_string(kNoAllocMaxRaw));
+    const uint64_t R = rawn;
+    FM_CUDA_TRY(h, cudaMemsetAsync(cnt, 0, (size_t)nq * 4, st));
+    FM_CUDA_TRY(h, cudaMemsetAsync(cursor, 0, (size_t)nq * 4, st));
+    if (R) k_hist<<<grid_cap(h, R, 256), 256, 0, st>>>(raw, R, cnt);
+    if ((rc = scan_u32(h, cnt, nq, start, tiles, st))) return rc;
+    if (R) k_scatter<<<grid_cap(h, R, 256), 256, 0, st>>>(raw, R, start, cursor, grouped);
+    k_sort_small<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, st>>>(nq, cnt, start, grouped,
+                                                                       ucnt, large, d_nlarge);
+    FM_CUDA_TRY(h, cudaGetLastError());
+    uint32_t nlarge = 0;
+    FM_CUDA_TRY(h, cudaMemcpyAsync(&nlarge, d_nlarge, 4, cudaMemcpyDeviceToHost, st));
+    FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+    if (nlarge) {
+        const size_t lsm = 8192 * sizeof(uint64_t);
+        FM_CUDA_TRY(h, cudaFuncSetAttribute(k_sort_large,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
+        unsigned lg = nlarge < (uint32_t)h->sms * 4 ? nlarge : (uint32_t)h->sms * 4;
+        k_sort_large<<<lg, 512, lsm, st>>>(large, d_nlarge, cnt, start, grouped, tmp, ucnt);
+        FM_CUDA_TRY(h, cudaGetLastError());
+    }
+    if ((rc = scan_u32(h, ucnt, nq, uoff, tiles, st))) return rc;
+    FM_CUDA_TRY(h, cudaMemcpyAsync(offsets, uoff, ((size_t)nq + 1) * 8, cudaMemcpyDeviceToDevice, st));
+    k_copy_counts<<<grid_cap(h, nq, 256), 256, 0, st>>>(nq, ucnt, counts);
+    FM_CUDA_TRY(h, cudaGetLastError());
+    uint64_t need = 0;
+    FM_CUDA_TRY(h, cudaMemcpyAsync(&need, uoff + nq, 8, cudaMemcpyDeviceToHost, st));
+    FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+    if (pairs_needed) *pairs_needed = need;
+    if (sp->stats) {
+        k_add_stats<<<1, 32, 0, st>>>(d_stats, d_raw_count, (unsigned long long *)sp->stats);
+        FM_CUDA_TRY(h, cudaGetLastError());
+    }
+    if (need > pair_capacity) {
+        FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+        return set_error(h, FM_ETRUNC, "pair capacity " + std::to_string(pair_capacity) +
+                                           " below the " + std::to_string(need) + " intervals found");
+    }
+    if (need) {
+        k_compact<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, st>>>(nq, ucnt, start, uoff,
+                                                                        grouped, pairs);
+        FM_CUDA_TRY(h, cudaGetLastError());
+    }
+    uint32_t derr = 0;
+    FM_CUDA_TRY(h, cudaMemcpyAsync(&derr, h->d_err + kErrDcalc, 4, cudaMemcpyDeviceToHost, st));
+    FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+    if (derr & kErrReadLen) return set_error(h, FM_EINVAL, "a read is longer than 255 symbols");
+    if (derr & kErrDomain) return set_error(h, FM_EINVAL, "a read holds a code above 3");
+    return FM_OK;
+}
+
+}  // namespace
+}  // namespace fm
+
+extern "C" int fm_inexact_noalloc(fm_index *h, const uint8_t *reads, const uint32_t *offs,
+                                  uint32_t n_reads, const fm_search_params *sp, uint32_t *counts,
+                                  uint64_t *offsets, uint32_t *pairs, uint64_t pair_capacity,
+                                  uint64_t *pairs_needed, void *stream) {
+    using namespace fm;
+    if (!h) return set_global_error(FM_EINVAL, "null index handle");
+    if (!sp) return set_error(h, FM_EINVAL, "search params are NULL");
+    if (!h->has_rev) return set_error(h, FM_EINVAL, "index built without reverse(R)");
+    if (sp->z > (uint32_t)kMaxZ) return set_error(h, FM_EINVAL, "z must be at most 7");
+    if (sp->max_gaps > (uint32_t)kMaxGaps) return set_error(h, FM_EINVAL, "max_gaps must be at most 7");
+    if (sp->strands != 1 && sp->strands != 2) return set_error(h, FM_EINVAL, "strands must be 1 or 2");
+    if (!offsets || (n_reads && (!reads || !offs || !counts))) return set_error(h, FM_EINVAL, "null buffer");
+    if (pair_capacity && !pairs) return set_error(h, FM_EINVAL, "pairs is NULL");
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+        cudaGetLastError();
+        prev = -1;
+    }
+    if (prev != h->device && cudaSetDevice(h->device) != cudaSuccess)
+        return cuda_status(h, cudaGetLastError(), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = FM_OK;
+    cudaError_t e = cudaMemsetAsync(h->d_err + kErrDcalc, 0, 8, st);
+    if (e != cudaSuccess) rc = cuda_status(h, e, "cudaMemsetAsync(error words)");
+    if (!rc)
+        rc = run_inexact_noalloc(h, reads, offs, n_reads, sp, counts, offsets, pairs,
+                                 pair_capacity, pairs_needed, st);
+    if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
+    return rc;
+}

@@ -63,7 +63,7 @@ class fm_tuning(C.Structure):
 # every symbol include/fmocc.h declares
 EXPORTS = ["fm_build", "fm_free", "fm_last_error", "fm_info", "fm_get_bwt", "fm_save", "fm_load",
            "fm_occ8", "fm_exact", "fm_dcalc", "fm_inexact", "fm_inexact_fetch", "fm_set_tuning",
-           "fm_get_tuning"]
+           "fm_get_tuning", "fm_inexact_noalloc"]
 
 _lib = None
 
@@ -92,6 +92,8 @@ def load_library(path: str = LIB_PATH):
     lib.fm_inexact.argtypes = [P, P, P, u32, C.POINTER(fm_search_params), P, P, P, u64,
                                C.POINTER(C.c_uint64), P]
     lib.fm_inexact_fetch.argtypes = [P, P, u64, P]
+    lib.fm_inexact_noalloc.argtypes = [P, P, P, u32, C.POINTER(fm_search_params), P, P, P, u64,
+                                       C.POINTER(C.c_uint64), P]
     lib.fm_set_tuning.argtypes = [P, C.POINTER(fm_tuning)]
     lib.fm_get_tuning.argtypes = [P, C.POINTER(fm_tuning)]
     for name in EXPORTS:
@@ -304,6 +306,34 @@ def fm_inexact(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int, max_ga
                                   _stream(stream))
     _check(rc, h)
     return counts[:nq], offsets, pairs[:int(need.value)]
+
+
+def fm_inexact_noalloc(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int,
+                       max_gaps: int = 0, strands: int = 1, counts=None, offsets=None,
+                       pairs=None, stream=None):
+    """fm_inexact without device allocation inside the library (fixed static scratch; at most
+    32,768 queries per call).  The caller provides (or this wrapper allocates through torch,
+    before the call) the output buffers.  Returns (counts, offsets, pairs, status); status is
+    FM_ETRUNC when ``pairs`` is too small (counts and offsets are then complete)."""
+    lib = load_library()
+    nr = offs.numel() - 1
+    nq = nr * strands
+    dev = offs.device
+    if counts is None:
+        counts = torch.empty(max(nq, 1), dtype=torch.int32, device=dev)
+    if offsets is None:
+        offsets = torch.empty(nq + 1, dtype=torch.int64, device=dev)
+    if pairs is None:
+        pairs = torch.empty((4 * nq + 1024, 2), dtype=torch.int32, device=dev)
+    sp = fm_search_params(z, max_gaps, strands, FM_KERNEL_PERSISTENT, None, None)
+    need = C.c_uint64(0)
+    rc = lib.fm_inexact_noalloc(h.ptr, _dptr(reads, _U8, "reads"), _dptr(offs, _U32, "offs"), nr,
+                                C.byref(sp), _dptr(counts, _U32, "counts"),
+                                _dptr(offsets, _U64, "offsets"), _dptr(pairs, _U32, "pairs"),
+                                pairs.shape[0], C.byref(need), _stream(stream))
+    if rc not in (FM_OK, FM_ETRUNC):
+        _check(rc, h)
+    return counts[:nq], offsets, pairs[:min(int(need.value), pairs.shape[0])], rc
 
 
 def fm_inexact_fetch(h: Index, pairs: torch.Tensor, stream=None):
