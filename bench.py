@@ -38,6 +38,8 @@ if ROOT not in sys.path:
 METRIC = ("reads/s at z<=2 (batched vs plain kernel, bit-exact); 8-Occ Gq/s vs gather "
           "roofline")
 SEED_EXACT, SEED_OCC, SEED_SEARCH = 1811061271, 1811061272, 1811061274
+# bytes of one checkpoint block per interval (fm_info reports the same)
+BLOCK_BYTES = {32: 32, 64: 32, 128: 64, 256: 96}
 
 
 def parse():
@@ -293,7 +295,7 @@ def main():
     st = stats.cpu().numpy()
     nodes_per_step = st[0] / args.steps
     blocks_per_step = st[1] / args.steps
-    bbytes = {64: 32, 128: 64, 256: 96}[args.interval]
+    bbytes = BLOCK_BYTES[args.interval]
     value = args.reads * args.steps * world / total_s
     # dominant kernel: the persistent search kernel, its own event-timed duration per launch
     k_ms = float(np.mean(search_ms))
@@ -435,7 +437,7 @@ def bench_occ8(args, torch, fmocc, synth, dev, hbm_peak, peak_kind, flush, barri
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
     t = max_over_ranks(float(np.mean(ms)) / 1000.0)
-    bb = {64: 32, 128: 64, 256: 96}[I]
+    bb = BLOCK_BYTES[I]
     gather = blocks * bb
     io = args.occ_queries * 40.0
     h.close()

@@ -51,8 +51,8 @@ typedef struct fm_index fm_index;
 
 /* Build options. */
 typedef struct fm_params {
-    uint32_t interval; /* checkpoint interval I: 64 (32-byte blocks), 128 (64-byte blocks)
-                          or 256 (96-byte blocks); 0 means 64 */
+    uint32_t interval; /* checkpoint interval I: 32 or 64 (32-byte blocks), 128 (64-byte
+                          blocks) or 256 (96-byte blocks); 0 means 64 */
     uint32_t flags;    /* FM_BUILD_* bits */
     int32_t device;    /* CUDA device ordinal; -1 = the calling thread's current device */
     uint32_t reserved;
@@ -66,7 +66,7 @@ typedef struct fm_params {
 typedef struct fm_info_t {
     uint64_t n;              /* reference length |R| */
     uint32_t interval;       /* checkpoint interval I */
-    uint32_t block_bytes;    /* bytes per checkpoint block: 32, 64 or 96 */
+    uint32_t block_bytes;    /* bytes per checkpoint block: 32 (I = 32, 64), 64 or 96 */
     uint64_t C[5];           /* C array (Fig. 1) */
     uint64_t dollar_row;     /* row of the forward BWT holding $ */
     uint64_t rev_dollar_row; /* the same for reverse(R) (0 without a reverse index) */

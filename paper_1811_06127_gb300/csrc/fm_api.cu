@@ -148,8 +148,8 @@ int fm_build(const char *ref, uint64_t n, const fm_params *p, fm_index **out) {
     if (n < 1 || n > 2147483646ull)
         return set_global_error(FM_EINVAL, "reference length must be in [1, 2147483646]");
     uint32_t I = p && p->interval ? p->interval : 64;
-    if (I != 64 && I != 128 && I != 256)
-        return set_global_error(FM_EINVAL, "interval must be 64, 128 or 256");
+    if (I != 32 && I != 64 && I != 128 && I != 256)
+        return set_global_error(FM_EINVAL, "interval must be 32, 64, 128 or 256");
     uint32_t flags = p ? p->flags : 0;
     int dev = -1;
     if (p && p->device >= 0) dev = p->device;
@@ -309,7 +309,7 @@ int fm_load(const char *path, const fm_params *p, fm_index **out) {
     if (!f) return set_global_error(FM_EIO, std::string("cannot open ") + path);
     FileHeader hd;
     if (fread(&hd, sizeof(hd), 1, f) != 1 || memcmp(hd.magic, kMagic, 8) != 0 ||
-        (hd.interval != 64 && hd.interval != 128 && hd.interval != 256) ||
+        (hd.interval != 32 && hd.interval != 64 && hd.interval != 128 && hd.interval != 256) ||
         hd.bbytes != block_bytes(hd.interval) || hd.n_blocks != (hd.n + 1) / hd.interval + 1) {
         fclose(f);
         return set_global_error(FM_EIO, "not an fmocc index file");

@@ -60,9 +60,11 @@ __device__ __forceinline__ uint32_t w_at(const uint8_t *reads, const uint4 &mt, 
     return reads[mt.z + i];
 }
 
-// One expansion.  Outputs the eight child intervals and two 9-bit masks:
-//   bit 0 insertion, bits 1..4 deletion with b = 0..3, bits 5..8 match/mismatch with b = 0..3;
-// push: child kept as a node; leaf: child is a result.
+// One expansion: the eight-Occ step of Listing 2 (rank(c, k) and rank(c, l+1) for c in ACGT
+// from one or two checkpoint blocks), then the children.  Every lane runs the same code, so
+// the block gathers of the whole warp are issued together.  Outputs the four child intervals
+// and two 9-bit masks: bit 0 insertion, bits 1..4 deletion with b = 0..3, bits 5..8
+// match/mismatch with b = 0..3; push: child kept as a node; leaf: child is a result.
 template <int I>
 __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, const uint4 &mt,
                                        uint32_t k2[4], uint32_t l2[4], uint32_t &push,
@@ -79,6 +81,7 @@ __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, cons
     Blk<I> Bk, Bl;
     if (jk == jl) {
         load_block<I>(c.ix.blocks, jk, ok > ol ? ok : ol, Bk);
+        Bl = Bk;
         nblocks = 1;
     } else {
         load_block<I>(c.ix.blocks, jk, ok, Bk);
@@ -87,32 +90,74 @@ __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, cons
     }
     uint32_t rk[4], rl[4];
     rank4_in<I>(Bk, jk, pk, c.ix.dollar, rk);
-    rank4_in<I>(jk == jl ? Bk : Bl, jl, pl, c.ix.dollar, rl);
+    rank4_in<I>(Bl, jl, pl, c.ix.dollar, rl);
     const uint32_t d_here = d_at(mt, i);
     const uint32_t d_next = d_at(mt, i - 1);
     const bool gap_ok = z >= 1u && g < c.max_gaps;
+    const bool del_ok = gap_ok && z - 1u >= d_here;
+    const bool last = i == 0;
     push = 0;
     leaf = 0;
     // insertion: W[i] against no reference symbol, interval unchanged
     if (gap_ok) {
-        if (i == 0) {
+        if (last) {
             if (k >= 1u) leaf |= 1u;
         } else if (z - 1u >= d_next) {
             push |= 1u;
         }
     }
+    const bool mm_ok = z >= 1u && (last || z - 1u >= d_next);   // a mismatch child survives
+    const bool ma_ok = last || z >= d_next;                      // the match child survives
+    uint32_t alive = 0;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         k2[b] = c.ix.C[b] + rk[b] + 1u;
         l2[b] = c.ix.C[b] + rl[b];
-        if (k2[b] > l2[b]) continue;
-        if (gap_ok && z - 1u >= d_here) push |= 2u << b;           // deletion of b
-        const uint32_t zc = (uint32_t)b == wi ? z : z - 1u;          // match or mismatch
-        if ((uint32_t)b == wi || z >= 1u) {
-            if (i == 0) leaf |= 32u << b;
-            else if (zc >= d_next) push |= 32u << b;
-        }
+        const bool ne = k2[b] <= l2[b];
+        alive |= (ne ? 1u : 0u) << b;
+        const bool keep = (uint32_t)b == wi ? ma_ok : mm_ok;
+        const uint32_t mm = (ne && keep) ? (32u << b) : 0u;
+        if (last) leaf |= mm; else push |= mm;
     }
+    if (del_ok) push |= alive << 1;   // deletion of each b with a non-empty interval
+}
+
+// One call of InexRecur with no difference left (z = 0): only the match b = W[i] can continue,
+// so the eight-Occ step reduces to rank(W[i], k) and rank(W[i], l+1), i.e. one step of
+// Listing 1.  The single child replaces the node (out), or the interval is a result (leaf at
+// i = 0), or the branch ends (empty interval, or D(i-1) > 0).
+template <int I>
+__device__ __forceinline__ void exact_step(const SearchCfg &c, const uint4 &nd, const uint4 &mt,
+                                           uint4 &out, bool &survive, bool &is_leaf,
+                                           uint32_t &nblocks) {
+    const uint32_t i = nd.y & 255u;
+    const uint32_t b = w_at(c.reads, mt, i);
+    const uint32_t k = nd.z, l = nd.w;
+    const uint32_t pk = k, pl = l + 1u;
+    const uint32_t jk = pk / I, jl = pl / I;
+    const uint32_t ok = pk - jk * I, ol = pl - jl * I;
+    Blk<I> Bk, Bl;
+    if (jk == jl) {
+        load_block<I>(c.ix.blocks, jk, ok > ol ? ok : ol, Bk);
+        Bl = Bk;
+        nblocks = 1;
+    } else {
+        load_block<I>(c.ix.blocks, jk, ok, Bk);
+        load_block<I>(c.ix.blocks, jl, ol, Bl);
+        nblocks = 2;
+    }
+    // C[b] by select: a runtime index into the parameter struct would copy it to local memory
+    const uint32_t cb = b == 0 ? c.ix.C[0] : (b == 1 ? c.ix.C[1] : (b == 2 ? c.ix.C[2] : c.ix.C[3]));
+    const uint32_t k2 = cb + rank1_in<I>(Bk, jk, pk, c.ix.dollar, b) + 1u;
+    const uint32_t l2 = cb + rank1_in<I>(Bl, jl, pl, c.ix.dollar, b);
+    const bool alive = k2 <= l2;
+    is_leaf = alive && i == 0u;
+    survive = alive && i > 0u && d_at(mt, (int)i - 1) == 0u;
+    out = make_uint4(nd.x, (i - 1u) | (nd.y & 0xf000u), k2, l2);
+}
+
+__device__ __forceinline__ uint32_t pick4(const uint32_t v[4], uint32_t b) {
+    return b == 0 ? v[0] : (b == 1 ? v[1] : (b == 2 ? v[2] : v[3]));
 }
 
 // child number t (0 insertion, 1..4 deletion, 5..8 match/mismatch) of node nd
@@ -128,25 +173,25 @@ __device__ __forceinline__ uint4 make_child(const uint4 &nd, int t, const uint32
         ch.z = nd.z;
         ch.w = nd.w;
     } else if (t <= 4) {
-        const int b = t - 1;
+        const uint32_t b = (uint32_t)(t - 1);
         ch.y = i | ((z - 1u) << 8) | ((g + 1u) << 12);
-        ch.z = k2[b];
-        ch.w = l2[b];
+        ch.z = pick4(k2, b);
+        ch.w = pick4(l2, b);
     } else {
-        const int b = t - 5;
-        const uint32_t zc = (uint32_t)b == wi ? z : z - 1u;
+        const uint32_t b = (uint32_t)(t - 5);
+        const uint32_t zc = b == wi ? z : z - 1u;
         ch.y = (i - 1u) | (zc << 8) | (g << 12);
-        ch.z = k2[b];
-        ch.w = l2[b];
+        ch.z = pick4(k2, b);
+        ch.w = pick4(l2, b);
     }
     return ch;
 }
 
 __device__ __forceinline__ uint32_t leaf_k(const uint4 &nd, int t, const uint32_t k2[4]) {
-    return t == 0 ? nd.z : k2[(t - 1) & 3];
+    return t == 0 ? nd.z : pick4(k2, (uint32_t)(t - 1) & 3u);
 }
 __device__ __forceinline__ uint32_t leaf_l(const uint4 &nd, int t, const uint32_t l2[4]) {
-    return t == 0 ? nd.w : l2[(t - 1) & 3];
+    return t == 0 ? nd.w : pick4(l2, (uint32_t)(t - 1) & 3u);
 }
 
 __device__ __forceinline__ uint4 root_of(const SearchCfg &c, uint32_t q, const uint4 &mt,
@@ -169,6 +214,7 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 __device__ __forceinline__ void emit_leaves(const SearchCfg &c, int lane, bool act,
                                             const uint4 &nd, uint32_t leaf, const uint32_t k2[4],
                                             const uint32_t l2[4]) {
+    if (!__any_sync(FULL, act && leaf != 0u)) return;
     const int lc = act ? __popc(leaf) : 0;
     const int incl = warp_incl_scan(lc, lane);
     const int tot = __shfl_sync(FULL, incl, 31);
@@ -190,6 +236,18 @@ __device__ __forceinline__ void emit_leaves(const SearchCfg &c, int lane, bool a
 // ------------------------------------------------------------------------------------------
 // persistent kernel
 // ------------------------------------------------------------------------------------------
+// Each warp keeps two node pools in one shared-memory array of stk entries: G (nodes with
+// z >= 1, growing up from entry 0) and E (nodes with z = 0, growing down from entry stk-1).
+// E nodes are exact continuations (one cheap step each, the child replacing the node); G nodes
+// take the full eight-value expansion.  Policy per step:
+//   * E holds >= 32 nodes, or only E has work: one exact step for up to 32 E nodes, the
+//     survivors go back to E (ballot compaction);
+//   * else a G step: up to 32 G nodes expanded; children with z' = 0 go to E, the others to G
+//     (two warp prefix sums); if they would not fit, G is first moved to the warp's spill
+//     region in device memory (E holds < 32 then, so 288 children always fit after that);
+//   * G empty but spilled nodes waiting: reload a batch;
+//   * both pools low: take the next chunk of queries from the work queue (their roots).
+// A warp leaves when the queue is drained and both pools and its spill are empty.
 template <int I>
 __global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk, uint4 *spill_all,
                                                             uint32_t spill_cap) {
@@ -200,49 +258,86 @@ __global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk
     const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     uint4 *spill = spill_all + gw * spill_cap;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    int top = 0;          // nodes in the shared pool (warp-uniform)
-    uint32_t stop = 0;    // nodes in the spill region (warp-uniform)
+    int gtop = 0;         // G: st[0, gtop)
+    int etop = 0;         // E: st[stk - etop, stk), top at st[stk - etop]
+    uint32_t stop = 0;    // spilled G nodes (warp-uniform)
     bool qdone = false;
     unsigned long long my_nodes = 0, my_blocks = 0;
 
     for (;;) {
-        if (top < 32) {
-            if (stop > 0) {
-                // drain spilled work before taking new queries
-                uint32_t nmove = stop < (uint32_t)(stk / 2) ? stop : (uint32_t)(stk / 2);
-                if ((uint32_t)top + nmove > (uint32_t)(stk - 288)) nmove = (uint32_t)(stk - 288 - top);
-                for (uint32_t t = lane; t < nmove; t += 32) st[top + t] = spill[stop - nmove + t];
-                stop -= nmove;
-                top += (int)nmove;
-                __syncwarp();
-            } else if (!qdone) {
-                uint32_t q0 = 0;
-                if (lane == 0) q0 = atomicAdd(c.next_q, c.chunk);
-                q0 = __shfl_sync(FULL, q0, 0);
-                if (q0 >= c.nq) {
-                    qdone = true;
+        if (gtop + etop < 32 && stop == 0 && !qdone) {
+            uint32_t q0 = 0;
+            if (lane == 0) q0 = atomicAdd(c.next_q, c.chunk);
+            q0 = __shfl_sync(FULL, q0, 0);
+            if (q0 >= c.nq) {
+                qdone = true;
+            } else {
+                const uint32_t q = q0 + lane;
+                bool ok = false;
+                uint4 nd;
+                if ((uint32_t)lane < c.chunk && q < c.nq) nd = root_of(c, q, c.qmeta[q], ok);
+                const uint32_t bal = __ballot_sync(FULL, ok);
+                const int pos = __popc(bal & lt_mask);
+                if (c.z == 0) {
+                    if (ok) st[stk - 1 - (etop + pos)] = nd;
+                    etop += __popc(bal);
                 } else {
-                    const uint32_t q = q0 + lane;
-                    bool ok = false;
-                    uint4 nd;
-                    if ((uint32_t)lane < c.chunk && q < c.nq) nd = root_of(c, q, c.qmeta[q], ok);
-                    const uint32_t bal = __ballot_sync(FULL, ok);
-                    if (ok) st[top + __popc(bal & lt_mask)] = nd;
-                    top += __popc(bal);
-                    __syncwarp();
+                    if (ok) st[gtop + pos] = nd;
+                    gtop += __popc(bal);
                 }
+                __syncwarp();
             }
         }
-        if (top == 0) {
-            if (stop > 0) continue;
-            if (qdone) break;
+        if (etop >= 32 || (etop > 0 && gtop == 0 && stop == 0)) {
+            // exact steps
+            const int take = etop < 32 ? etop : 32;
+            const bool act = lane < take;
+            uint4 nd = make_uint4(0, 0, 0, 0), ch = make_uint4(0, 0, 0, 0);
+            if (act) nd = st[stk - etop + lane];
+            etop -= take;
+            __syncwarp();
+            bool survive = false, is_leaf = false;
+            if (act) {
+                const uint4 mt = c.qmeta[nd.x];
+                uint32_t nb = 0;
+                exact_step<I>(c, nd, mt, ch, survive, is_leaf, nb);
+                my_nodes += 1;
+                my_blocks += nb;
+            }
+            const uint32_t bal = __ballot_sync(FULL, survive);
+            if (survive) st[stk - 1 - (etop + __popc(bal & lt_mask))] = ch;
+            etop += __popc(bal);
+            const uint32_t lb = __ballot_sync(FULL, is_leaf);
+            if (lb) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(c.raw_count, (unsigned long long)__popc(lb));
+                base = __shfl_sync(FULL, base, 0);
+                const uint64_t pos = base + __popc(lb & lt_mask);
+                if (is_leaf && pos < c.raw_cap) c.raw[pos] = make_uint4(nd.x, ch.z, ch.w, 0u);
+            }
+            __syncwarp();
             continue;
         }
-        const int take = top < 32 ? top : 32;
+        if (gtop == 0 && stop > 0) {
+            // reload spilled G nodes: keep room for the children of one G step (288) plus E
+            int room = stk - 256 - etop;
+            uint32_t nmove = stop < (uint32_t)room ? stop : (uint32_t)room;
+            for (uint32_t t = lane; t < nmove; t += 32) st[t] = spill[stop - nmove + t];
+            stop -= nmove;
+            gtop = (int)nmove;
+            __syncwarp();
+            continue;
+        }
+        if (gtop == 0) {
+            if (qdone && etop == 0 && stop == 0) break;
+            continue;
+        }
+        // general step on up to 32 G nodes
+        const int take = gtop < 32 ? gtop : 32;
         const bool act = lane < take;
         uint4 nd = make_uint4(0, 0, 0, 0), mt = make_uint4(0, 0, 0, 0);
-        if (act) nd = st[top - 1 - lane];
-        top -= take;
+        if (act) nd = st[gtop - 1 - lane];
+        gtop -= take;
         __syncwarp();
         uint32_t k2[4] = {0, 0, 0, 0}, l2[4] = {0, 0, 0, 0}, push = 0, leaf = 0, nb = 0, wi = 0;
         if (act) {
@@ -251,32 +346,41 @@ __global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk
             my_nodes += 1;
             my_blocks += nb;
         }
-        // compaction of the surviving children
-        const int pc = __popc(push);
-        const int incl = warp_incl_scan(pc, lane);
-        const int total = __shfl_sync(FULL, incl, 31);
-        if (top + total > stk) {
-            // pool full: move it to the spill region
-            if (stop + (uint32_t)top > spill_cap) {
+        // children with z' = 0 (every child but the match of a z = 1 node) go to E
+        const uint32_t z = (nd.y >> 8) & 15u;
+        const uint32_t emask = z == 1u ? (push & ~(32u << wi)) : 0u;
+        const uint32_t gmask = push & ~emask;
+        const int gc = __popc(gmask), ec = __popc(emask);
+        const int gincl = warp_incl_scan(gc, lane);
+        const int eincl = warp_incl_scan(ec, lane);
+        const int gtot = __shfl_sync(FULL, gincl, 31);
+        const int etot = __shfl_sync(FULL, eincl, 31);
+        if (gtop + gtot + etop + etot > stk) {
+            // pools full: move G to the spill region (E holds < 32 nodes here)
+            if (stop + (uint32_t)gtop > spill_cap) {
                 if (lane == 0) atomicOr(c.err, kErrSpill);
-                top = 0;   // work dropped: the host grows the spill region and reruns
+                gtop = 0;   // work dropped: the host grows the spill region and reruns
             } else {
-                for (int t = lane; t < top; t += 32) spill[stop + t] = st[t];
-                stop += (uint32_t)top;
-                top = 0;
+                for (int t = lane; t < gtop; t += 32) spill[stop + t] = st[t];
+                stop += (uint32_t)gtop;
+                gtop = 0;
             }
             __syncwarp();
         }
         {
-            int pos = top + incl - pc;
+            int gpos = gtop + gincl - gc;
+            int epos = etop + eincl - ec;
             uint32_t mset = push;
             while (mset) {
                 const int t = __ffs(mset) - 1;
                 mset &= mset - 1;
-                st[pos++] = make_child(nd, t, k2, l2, wi);
+                const uint4 chd = make_child(nd, t, k2, l2, wi);
+                if ((emask >> t) & 1u) st[stk - 1 - (epos++)] = chd;
+                else st[gpos++] = chd;
             }
         }
-        top += total;
+        gtop += gtot;
+        etop += etot;
         emit_leaves(c, lane, act, nd, leaf, k2, l2);
         __syncwarp();
     }
@@ -307,6 +411,10 @@ __global__ void __launch_bounds__(256) k_inexact_plain(SearchCfg c, uint4 *stack
     uint32_t q = tid;
     uint32_t sp = 0;
     bool have = false;
+    // a node with z = 0 is continued in place (one Listing 1 step per loop iteration) instead of
+    // being pushed and popped
+    bool cur = false;
+    uint4 curnd = make_uint4(0, 0, 0, 0);
     for (;;) {
         // fetch the next query when the stack is empty
         while (!have && q < c.nq) {
@@ -324,27 +432,51 @@ __global__ void __launch_bounds__(256) k_inexact_plain(SearchCfg c, uint4 *stack
         if (!__any_sync(FULL, act)) break;
         uint4 nd = make_uint4(0, 0, 0, 0);
         uint32_t k2[4] = {0, 0, 0, 0}, l2[4] = {0, 0, 0, 0}, push = 0, leaf = 0, nb = 0, wi = 0;
+        bool ex_leaf = false;
+        uint4 ex_out = make_uint4(0, 0, 0, 0);
         if (act) {
-            nd = stacks[(size_t)(sp - 1) * T + tid];
-            --sp;
+            if (cur) {
+                nd = curnd;
+            } else {
+                nd = stacks[(size_t)(sp - 1) * T + tid];
+                --sp;
+            }
+            cur = false;
             const uint4 mt = c.qmeta[nd.x];
-            expand<I>(c, nd, mt, k2, l2, push, leaf, nb, wi);
-            my_nodes += 1;
-            my_blocks += nb;
-            uint32_t mset = push;
-            while (mset) {
-                const int t = __ffs(mset) - 1;
-                mset &= mset - 1;
-                if (sp < cap) {
-                    stacks[(size_t)sp * T + tid] = make_child(nd, t, k2, l2, wi);
-                    ++sp;
-                } else {
-                    atomicOr(c.err, kErrStack);
+            if (((nd.y >> 8) & 15u) == 0u) {
+                bool survive = false;
+                exact_step<I>(c, nd, mt, ex_out, survive, ex_leaf, nb);
+                if (survive) {
+                    curnd = ex_out;
+                    cur = true;
+                }
+            } else {
+                expand<I>(c, nd, mt, k2, l2, push, leaf, nb, wi);
+                uint32_t mset = push;
+                while (mset) {
+                    const int t = __ffs(mset) - 1;
+                    mset &= mset - 1;
+                    if (sp < cap) {
+                        stacks[(size_t)sp * T + tid] = make_child(nd, t, k2, l2, wi);
+                        ++sp;
+                    } else {
+                        atomicOr(c.err, kErrStack);
+                    }
                 }
             }
-            if (sp == 0) have = false;
+            my_nodes += 1;
+            my_blocks += nb;
+            if (sp == 0 && !cur) have = false;
         }
         emit_leaves(c, lane, act, nd, leaf, k2, l2);
+        const uint32_t lb = __ballot_sync(FULL, ex_leaf);
+        if (lb) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(c.raw_count, (unsigned long long)__popc(lb));
+            base = __shfl_sync(FULL, base, 0);
+            const uint64_t pos = base + __popc(lb & ((1u << lane) - 1u));
+            if (ex_leaf && pos < c.raw_cap) c.raw[pos] = make_uint4(nd.x, ex_out.z, ex_out.w, 0u);
+        }
     }
     if (c.stats) {
 #pragma unroll
@@ -773,11 +905,11 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
     const int block = (int)tu.warps_per_block * 32;
     const int stk = 352;   // pool entries per warp: >= 288 (children of 32 nodes) + 32
     const size_t smem = (size_t)(block / 32) * stk * sizeof(uint4);
-    cudaError_t e = I == 64 ? set_smem_attr<64>(smem) : (I == 128 ? set_smem_attr<128>(smem)
-                                                                  : set_smem_attr<256>(smem));
+    cudaError_t e = I == 32 ? set_smem_attr<32>(smem) : (I == 64 ? set_smem_attr<64>(smem) : (I == 128 ? set_smem_attr<128>(smem)
+                                                                  : set_smem_attr<256>(smem)));
     if (e != cudaSuccess) return cuda_status(h, e, "cudaFuncSetAttribute");
     int bps = (int)tu.blocks_per_sm;
-    const int occ = I == 64 ? occupancy_blocks<64>(block, smem)
+    const int occ = I == 32 ? occupancy_blocks<32>(block, smem) : I == 64 ? occupancy_blocks<64>(block, smem)
                             : (I == 128 ? occupancy_blocks<128>(block, smem)
                                         : occupancy_blocks<256>(block, smem));
     if (bps <= 0 || bps > occ) bps = occ;
@@ -824,6 +956,7 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
         c.err = h->d_err + kErrSearch;
         if (prof) FM_CUDA_TRY(h, cudaEventRecord(ev[1], st));
         switch (I) {
+            case 32: rc = launch_search<32>(h, c, sp->kernel, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, (uint4 *)h->s_plain.ptr, cap, T, st); break;
             case 64: rc = launch_search<64>(h, c, sp->kernel, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, (uint4 *)h->s_plain.ptr, cap, T, st); break;
             case 128: rc = launch_search<128>(h, c, sp->kernel, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, (uint4 *)h->s_plain.ptr, cap, T, st); break;
             default: rc = launch_search<256>(h, c, sp->kernel, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, (uint4 *)h->s_plain.ptr, cap, T, st); break;
@@ -1061,6 +1194,7 @@ int run_inexact_noalloc(fm_index *h, const uint8_t *reads, const uint32_t *offs,
     c.stats = d_stats;
     c.err = h->d_err + kErrSearch;
     switch (h->interval) {
+        case 32: rc = noalloc_launch<32>(h, c, stacks, st); break;
         case 64: rc = noalloc_launch<64>(h, c, stacks, st); break;
         case 128: rc = noalloc_launch<128>(h, c, stacks, st); break;
         default: rc = noalloc_launch<256>(h, c, stacks, st); break;

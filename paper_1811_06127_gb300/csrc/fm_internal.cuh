@@ -6,7 +6,8 @@
 //   bytes 16..    the I BWT symbols of the block, 2 bits each, symbol t of the block at bits
 //                 2(t%32)..2(t%32)+1 of 64-bit word t/32 (the little-endian 2-bit code of
 //                 Fig. 2); $ is stored as A and corrected for through dollar_row
-//   I = 64: 32-byte blocks (one DRAM sector); I = 128: 64 bytes; I = 256: 96 bytes (80 used).
+//   I = 32: 32-byte blocks (24 used), I = 64: 32-byte blocks (one DRAM sector);
+//   I = 128: 64 bytes; I = 256: 96 bytes (80 used).
 // One extra final block holds the totals, so rank(c, n+1) needs no special case.
 // This interleaving of counters and symbols in one block follows the bucket layout the paper
 // describes in Sec. 2 (128 symbols with 4 x 64-bit counters); here the counters are uint32
@@ -27,7 +28,7 @@ constexpr int kMaxZ = 7;
 constexpr int kMaxGaps = 7;
 
 __host__ __device__ constexpr uint32_t block_bytes(uint32_t I) {
-    return I == 64 ? 32u : (I == 128 ? 64u : 96u);
+    return I <= 64 ? 32u : (I == 128 ? 64u : 96u);
 }
 
 // Device view of one resident index.
@@ -173,45 +174,63 @@ __device__ __forceinline__ void load_block(const uint8_t *blocks, uint32_t j, ui
     ldg256(p, a, b);
     B.cnt = a;
     B.w[0] = u64of(b.x, b.y);
-    B.w[1] = u64of(b.z, b.w);
+    if constexpr (I >= 64) B.w[1] = u64of(b.z, b.w);
     if constexpr (I >= 128) {
-        if (upto > 64) {
-            uint4 c, d;
-            ldg256(p + 32, c, d);
-            B.w[2] = u64of(c.x, c.y);
-            B.w[3] = u64of(c.z, c.w);
-            if constexpr (I == 256) {
-                B.w[4] = u64of(d.x, d.y);
-                B.w[5] = u64of(d.z, d.w);
-                if (upto > 192) {
-                    uint4 e, f;
-                    ldg256(p + 64, e, f);
-                    B.w[6] = u64of(e.x, e.y);
-                    B.w[7] = u64of(e.z, e.w);
-                } else {
-                    B.w[6] = B.w[7] = 0;
-                }
-            }
-        } else {
-            B.w[2] = B.w[3] = 0;
-            if constexpr (I == 256) B.w[4] = B.w[5] = B.w[6] = B.w[7] = 0;
+        // every word is assigned once; a sector no offset needs is not read
+        uint4 c = make_uint4(0, 0, 0, 0), d = make_uint4(0, 0, 0, 0);
+        if (upto > 64) ldg256(p + 32, c, d);
+        B.w[2] = u64of(c.x, c.y);
+        B.w[3] = u64of(c.z, c.w);
+        if constexpr (I == 256) {
+            uint4 e = make_uint4(0, 0, 0, 0), f;
+            B.w[4] = u64of(d.x, d.y);
+            B.w[5] = u64of(d.z, d.w);
+            if (upto > 192) ldg256(p + 64, e, f);
+            B.w[6] = u64of(e.x, e.y);
+            B.w[7] = u64of(e.z, e.w);
         }
     }
+}
+
+// Mask of the low `width` bits (width in [0, 32]).
+__device__ __forceinline__ uint32_t low_mask(uint32_t width) {
+    uint32_t m;
+    asm("bmsk.clamp.b32 %0, %1, %2;" : "=r"(m) : "r"(0u), "r"(width));
+    return m;
+}
+
+// C, G and T among the first t symbols (t in [0, 32]) of one 64-bit word, in 32-bit steps:
+// the lo/hi bit planes of the two 16-symbol halves are masked to the prefix and interleaved
+// into one 32-bit word each, so three popcounts count 32 symbols.
+__device__ __forceinline__ void count_word32(uint64_t w, uint32_t t, uint32_t &c, uint32_t &g,
+                                             uint32_t &tt) {
+    const uint32_t m55 = 0x55555555u;
+    const uint32_t w0 = (uint32_t)w, w1 = (uint32_t)(w >> 32);
+    const uint32_t t0 = t < 16u ? t : 16u;
+    const uint32_t m0 = low_mask(2u * t0) & m55;
+    const uint32_t m1 = low_mask(2u * (t - t0)) & m55;
+    const uint32_t L = (w0 & m0) | ((w1 & m1) << 1);
+    const uint32_t H = ((w0 >> 1) & m0) | (((w1 >> 1) & m1) << 1);
+    const uint32_t both = __popc(L & H);
+    tt += both;
+    c += __popc(L) - both;
+    g += __popc(H) - both;
 }
 
 // rank(c, p) for c = A,C,G,T given the loaded block of p (block index j = p / I).
 template <int I>
 __device__ __forceinline__ void rank4_in(const Blk<I> &B, uint32_t j, uint32_t p, uint32_t dollar,
                                          uint32_t r[4]) {
-    uint32_t o = p - j * (uint32_t)I;
+    const uint32_t o = p - j * (uint32_t)I;
     uint32_t c = 0, g = 0, t = 0;
 #pragma unroll
     for (int wi = 0; wi < I / 32; ++wi) {
-        int32_t left = (int32_t)o - 32 * wi;
-        if (left > 0) count_word(B.w[wi], (uint32_t)(left > 32 ? 32 : left), c, g, t);
+        const int32_t left = (int32_t)o - 32 * wi;
+        const uint32_t n = left <= 0 ? 0u : (left >= 32 ? 32u : (uint32_t)left);
+        count_word32(B.w[wi], n, c, g, t);
     }
     uint32_t a = o - c - g - t;
-    uint32_t base = j * (uint32_t)I;
+    const uint32_t base = j * (uint32_t)I;
     a -= (dollar >= base && dollar < p) ? 1u : 0u;
     r[0] = B.cnt.x + a;
     r[1] = B.cnt.y + c;
@@ -219,13 +238,46 @@ __device__ __forceinline__ void rank4_in(const Blk<I> &B, uint32_t j, uint32_t p
     r[3] = B.cnt.w + t;
 }
 
-// rank(b, p) for one symbol b.
+// Occurrences of symbol b among the first t symbols (t in [0, 32]) of one 64-bit word, in
+// 32-bit steps: XOR with b's pattern turns b's pairs into 00; a pair is 00 when neither bit is
+// set; the two 16-symbol halves are interleaved into one word for a single popcount.
+__device__ __forceinline__ uint32_t count_sym(uint64_t w, uint32_t t, uint32_t b) {
+    const uint32_t m55 = 0x55555555u;
+    const uint32_t pat = m55 * b;
+    const uint32_t x0 = (uint32_t)w ^ pat, x1 = (uint32_t)(w >> 32) ^ pat;
+    const uint32_t t0 = t < 16u ? t : 16u;
+    const uint32_t y0 = ~(x0 | (x0 >> 1)) & (low_mask(2u * t0) & m55);
+    const uint32_t y1 = ~(x1 | (x1 >> 1)) & (low_mask(2u * (t - t0)) & m55);
+    return __popc(y0 | (y1 << 1));
+}
+
+// rank(b, p) for one symbol b given the loaded block of p.
 template <int I>
 __device__ __forceinline__ uint32_t rank1_in(const Blk<I> &B, uint32_t j, uint32_t p,
                                              uint32_t dollar, uint32_t b) {
-    uint32_t r[4];
-    rank4_in<I>(B, j, p, dollar, r);
-    return b == 0 ? r[0] : (b == 1 ? r[1] : (b == 2 ? r[2] : r[3]));
+    const uint32_t o = p - j * (uint32_t)I;
+    uint32_t r = 0;
+#pragma unroll
+    for (int wi = 0; wi < I / 32; ++wi) {
+        const int32_t left = (int32_t)o - 32 * wi;
+        const uint32_t n = left <= 0 ? 0u : (left >= 32 ? 32u : (uint32_t)left);
+        r += count_sym(B.w[wi], n, b);
+    }
+    const uint32_t base = j * (uint32_t)I;
+    if (b == 0u) r -= (dollar >= base && dollar < p) ? 1u : 0u;   // $ is stored as A
+    const uint32_t cnt = b == 0 ? B.cnt.x : (b == 1 ? B.cnt.y : (b == 2 ? B.cnt.z : B.cnt.w));
+    return cnt + r;
+}
+
+// BWT symbol at row p of the loaded block j (the $ row reads as A).
+template <int I>
+__device__ __forceinline__ uint32_t sym_in(const Blk<I> &B, uint32_t j, uint32_t p) {
+    const uint32_t o = p - j * (uint32_t)I;
+    const uint32_t sel = o >> 5;
+    uint64_t w = 0;   // masked OR, not an indexed read: keeps the block in registers
+#pragma unroll
+    for (int t = 0; t < I / 32; ++t) w |= B.w[t] & (0ull - (uint64_t)(sel == (uint32_t)t));
+    return (uint32_t)(w >> (2 * (o & 31))) & 3u;
 }
 
 }  // namespace fm

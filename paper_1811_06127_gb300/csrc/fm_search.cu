@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(256) k_occ8(IndexView ix, const uint32_t *__re
                 uint32_t o1 = p1[t] - j1[t] * I, o2 = p2[t] - j2[t] * I;
                 if (j1[t] == j2[t]) {
                     load_block<I>(ix.blocks, j1[t], o1 > o2 ? o1 : o2, B1[t]);
+                    B2[t] = B1[t];
                 } else {
                     load_block<I>(ix.blocks, j1[t], o1, B1[t]);
                     load_block<I>(ix.blocks, j2[t], o2, B2[t]);
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(256) k_occ8(IndexView ix, const uint32_t *__re
             uint32_t a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
             if (ok[t]) {
                 rank4_in<I>(B1[t], j1[t], p1[t], ix.dollar, a);
-                rank4_in<I>(j1[t] == j2[t] ? B1[t] : B2[t], j2[t], p2[t], ix.dollar, b);
+                rank4_in<I>(B2[t], j2[t], p2[t], ix.dollar, b);
             } else {
                 atomicOr(err, kErrDomain);
             }
@@ -116,14 +117,16 @@ __global__ void __launch_bounds__(128) k_exact(IndexView ix, const uint8_t *__re
             const uint32_t ok = pk - jk * I, ol = pl - jl * I;
             if (jk == jl) {
                 load_block<I>(ix.blocks, jk, ok > ol ? ok : ol, Bk);
+                Bl = Bk;
             } else {
                 load_block<I>(ix.blocks, jk, ok, Bk);
                 load_block<I>(ix.blocks, jl, ol, Bl);
             }
             const uint32_t rk = rank1_in<I>(Bk, jk, pk, ix.dollar, b);
-            const uint32_t rl = rank1_in<I>(jk == jl ? Bk : Bl, jl, pl, ix.dollar, b);
-            k = ix.C[b] + rk + 1u;
-            l = ix.C[b] + rl;
+            const uint32_t rl = rank1_in<I>(Bl, jl, pl, ix.dollar, b);
+            const uint32_t cb = b == 0 ? ix.C[0] : (b == 1 ? ix.C[1] : (b == 2 ? ix.C[2] : ix.C[3]));
+            k = cb + rk + 1u;
+            l = cb + rl;
         }
         kout[r] = k;
         lout[r] = l;
@@ -148,7 +151,8 @@ __global__ void __launch_bounds__(128) k_dcalc(IndexView rv, const uint8_t *__re
         const uint32_t strand = strands == 2 ? (q & 1u) : 0u;
         const uint32_t s = offs[r];
         const uint32_t m = offs[r + 1] - s;
-        uint8_t bp[8] = {255, 255, 255, 255, 255, 255, 255, 255};
+        // breakpoint j = first i with D(i) >= j+1, 8 bits each, 255 = never
+        uint32_t bp_lo = 0xffffffffu, bp_hi = 0xffffffffu;
         bool bad = m > (uint32_t)kMaxReadLen;
         if (bad) atomicOr(err, kErrReadLen);
         uint32_t k = 0, l = rv.n, z = 0;
@@ -167,14 +171,17 @@ __global__ void __launch_bounds__(128) k_dcalc(IndexView rv, const uint8_t *__re
             const uint32_t ok = pk - jk * I, ol = pl - jl * I;
             if (jk == jl) {
                 load_block<I>(rv.blocks, jk, ok > ol ? ok : ol, Bk);
+                Bl = Bk;
             } else {
                 load_block<I>(rv.blocks, jk, ok, Bk);
                 load_block<I>(rv.blocks, jl, ol, Bl);
             }
-            const uint32_t k2 = rv.C[b] + rank1_in<I>(Bk, jk, pk, rv.dollar, b) + 1u;
-            const uint32_t l2 = rv.C[b] + rank1_in<I>(jk == jl ? Bk : Bl, jl, pl, rv.dollar, b);
+            const uint32_t cb = b == 0 ? rv.C[0] : (b == 1 ? rv.C[1] : (b == 2 ? rv.C[2] : rv.C[3]));
+            const uint32_t k2 = cb + rank1_in<I>(Bk, jk, pk, rv.dollar, b) + 1u;
+            const uint32_t l2 = cb + rank1_in<I>(Bl, jl, pl, rv.dollar, b);
             if (k2 > l2) {   // W[j..i] does not occur: close the window, restart after i
-                if (z < 8) bp[z] = (uint8_t)i;
+                if (z < 4) bp_lo = (bp_lo & ~(0xffu << (8 * z))) | (i << (8 * z));
+                else if (z < 8) bp_hi = (bp_hi & ~(0xffu << (8 * (z - 4)))) | (i << (8 * (z - 4)));
                 ++z;
                 k = 0;
                 l = rv.n;
@@ -186,10 +193,8 @@ __global__ void __launch_bounds__(128) k_dcalc(IndexView rv, const uint8_t *__re
         }
         if (qmeta) {
             uint4 mt;
-            mt.x = (uint32_t)bp[0] | ((uint32_t)bp[1] << 8) | ((uint32_t)bp[2] << 16) |
-                   ((uint32_t)bp[3] << 24);
-            mt.y = (uint32_t)bp[4] | ((uint32_t)bp[5] << 8) | ((uint32_t)bp[6] << 16) |
-                   ((uint32_t)bp[7] << 24);
+            mt.x = bp_lo;
+            mt.y = bp_hi;
             mt.z = s;
             // a bad query is given length 0: the search then reports nothing for it
             mt.w = (bad ? 0u : m) | (strand << 8);
@@ -216,6 +221,7 @@ int launch_occ8(fm_index *h, const uint32_t *k, const uint32_t *l, uint32_t *out
     const int block = 256;
     int grid = grid_occ(h, (N + Q - 1) / Q, block);
     switch (h->interval) {
+        case 32: k_occ8<32, Q><<<grid, block, 0, st>>>(ix, k, l, out8, N, err); break;
         case 64: k_occ8<64, Q><<<grid, block, 0, st>>>(ix, k, l, out8, N, err); break;
         case 128: k_occ8<128, Q><<<grid, block, 0, st>>>(ix, k, l, out8, N, err); break;
         default: k_occ8<256, Q><<<grid, block, 0, st>>>(ix, k, l, out8, N, err); break;
@@ -232,6 +238,7 @@ int launch_exact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32
     const int block = 128;
     int grid = grid_occ(h, n_reads, block);
     switch (h->interval) {
+        case 32: k_exact<32><<<grid, block, 0, st>>>(ix, reads, offs, n_reads, k_out, l_out, err); break;
         case 64: k_exact<64><<<grid, block, 0, st>>>(ix, reads, offs, n_reads, k_out, l_out, err); break;
         case 128: k_exact<128><<<grid, block, 0, st>>>(ix, reads, offs, n_reads, k_out, l_out, err); break;
         default: k_exact<256><<<grid, block, 0, st>>>(ix, reads, offs, n_reads, k_out, l_out, err); break;
@@ -249,6 +256,7 @@ int launch_dcalc(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32
     const int block = 128;
     int grid = grid_occ(h, nq, block);
     switch (h->interval) {
+        case 32: k_dcalc<32><<<grid, block, 0, st>>>(rv, reads, offs, n_reads, strands, qmeta, D_out, err); break;
         case 64: k_dcalc<64><<<grid, block, 0, st>>>(rv, reads, offs, n_reads, strands, qmeta, D_out, err); break;
         case 128: k_dcalc<128><<<grid, block, 0, st>>>(rv, reads, offs, n_reads, strands, qmeta, D_out, err); break;
         default: k_dcalc<256><<<grid, block, 0, st>>>(rv, reads, offs, n_reads, strands, qmeta, D_out, err); break;

@@ -70,7 +70,7 @@ def _text(kind, n):
     return synth.repeat_text(77, n, families=20, min_len=300, max_len=3000)
 
 
-@pytest.mark.parametrize("interval", [64, 128, 256])
+@pytest.mark.parametrize("interval", [32, 64, 128, 256])
 @pytest.mark.parametrize("kind,n", TEXTS)
 def test_bwt_c_dollar(fm, kind, n, interval):
     R = _text(kind, n)
@@ -100,7 +100,7 @@ def _edge_queries(n, I):
     return np.array(ks, np.uint32), np.array(ls, np.uint32)
 
 
-@pytest.mark.parametrize("interval", [64, 128, 256])
+@pytest.mark.parametrize("interval", [32, 64, 128, 256])
 @pytest.mark.parametrize("kind,n", [("uniform", 1), ("uniform", 65), ("uniform", 1000),
                                     ("repeat", 100_000), ("uniform", 1_000_000)])
 def test_occ8_matches_oracle(fm, kind, n, interval):
@@ -137,7 +137,7 @@ def test_occ8_domain_error_and_empty(fm):
     h.close()
 
 
-@pytest.mark.parametrize("interval", [64, 128, 256])
+@pytest.mark.parametrize("interval", [32, 64, 128, 256])
 def test_exact_matches_oracle(fm, interval):
     R = synth.uniform_text(1811061271, 1_000_000)
     h = fm.fm_build(R, interval=interval)
@@ -162,7 +162,7 @@ def test_exact_bad_code(fm):
     h.close()
 
 
-@pytest.mark.parametrize("interval", [64, 256])
+@pytest.mark.parametrize("interval", [32, 64, 256])
 def test_dcalc_matches_oracle(fm, interval):
     R = synth.repeat_text(5, 300_000, families=30, min_len=300, max_len=3000)
     h = fm.fm_build(R, interval=interval)
@@ -207,7 +207,7 @@ def test_inexact_matches_oracle(fm, z, gaps):
     _inexact_case(fm, R, reads, z, gaps, 64)
 
 
-@pytest.mark.parametrize("interval", [128, 256])
+@pytest.mark.parametrize("interval", [32, 128, 256])
 def test_inexact_intervals(fm, interval):
     R = synth.repeat_text(11, 200_000, families=20, min_len=300, max_len=3000)
     reads = synth.sample_reads(12, R, 300, 30, 100, sub_rate=0.02, both_strands=True)
