@@ -289,31 +289,47 @@ __global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk
             }
         }
         if (etop >= 32 || (etop > 0 && gtop == 0 && stop == 0)) {
-            // exact steps
-            const int take = etop < 32 ? etop : 32;
-            const bool act = lane < take;
-            uint4 nd = make_uint4(0, 0, 0, 0), ch = make_uint4(0, 0, 0, 0);
-            if (act) nd = st[stk - etop + lane];
+            // exact steps: up to 64 E nodes, two per lane, their gathers in flight together
+            const int take = etop < 64 ? etop : 64;
+            const bool a0 = lane < take, a1 = lane + 32 < take;
+            uint4 n0 = make_uint4(0, 0, 0, 0), n1 = make_uint4(0, 0, 0, 0);
+            if (a0) n0 = st[stk - etop + lane];
+            if (a1) n1 = st[stk - etop + 32 + lane];
             etop -= take;
             __syncwarp();
-            bool survive = false, is_leaf = false;
-            if (act) {
-                const uint4 mt = c.qmeta[nd.x];
-                uint32_t nb = 0;
-                exact_step<I>(c, nd, mt, ch, survive, is_leaf, nb);
-                my_nodes += 1;
-                my_blocks += nb;
+            uint4 c0 = make_uint4(0, 0, 0, 0), c1 = make_uint4(0, 0, 0, 0);
+            bool s0 = false, s1 = false, f0 = false, f1 = false;
+            {
+                uint4 m0 = make_uint4(0, 0, 0, 0), m1 = make_uint4(0, 0, 0, 0);
+                if (a0) m0 = c.qmeta[n0.x];
+                if (a1) m1 = c.qmeta[n1.x];
+                uint32_t b0 = 0, b1 = 0;
+                if (a0) {
+                    exact_step<I>(c, n0, m0, c0, s0, f0, b0);
+                    my_nodes += 1;
+                    my_blocks += b0;
+                }
+                if (a1) {
+                    exact_step<I>(c, n1, m1, c1, s1, f1, b1);
+                    my_nodes += 1;
+                    my_blocks += b1;
+                }
             }
-            const uint32_t bal = __ballot_sync(FULL, survive);
-            if (survive) st[stk - 1 - (etop + __popc(bal & lt_mask))] = ch;
-            etop += __popc(bal);
-            const uint32_t lb = __ballot_sync(FULL, is_leaf);
-            if (lb) {
+            const uint32_t bal0 = __ballot_sync(FULL, s0);
+            const uint32_t bal1 = __ballot_sync(FULL, s1);
+            if (s0) st[stk - 1 - (etop + __popc(bal0 & lt_mask))] = c0;
+            if (s1) st[stk - 1 - (etop + __popc(bal0) + __popc(bal1 & lt_mask))] = c1;
+            etop += __popc(bal0) + __popc(bal1);
+            const uint32_t lb0 = __ballot_sync(FULL, f0), lb1 = __ballot_sync(FULL, f1);
+            if (lb0 | lb1) {
                 unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(c.raw_count, (unsigned long long)__popc(lb));
+                if (lane == 0)
+                    base = atomicAdd(c.raw_count, (unsigned long long)(__popc(lb0) + __popc(lb1)));
                 base = __shfl_sync(FULL, base, 0);
-                const uint64_t pos = base + __popc(lb & lt_mask);
-                if (is_leaf && pos < c.raw_cap) c.raw[pos] = make_uint4(nd.x, ch.z, ch.w, 0u);
+                const uint64_t p0 = base + __popc(lb0 & lt_mask);
+                const uint64_t p1 = base + __popc(lb0) + __popc(lb1 & lt_mask);
+                if (f0 && p0 < c.raw_cap) c.raw[p0] = make_uint4(n0.x, c0.z, c0.w, 0u);
+                if (f1 && p1 < c.raw_cap) c.raw[p1] = make_uint4(n1.x, c1.z, c1.w, 0u);
             }
             __syncwarp();
             continue;
@@ -903,7 +919,7 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
     const uint32_t I = h->interval;
     const Tuning &tu = h->tune;
     const int block = (int)tu.warps_per_block * 32;
-    const int stk = 352;   // pool entries per warp: >= 288 (children of 32 nodes) + 32
+    const int stk = 320;   // pool entries per warp: G + E never exceed 31 + 288 (see the kernel)
     const size_t smem = (size_t)(block / 32) * stk * sizeof(uint4);
     cudaError_t e = I == 32 ? set_smem_attr<32>(smem) : (I == 64 ? set_smem_attr<64>(smem) : (I == 128 ? set_smem_attr<128>(smem)
                                                                   : set_smem_attr<256>(smem)));

@@ -131,9 +131,10 @@ enum ErrBits : uint32_t {
 // device helpers
 // -----------------------------------------------------------------------------------------
 
-// 256-bit read-only load of one 32-byte sector (sm_100+ PTX).
+// 256-bit read-only load of one 32-byte sector (sm_100+ PTX).  Not volatile: the tables are
+// read-only while a kernel runs, so the compiler may hoist and batch these loads.
 __device__ __forceinline__ void ldg256(const void *p, uint4 &a, uint4 &b) {
-    asm volatile("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+    asm("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                  : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z),
                    "=r"(b.w)
                  : "l"(p));
