@@ -136,6 +136,8 @@ typedef struct fm_profile {
     float ms_total;    /* whole call, first launch to last */
     uint32_t launches; /* kernels launched by the call */
     uint32_t passes;   /* search passes (1 unless scratch was regrown) */
+    uint32_t graph;    /* 1 when the call replayed a captured CUDA graph, 0 when eager */
+    uint32_t reserved;
 } fm_profile;
 
 /* Inexact search options. */
@@ -222,6 +224,9 @@ typedef struct fm_tuning {
     uint32_t blocks_per_sm;     /* persistent kernel: resident CTAs per SM (occupancy) */
     uint32_t chunk;             /* queries a warp takes from the work queue at once (1..32) */
     uint32_t plain_block;       /* plain kernel threads per CTA (a multiple of 32, <= 256) */
+    uint32_t graphs;            /* 1: run the persistent search as a CUDA graph (captured on the
+                                   first call with given buffers and sizes, replayed after);
+                                   2: always launch eagerly */
 } fm_tuning;
 
 int fm_set_tuning(fm_index *h, const fm_tuning *t);

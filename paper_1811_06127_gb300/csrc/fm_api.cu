@@ -115,6 +115,10 @@ void release(fm_index *h) {
     fm::Scratch *ss[] = {&h->s_qmeta, &h->s_raw, &h->s_spill, &h->s_group, &h->s_scan, &h->s_plain,
                          &h->s_misc};
     for (auto *s : ss) cudaFree(s->ptr);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (auto &e : h->gev)
+        if (e) cudaEventDestroy(e);
     delete h;
 }
 
@@ -450,6 +454,8 @@ int fm_set_tuning(fm_index *h, const fm_tuning *t) {
     if (t->blocks_per_sm) h->tune.blocks_per_sm = t->blocks_per_sm;
     if (t->chunk) h->tune.chunk = t->chunk;
     if (t->plain_block) h->tune.plain_block = t->plain_block;
+    if (t->graphs > 2) return set_error(h, FM_EINVAL, "graphs must be 0, 1 or 2");
+    if (t->graphs) h->use_graphs = t->graphs == 1;
     return FM_OK;
 }
 
@@ -460,6 +466,7 @@ int fm_get_tuning(const fm_index *h, fm_tuning *t) {
     t->blocks_per_sm = h->tune.blocks_per_sm;
     t->chunk = h->tune.chunk;
     t->plain_block = h->tune.plain_block;
+    t->graphs = h->use_graphs ? 1u : 2u;
     return FM_OK;
 }
 

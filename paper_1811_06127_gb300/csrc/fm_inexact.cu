@@ -510,14 +510,19 @@ __global__ void __launch_bounds__(256) k_inexact_plain(SearchCfg c, uint4 *stack
 // ------------------------------------------------------------------------------------------
 // canonical result sets
 // ------------------------------------------------------------------------------------------
-__global__ void k_hist(const uint4 *__restrict__ raw, uint64_t R, uint32_t *__restrict__ cnt) {
+// raw results: R = min(*d_R, cap) read on the device, so the launch needs no host sync
+__global__ void k_hist(const uint4 *__restrict__ raw, const unsigned long long *__restrict__ d_R,
+                       uint64_t cap, uint32_t *__restrict__ cnt) {
+    const uint64_t R = *d_R < cap ? *d_R : cap;
     for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < R;
          e += (uint64_t)gridDim.x * blockDim.x)
         atomicAdd(cnt + raw[e].x, 1u);
 }
 
-__global__ void k_scatter(const uint4 *__restrict__ raw, uint64_t R, const uint64_t *__restrict__ start,
+__global__ void k_scatter(const uint4 *__restrict__ raw, const unsigned long long *__restrict__ d_R,
+                          uint64_t cap, const uint64_t *__restrict__ start,
                           uint32_t *__restrict__ cursor, uint64_t *__restrict__ grouped) {
+    const uint64_t R = *d_R < cap ? *d_R : cap;
     for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < R;
          e += (uint64_t)gridDim.x * blockDim.x) {
         const uint4 v = raw[e];
@@ -640,9 +645,12 @@ __global__ void k_sort_large(const uint32_t *__restrict__ large, const uint32_t 
     }
 }
 
+// writes nothing unless the total (offsets[nq]) fits the caller's capacity
 __global__ void k_compact(uint32_t nq, const uint32_t *__restrict__ ucnt,
                           const uint64_t *__restrict__ start, const uint64_t *__restrict__ offsets,
-                          const uint64_t *__restrict__ grouped, uint32_t *__restrict__ pairs) {
+                          const uint64_t *__restrict__ grouped, uint32_t *__restrict__ pairs,
+                          uint64_t capacity) {
+    if (offsets[nq] > capacity) return;
     const int lane = threadIdx.x & 31;
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += warps) {
@@ -657,13 +665,30 @@ __global__ void k_compact(uint32_t nq, const uint32_t *__restrict__ ucnt,
     }
 }
 
+// adds this call's counters to the caller's, unless the pass overflowed (it is then rerun)
 __global__ void k_add_stats(const unsigned long long *__restrict__ in,
                             const unsigned long long *__restrict__ raw,
-                            unsigned long long *__restrict__ out) {
+                            unsigned long long *__restrict__ out, uint64_t raw_cap,
+                            const uint32_t *__restrict__ err) {
+    if (*raw > raw_cap || (*err & (kErrSpill | kErrStack))) return;
     if (threadIdx.x == 0) {
         out[0] += in[0];
         out[1] += in[1];
         out[2] += *raw;
+    }
+}
+
+// the scalars the host reads after a captured search: raw count, search and D error words,
+// large segments and the interval total
+__global__ void k_status(const unsigned long long *__restrict__ raw, const uint32_t *__restrict__ err,
+                         const uint32_t *__restrict__ nlarge, const uint64_t *__restrict__ total,
+                         unsigned long long *__restrict__ out) {
+    if (threadIdx.x == 0) {
+        out[0] = *raw;
+        out[1] = err[kErrSearch];
+        out[2] = err[kErrDcalc];
+        out[3] = *nlarge;
+        out[4] = *total;
     }
 }
 
@@ -862,15 +887,225 @@ int fetch_inexact(fm_index *h, uint32_t *pairs, uint64_t pair_capacity, cudaStre
     const uint32_t nq = h->last_nq;
     k_compact<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, st>>>(
         nq, (const uint32_t *)(gb + h->last_off_ucnt), (const uint64_t *)(gb + h->last_off_start),
-        (const uint64_t *)(gb + h->last_off_uoff), (const uint64_t *)(gb + h->last_off_grp), pairs);
+        (const uint64_t *)(gb + h->last_off_uoff), (const uint64_t *)(gb + h->last_off_grp), pairs,
+        pair_capacity);
     FM_CUDA_TRY(h, cudaGetLastError());
     FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+    return FM_OK;
+}
+
+// Group scratch layout for up to R raw results.
+struct GroupLayout {
+    size_t cnt, cur, ucnt, large, start, uoff, tiles, grp, tmp, total;
+    GroupLayout(uint32_t nq, uint64_t R) {
+        const uint64_t ntiles = (nq + kScanTile - 1) / kScanTile + 2;
+        cnt = 0;
+        cur = cnt + (size_t)nq * 4;
+        ucnt = cur + (size_t)nq * 4;
+        large = ucnt + (size_t)nq * 4;
+        start = (large + (size_t)nq * 4 + 15) / 16 * 16;
+        uoff = start + ((size_t)nq + 1) * 8;
+        tiles = uoff + ((size_t)nq + 1) * 8;
+        grp = tiles + ntiles * 8;
+        tmp = grp + (R ? R : 1) * 8;
+        total = tmp + (R ? R : 1) * 8;
+    }
+};
+
+// The persistent search of one call as a CUDA graph: D pass, search, grouping, sorting,
+// deduplication and compaction, with every size the host used to read in between taken on the
+// device (raw count, large segments, pair total), so the whole call is one graph launch and one
+// status read.  The graph is captured on a private stream the first time a key is seen (same
+// buffers, sizes and parameters) and replayed on the caller's stream afterwards.  It needs
+// scratch already sized by an earlier eager call; when the replayed pass overflows the raw
+// buffer or a spill region, *fallback is set and the eager path regrows and reruns.
+static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *offs,
+                             uint32_t n_reads, const fm_search_params *sp, uint32_t *counts,
+                             uint64_t *offsets, uint32_t *pairs, uint64_t pair_capacity,
+                             uint64_t *pairs_needed, cudaStream_t st, bool *fallback) {
+    *fallback = true;
+    const uint32_t nq = n_reads * sp->strands;
+    const uint32_t I = h->interval;
+    const Tuning &tu = h->tune;
+    const int block = (int)tu.warps_per_block * 32;
+    const int stk = 320;
+    const size_t smem = (size_t)(block / 32) * stk * sizeof(uint4);
+    int bps = (int)tu.blocks_per_sm;
+    const int occ = I == 32 ? occupancy_blocks<32>(block, smem) : I == 64 ? occupancy_blocks<64>(block, smem)
+                            : (I == 128 ? occupancy_blocks<128>(block, smem) : occupancy_blocks<256>(block, smem));
+    if (bps <= 0 || bps > occ) bps = occ;
+    if (bps <= 0) return FM_OK;
+    const int grid = h->sms * bps;
+    const uint64_t nwarps = (uint64_t)grid * (block / 32);
+    if (!h->s_raw.ptr || !h->s_spill.ptr || !h->s_misc.ptr) return FM_OK;   // not sized yet
+    const uint64_t raw_cap = h->s_raw.bytes / sizeof(uint4);
+    const uint32_t spill_cap = (uint32_t)(h->s_spill.bytes / sizeof(uint4) / nwarps);
+    if (raw_cap < (uint64_t)nq * 4 || spill_cap < 4096) return FM_OK;
+    int rc;
+    if ((rc = ensure_scratch(h, h->s_qmeta, (size_t)nq * sizeof(uint4)))) return rc;
+    const GroupLayout L(nq, raw_cap);
+    if ((rc = ensure_scratch(h, h->s_group, L.total))) return rc;
+    if (!h->cap_stream) FM_CUDA_TRY(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    fm_profile *prof = sp->profile;
+    if (prof && !h->gev[0])
+        for (auto &e : h->gev) FM_CUDA_TRY(h, cudaEventCreate(&e));
+
+    GraphKey key{};
+    key.reads = reads; key.offs = offs; key.counts = counts; key.offsets = offsets;
+    key.pairs = pairs; key.stats = sp->stats; key.qmeta = h->s_qmeta.ptr; key.raw = h->s_raw.ptr;
+    key.spill = h->s_spill.ptr; key.group = h->s_group.ptr; key.misc = h->s_misc.ptr;
+    key.pair_capacity = pair_capacity; key.raw_cap = raw_cap; key.n_reads = n_reads;
+    key.strands = sp->strands; key.z = sp->z; key.max_gaps = sp->max_gaps; key.interval = I;
+    key.grid = (uint32_t)grid; key.block = (uint32_t)block; key.chunk = tu.chunk;
+    key.spill_cap = spill_cap; key.profile = prof ? 1u : 0u;
+
+    char *misc = (char *)h->s_misc.ptr;
+    unsigned long long *d_raw_count = (unsigned long long *)misc;
+    uint32_t *d_next_q = (uint32_t *)(misc + 8);
+    uint32_t *d_nlarge = (uint32_t *)(misc + 12);
+    unsigned long long *d_stats = (unsigned long long *)(misc + 32);
+    unsigned long long *d_status = (unsigned long long *)(misc + 64);
+    char *gb = (char *)h->s_group.ptr;
+    uint32_t *cnt = (uint32_t *)(gb + L.cnt), *cursor = (uint32_t *)(gb + L.cur),
+             *ucnt = (uint32_t *)(gb + L.ucnt), *large = (uint32_t *)(gb + L.large);
+    uint64_t *start = (uint64_t *)(gb + L.start), *uoff = (uint64_t *)(gb + L.uoff),
+             *tiles = (uint64_t *)(gb + L.tiles), *grouped = (uint64_t *)(gb + L.grp),
+             *tmp = (uint64_t *)(gb + L.tmp);
+
+    if (!(h->gexec && h->gkey == key)) {
+        if (h->gexec) {
+            cudaGraphExecDestroy(h->gexec);
+            h->gexec = nullptr;
+        }
+        cudaError_t e = I == 32 ? set_smem_attr<32>(smem) : (I == 64 ? set_smem_attr<64>(smem)
+                        : (I == 128 ? set_smem_attr<128>(smem) : set_smem_attr<256>(smem)));
+        if (e != cudaSuccess) return cuda_status(h, e, "cudaFuncSetAttribute");
+        FM_CUDA_TRY(h, cudaFuncSetAttribute(k_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(8192 * sizeof(uint64_t))));
+        cudaStream_t cs = h->cap_stream;
+        FM_CUDA_TRY(h, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        uint32_t launches = 0;
+        int crc = FM_OK;
+        do {
+            if (prof && cudaEventRecordWithFlags(h->gev[0], cs, cudaEventRecordExternal)) { crc = FM_ECUDA; break; }
+            if (cudaMemsetAsync(h->d_err + kErrDcalc, 0, 8, cs)) { crc = FM_ECUDA; break; }
+            if ((crc = launch_dcalc(h, reads, offs, n_reads, sp->strands, (uint4 *)h->s_qmeta.ptr, nullptr, cs))) break;
+            ++launches;
+            if (prof && cudaEventRecordWithFlags(h->gev[1], cs, cudaEventRecordExternal)) { crc = FM_ECUDA; break; }
+            if (cudaMemsetAsync(misc, 0, 64, cs)) { crc = FM_ECUDA; break; }
+            SearchCfg c;
+            c.ix = view_fwd(h);
+            c.reads = reads;
+            c.qmeta = (const uint4 *)h->s_qmeta.ptr;
+            c.nq = nq;
+            c.z = sp->z;
+            c.max_gaps = sp->max_gaps;
+            c.chunk = tu.chunk;
+            c.next_q = d_next_q;
+            c.raw = (uint4 *)h->s_raw.ptr;
+            c.raw_count = d_raw_count;
+            c.raw_cap = raw_cap;
+            c.stats = d_stats;
+            c.err = h->d_err + kErrSearch;
+            switch (I) {
+                case 32: crc = launch_search<32>(h, c, FM_KERNEL_PERSISTENT, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, nullptr, 0, 0, cs); break;
+                case 64: crc = launch_search<64>(h, c, FM_KERNEL_PERSISTENT, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, nullptr, 0, 0, cs); break;
+                case 128: crc = launch_search<128>(h, c, FM_KERNEL_PERSISTENT, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, nullptr, 0, 0, cs); break;
+                default: crc = launch_search<256>(h, c, FM_KERNEL_PERSISTENT, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, nullptr, 0, 0, cs); break;
+            }
+            if (crc) break;
+            ++launches;
+            if (prof && cudaEventRecordWithFlags(h->gev[2], cs, cudaEventRecordExternal)) { crc = FM_ECUDA; break; }
+            if (cudaMemsetAsync(cnt, 0, (size_t)nq * 8, cs)) { crc = FM_ECUDA; break; }
+            const uint4 *raw = (const uint4 *)h->s_raw.ptr;
+            k_hist<<<grid_cap(h, raw_cap, 256), 256, 0, cs>>>(raw, d_raw_count, raw_cap, cnt);
+            if ((crc = scan_u32(h, cnt, nq, start, tiles, cs))) break;
+            k_scatter<<<grid_cap(h, raw_cap, 256), 256, 0, cs>>>(raw, d_raw_count, raw_cap, start, cursor, grouped);
+            k_sort_small<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, cs>>>(nq, cnt, start, grouped, ucnt, large, d_nlarge);
+            k_sort_large<<<(unsigned)h->sms * 4, 512, 8192 * sizeof(uint64_t), cs>>>(large, d_nlarge, cnt, start, grouped, tmp, ucnt);
+            launches += 2 + 3 + 2;
+            if ((crc = scan_u32(h, ucnt, nq, uoff, tiles, cs))) break;
+            if (cudaMemcpyAsync(offsets, uoff, ((size_t)nq + 1) * 8, cudaMemcpyDeviceToDevice, cs)) { crc = FM_ECUDA; break; }
+            k_copy_counts<<<grid_cap(h, nq, 256), 256, 0, cs>>>(nq, ucnt, counts);
+            k_compact<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, cs>>>(nq, ucnt, start, uoff, grouped, pairs, pair_capacity);
+            launches += 3 + 2;
+            if (sp->stats) {
+                k_add_stats<<<1, 32, 0, cs>>>(d_stats, d_raw_count, (unsigned long long *)sp->stats, raw_cap, h->d_err);
+                ++launches;
+            }
+            k_status<<<1, 32, 0, cs>>>(d_raw_count, h->d_err, d_nlarge, uoff + nq, d_status);
+            ++launches;
+            if (prof && cudaEventRecordWithFlags(h->gev[3], cs, cudaEventRecordExternal)) { crc = FM_ECUDA; break; }
+            if (cudaGetLastError() != cudaSuccess) crc = FM_ECUDA;
+        } while (0);
+        cudaGraph_t graph = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+        if (crc || ee != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return FM_OK;   // capture failed: the eager path runs the call
+        }
+        ee = cudaGraphInstantiate(&h->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ee != cudaSuccess) {
+            h->gexec = nullptr;
+            cudaGetLastError();
+            return FM_OK;
+        }
+        h->gkey = key;
+        h->glaunches = launches;
+        h->graph_captures += 1;
+    }
+    FM_CUDA_TRY(h, cudaGraphLaunch(h->gexec, st));
+    h->graph_replays += 1;
+    unsigned long long status[5] = {0, 0, 0, 0, 0};
+    FM_CUDA_TRY(h, cudaMemcpyAsync(status, d_status, sizeof(status), cudaMemcpyDeviceToHost, st));
+    FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+    const uint64_t rawn = status[0], need = status[4];
+    const uint32_t errs = (uint32_t)status[1], errd = (uint32_t)status[2];
+    if (rawn > raw_cap || (errs & (kErrSpill | kErrStack))) return FM_OK;   // regrow eagerly
+    *fallback = false;
+    h->last_nq = nq;
+    h->last_total = need;
+    h->last_off_ucnt = L.ucnt;
+    h->last_off_start = L.start;
+    h->last_off_uoff = L.uoff;
+    h->last_off_grp = L.grp;
+    h->last_valid = true;
+    if (pairs_needed) *pairs_needed = need;
+    if (prof) {
+        memset(prof, 0, sizeof(*prof));
+        float a = 0, b = 0, cc = 0, d = 0;
+        FM_CUDA_TRY(h, cudaEventElapsedTime(&a, h->gev[0], h->gev[1]));
+        FM_CUDA_TRY(h, cudaEventElapsedTime(&b, h->gev[1], h->gev[2]));
+        FM_CUDA_TRY(h, cudaEventElapsedTime(&cc, h->gev[2], h->gev[3]));
+        FM_CUDA_TRY(h, cudaEventElapsedTime(&d, h->gev[0], h->gev[3]));
+        prof->ms_dcalc = a;
+        prof->ms_search = b;
+        prof->ms_canon = cc;
+        prof->ms_total = d;
+        prof->launches = h->glaunches;
+        prof->passes = 1;
+        prof->graph = 1;
+    }
+    if (errd & kErrReadLen) return set_error(h, FM_EINVAL, "a read is longer than 255 symbols");
+    if (errd & kErrDomain) return set_error(h, FM_EINVAL, "a read holds a code above 3");
+    if (need > pair_capacity)
+        return set_error(h, FM_ETRUNC, "pair capacity " + std::to_string(pair_capacity) +
+                                           " below the " + std::to_string(need) + " intervals found");
     return FM_OK;
 }
 
 int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
                 const fm_search_params *sp, uint32_t *counts, uint64_t *offsets, uint32_t *pairs,
                 uint64_t pair_capacity, uint64_t *pairs_needed, cudaStream_t st) {
+    if (h->use_graphs && sp->kernel != FM_KERNEL_PLAIN && n_reads > 0) {
+        bool fallback = true;
+        const int grc = run_inexact_graph(h, reads, offs, n_reads, sp, counts, offsets, pairs,
+                                          pair_capacity, pairs_needed, st, &fallback);
+        if (!fallback) return grc;
+        if (grc) return grc;
+    }
     const uint32_t strands = sp->strands;
     const uint64_t nq64 = (uint64_t)n_reads * strands;
     if (nq64 > 0xffffffffull) return set_error(h, FM_EINVAL, "too many queries");
@@ -1020,9 +1255,9 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
                      *tmp = (uint64_t *)(gb + off_tmp);
             FM_CUDA_TRY(h, cudaMemsetAsync(cnt, 0, (size_t)nq * 8, st));   // cnt and cursor
             const uint4 *raw = (const uint4 *)h->s_raw.ptr;
-            if (R) k_hist<<<grid_cap(h, R, 256), 256, 0, st>>>(raw, R, cnt);
+            if (R) k_hist<<<grid_cap(h, R, 256), 256, 0, st>>>(raw, d_raw_count, raw_cap, cnt);
             if ((rc = scan_u32(h, cnt, nq, start, tiles, st))) return rc;
-            if (R) k_scatter<<<grid_cap(h, R, 256), 256, 0, st>>>(raw, R, start, cursor, grouped);
+            if (R) k_scatter<<<grid_cap(h, R, 256), 256, 0, st>>>(raw, d_raw_count, raw_cap, start, cursor, grouped);
             k_sort_small<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, st>>>(nq, cnt, start, grouped, ucnt, large, d_nlarge);
             FM_CUDA_TRY(h, cudaGetLastError());
             launches += (R ? 2u : 0u) + 3u + 1u;
@@ -1054,7 +1289,8 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
             h->last_off_grp = off_grp;
             h->last_valid = true;
             if (sp->stats) {
-                k_add_stats<<<1, 32, 0, st>>>(d_stats, d_raw_count, (unsigned long long *)sp->stats);
+                k_add_stats<<<1, 32, 0, st>>>(d_stats, d_raw_count, (unsigned long long *)sp->stats,
+                                              raw_cap, h->d_err);
                 FM_CUDA_TRY(h, cudaGetLastError());
                 ++launches;
             }
@@ -1064,7 +1300,8 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
                                                    " below the " + std::to_string(need) + " intervals found");
             }
             if (need) {
-                k_compact<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, st>>>(nq, ucnt, start, uoff, grouped, pairs);
+                k_compact<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, st>>>(nq, ucnt, start, uoff, grouped, pairs,
+                                                                                pair_capacity);
                 FM_CUDA_TRY(h, cudaGetLastError());
                 ++launches;
             }
@@ -1230,9 +1467,9 @@ int run_inexact_noalloc(fm_index *h, const uint8_t *reads, const uint32_t *offs,
     const uint64_t R = rawn;
     FM_CUDA_TRY(h, cudaMemsetAsync(cnt, 0, (size_t)nq * 4, st));
     FM_CUDA_TRY(h, cudaMemsetAsync(cursor, 0, (size_t)nq * 4, st));
-    if (R) k_hist<<<grid_cap(h, R, 256), 256, 0, st>>>(raw, R, cnt);
+    if (R) k_hist<<<grid_cap(h, R, 256), 256, 0, st>>>(raw, d_raw_count, kNoAllocMaxRaw, cnt);
     if ((rc = scan_u32(h, cnt, nq, start, tiles, st))) return rc;
-    if (R) k_scatter<<<grid_cap(h, R, 256), 256, 0, st>>>(raw, R, start, cursor, grouped);
+    if (R) k_scatter<<<grid_cap(h, R, 256), 256, 0, st>>>(raw, d_raw_count, kNoAllocMaxRaw, start, cursor, grouped);
     k_sort_small<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, st>>>(nq, cnt, start, grouped,
                                                                        ucnt, large, d_nlarge);
     FM_CUDA_TRY(h, cudaGetLastError());
@@ -1256,7 +1493,8 @@ int run_inexact_noalloc(fm_index *h, const uint8_t *reads, const uint32_t *offs,
     FM_CUDA_TRY(h, cudaStreamSynchronize(st));
     if (pairs_needed) *pairs_needed = need;
     if (sp->stats) {
-        k_add_stats<<<1, 32, 0, st>>>(d_stats, d_raw_count, (unsigned long long *)sp->stats);
+        k_add_stats<<<1, 32, 0, st>>>(d_stats, d_raw_count, (unsigned long long *)sp->stats,
+                                      kNoAllocMaxRaw, h->d_err);
         FM_CUDA_TRY(h, cudaGetLastError());
     }
     if (need > pair_capacity) {
@@ -1266,7 +1504,7 @@ int run_inexact_noalloc(fm_index *h, const uint8_t *reads, const uint32_t *offs,
     }
     if (need) {
         k_compact<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, st>>>(nq, ucnt, start, uoff,
-                                                                        grouped, pairs);
+                                                                        grouped, pairs, pair_capacity);
         FM_CUDA_TRY(h, cudaGetLastError());
     }
     uint32_t derr = 0;

@@ -45,6 +45,23 @@ struct Scratch {
     size_t bytes = 0;
 };
 
+// What a captured search graph depends on; a call with another key captures a new graph.
+struct GraphKey {
+    const void *reads, *offs, *counts, *offsets, *pairs, *stats;
+    const void *qmeta, *raw, *spill, *group, *misc;
+    uint64_t pair_capacity, raw_cap;
+    uint32_t n_reads, strands, z, max_gaps, interval, grid, block, chunk, spill_cap, profile;
+    bool operator==(const GraphKey &o) const {
+        return reads == o.reads && offs == o.offs && counts == o.counts && offsets == o.offsets &&
+               pairs == o.pairs && stats == o.stats && qmeta == o.qmeta && raw == o.raw &&
+               spill == o.spill && group == o.group && misc == o.misc &&
+               pair_capacity == o.pair_capacity && raw_cap == o.raw_cap && n_reads == o.n_reads &&
+               strands == o.strands && z == o.z && max_gaps == o.max_gaps &&
+               interval == o.interval && grid == o.grid && block == o.block && chunk == o.chunk &&
+               spill_cap == o.spill_cap && profile == o.profile;
+    }
+};
+
 struct Tuning {
     uint32_t warps_per_block = 8;
     uint32_t blocks_per_sm = 0;     // 0: from the occupancy calculator
@@ -79,6 +96,14 @@ struct fm_index {
     uint64_t last_total = 0;
     bool last_valid = false;
     size_t last_off_ucnt = 0, last_off_start = 0, last_off_uoff = 0, last_off_grp = 0;
+    // CUDA graph of the persistent search call (captured once per key, replayed after)
+    bool use_graphs = true;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    fm::GraphKey gkey{};
+    uint32_t glaunches = 0;
+    cudaEvent_t gev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    uint64_t graph_replays = 0, graph_captures = 0;
 };
 
 namespace fm {

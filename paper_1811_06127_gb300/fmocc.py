@@ -43,7 +43,8 @@ class fm_info_t(C.Structure):
 
 class fm_profile(C.Structure):
     _fields_ = [("ms_dcalc", C.c_float), ("ms_search", C.c_float), ("ms_canon", C.c_float),
-                ("ms_total", C.c_float), ("launches", C.c_uint32), ("passes", C.c_uint32)]
+                ("ms_total", C.c_float), ("launches", C.c_uint32), ("passes", C.c_uint32),
+                ("graph", C.c_uint32), ("reserved", C.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -57,7 +58,7 @@ class fm_search_params(C.Structure):
 
 class fm_tuning(C.Structure):
     _fields_ = [("warps_per_block", C.c_uint32), ("blocks_per_sm", C.c_uint32),
-                ("chunk", C.c_uint32), ("plain_block", C.c_uint32)]
+                ("chunk", C.c_uint32), ("plain_block", C.c_uint32), ("graphs", C.c_uint32)]
 
 
 # every symbol include/fmocc.h declares
@@ -342,8 +343,10 @@ def fm_inexact_fetch(h: Index, pairs: torch.Tensor, stream=None):
     return pairs
 
 
-def fm_set_tuning(h: Index, warps_per_block=0, blocks_per_sm=0, chunk=0, plain_block=0):
-    t = fm_tuning(warps_per_block, blocks_per_sm, chunk, plain_block)
+def fm_set_tuning(h: Index, warps_per_block=0, blocks_per_sm=0, chunk=0, plain_block=0,
+                  graphs=0):
+    """Zero keeps a knob; graphs: 1 on, 2 off."""
+    t = fm_tuning(warps_per_block, blocks_per_sm, chunk, plain_block, graphs)
     _check(load_library().fm_set_tuning(h.ptr, C.byref(t)), h)
 
 
@@ -351,7 +354,7 @@ def fm_get_tuning(h: Index) -> dict:
     t = fm_tuning()
     _check(load_library().fm_get_tuning(h.ptr, C.byref(t)), h)
     return {"warps_per_block": t.warps_per_block, "blocks_per_sm": t.blocks_per_sm,
-            "chunk": t.chunk, "plain_block": t.plain_block}
+            "chunk": t.chunk, "plain_block": t.plain_block, "graphs": t.graphs}
 
 
 # ---------------------------------------------------------------------------------------------
