@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--autotune", type=int, default=1, help="1: tune interval/occupancy/chunk")
+    ap.add_argument("--tune-reads", type=int, default=200_000)
+    ap.add_argument("--tune-cache", default=None, help="JSON cache of tuning results")
     ap.add_argument("--cpu-sample-reads", type=int, default=200_000)
     ap.add_argument("--cpu-sample-ref", type=int, default=32_000_000)
     ap.add_argument("--log", default=None, help="also append the JSON line to this file")
@@ -242,13 +245,22 @@ def main():
     R = synth.repeat_text(SEED_SEARCH, args.ref_n)
     notes["ref_gen_s"] = time.time() - t0
     t0 = time.time()
-    h = fmocc.fm_build(R, interval=args.interval, device=local)
-    torch.cuda.synchronize()
-    notes["build_s"] = time.time() - t0
-    t0 = time.time()
     reads = synth.sample_reads(SEED_SEARCH + 1000 * rank, R, args.reads, 50, 250, sub_rate=0.01,
                                indel_rate=0.0005, both_strands=True)
     notes["reads_gen_s"] = time.time() - t0
+    tuned = None
+    if args.autotune:
+        from paper_1811_06127_gb300 import autotune
+        tuned = autotune.autotune(R, reads, 2, 1, strands=2, device=local,
+                                  workload={"reads": "50-250 bp, 1% subst, 0.05% indel"},
+                                  sample_reads=args.tune_reads, cache_path=args.tune_cache)
+        args.interval = tuned["interval"]
+    t0 = time.time()
+    h = fmocc.fm_build(R, interval=args.interval, device=local)
+    torch.cuda.synchronize()
+    notes["build_s"] = time.time() - t0
+    if tuned:
+        autotune.apply(h, tuned)
     del R
     codes_h = torch.from_numpy(reads.codes).pin_memory()
     offs_h = torch.from_numpy(reads.offs.view(np.int32)).pin_memory()
@@ -375,6 +387,9 @@ def main():
                                 "kernel"),
                    "reference_bp": args.ref_n, "reads_per_step": args.reads,
                    "queries_per_step": nq, "interval": args.interval,
+                   "tuning": ({k: tuned[k] for k in ("interval", "warps_per_block",
+                                                      "blocks_per_sm", "chunk", "trials",
+                                                      "tune_seconds")} if tuned else None),
                    "parallelism": f"replicas x{world} (read sharding)",
                    "l2": "flushed between timed steps (256 MB write); index 2x1 GB > L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
