@@ -217,6 +217,65 @@ int fm_inexact_noalloc(fm_index *h, const uint8_t *reads, const uint32_t *offs, 
                        uint32_t *pairs, uint64_t pair_capacity, uint64_t *pairs_needed,
                        void *stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Serving: a request loop over a resident index (the paper has no serving layer; it states the
+ * search per read, Listing 1 and Listing 2, and this loop runs those searches for a stream of
+ * requests).  A server thread owned by the library keeps the index resident and forms device
+ * batches continuously: requests that arrive while a batch is on the GPU wait in a FIFO and
+ * are admitted into the next batch as its read slots and device-memory budget allow; one batch
+ * holds requests of one search mode (z, max_gaps), and requests of any size share it (their
+ * queries run together in the persistent kernel).  Each request's result is exactly what
+ * fm_inexact returns for that request alone.  While a server runs, no other call may use its
+ * index handle.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct fm_server fm_server;
+
+typedef struct fm_server_params {
+    uint32_t max_batch_reads; /* read slots per device batch (0: 262,144) */
+    uint32_t strands;         /* 1 or 2, for every request */
+    uint64_t frontier_budget; /* device bytes the search scratch of one batch may use
+                                 (0: 64 GiB); bounds the reads admitted per batch */
+    uint32_t kernel;          /* FM_KERNEL_* */
+    uint32_t reserved;
+} fm_server_params;
+
+/* Result of one request, owned by the server until fm_server_release. */
+typedef struct fm_server_result {
+    int32_t status;          /* FM_OK or the error of the batch that held the request */
+    uint32_t n_queries;      /* n_reads * strands */
+    const uint32_t *counts;  /* host [n_queries] */
+    const uint64_t *offsets; /* host [n_queries+1], from 0 */
+    const uint32_t *pairs;   /* host [2*offsets[n_queries]] (k, l), sorted per query */
+    uint64_t t_submit_ns;    /* steady-clock times: submission, batch start, completion */
+    uint64_t t_start_ns;
+    uint64_t t_done_ns;
+    uint32_t batch_reads;    /* reads in the batch that held the request */
+    uint32_t reserved;
+} fm_server_result;
+
+/* Start the server thread on h.  Errors: FM_EINVAL, FM_ENOMEM, FM_ECUDA. */
+int fm_server_start(fm_index *h, const fm_server_params *p, fm_server **out);
+
+/* Queue a request: reads are host memory (codes 0..3, concatenated, offs[n_reads+1]); they are
+ * copied before the call returns.  z <= 7, max_gaps <= 7, read lengths 1..255 (else FM_EINVAL).
+ * *ticket identifies the request. */
+int fm_server_submit(fm_server *s, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
+                     uint32_t z, uint32_t max_gaps, uint64_t *ticket);
+
+/* Wait up to wait_ms milliseconds (0: do not wait) for a request.  FM_OK fills *res;
+ * FM_ETIMEOUT when it is not done yet; FM_EINVAL for an unknown ticket. */
+int fm_server_poll(fm_server *s, uint64_t ticket, uint32_t wait_ms, fm_server_result *res);
+
+/* Drop a finished request's result memory. */
+int fm_server_release(fm_server *s, uint64_t ticket);
+
+/* Counters: batches run, reads searched, requests finished, GPU busy milliseconds. */
+int fm_server_stats(fm_server *s, uint64_t out[4]);
+
+/* Finish the queued requests, stop the thread and free the server (results not released are
+ * freed too).  NULL is ignored. */
+int fm_server_stop(fm_server *s);
+
 /* Tuning knobs of the search kernels (the autotuner writes them).  Zero fields keep the
  * current value.  Errors: FM_EINVAL for out-of-range values. */
 typedef struct fm_tuning {

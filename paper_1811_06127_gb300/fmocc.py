@@ -61,10 +61,25 @@ class fm_tuning(C.Structure):
                 ("chunk", C.c_uint32), ("plain_block", C.c_uint32), ("graphs", C.c_uint32)]
 
 
+class fm_server_params(C.Structure):
+    _fields_ = [("max_batch_reads", C.c_uint32), ("strands", C.c_uint32),
+                ("frontier_budget", C.c_uint64), ("kernel", C.c_uint32),
+                ("reserved", C.c_uint32)]
+
+
+class fm_server_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_queries", C.c_uint32),
+                ("counts", C.POINTER(C.c_uint32)), ("offsets", C.POINTER(C.c_uint64)),
+                ("pairs", C.POINTER(C.c_uint32)), ("t_submit_ns", C.c_uint64),
+                ("t_start_ns", C.c_uint64), ("t_done_ns", C.c_uint64),
+                ("batch_reads", C.c_uint32), ("reserved", C.c_uint32)]
+
+
 # every symbol include/fmocc.h declares
 EXPORTS = ["fm_build", "fm_free", "fm_last_error", "fm_info", "fm_get_bwt", "fm_save", "fm_load",
            "fm_occ8", "fm_exact", "fm_dcalc", "fm_inexact", "fm_inexact_fetch", "fm_set_tuning",
-           "fm_get_tuning", "fm_inexact_noalloc"]
+           "fm_get_tuning", "fm_inexact_noalloc", "fm_server_start", "fm_server_submit",
+           "fm_server_poll", "fm_server_release", "fm_server_stats", "fm_server_stop"]
 
 _lib = None
 
@@ -96,6 +111,12 @@ def load_library(path: str = LIB_PATH):
     lib.fm_inexact_noalloc.argtypes = [P, P, P, u32, C.POINTER(fm_search_params), P, P, P, u64,
                                        C.POINTER(C.c_uint64), P]
     lib.fm_set_tuning.argtypes = [P, C.POINTER(fm_tuning)]
+    lib.fm_server_start.argtypes = [P, C.POINTER(fm_server_params), C.POINTER(P)]
+    lib.fm_server_submit.argtypes = [P, P, P, u32, u32, u32, C.POINTER(C.c_uint64)]
+    lib.fm_server_poll.argtypes = [P, u64, u32, C.POINTER(fm_server_result)]
+    lib.fm_server_release.argtypes = [P, u64]
+    lib.fm_server_stats.argtypes = [P, P]
+    lib.fm_server_stop.argtypes = [P]
     lib.fm_get_tuning.argtypes = [P, C.POINTER(fm_tuning)]
     for name in EXPORTS:
         f = getattr(lib, name)
@@ -355,6 +376,75 @@ def fm_get_tuning(h: Index) -> dict:
     _check(load_library().fm_get_tuning(h.ptr, C.byref(t)), h)
     return {"warps_per_block": t.warps_per_block, "blocks_per_sm": t.blocks_per_sm,
             "chunk": t.chunk, "plain_block": t.plain_block, "graphs": t.graphs}
+
+
+class Server:
+    """Request loop over a resident index (fm_server_*): submit host read batches, poll for
+    their interval sets.  While it runs, the index handle belongs to the server."""
+
+    def __init__(self, h: Index, max_batch_reads: int = 0, strands: int = 2,
+                 frontier_budget: int = 0, kernel="persistent"):
+        self.lib = load_library()
+        self.h = h
+        self.strands = strands
+        kern = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        p = fm_server_params(max_batch_reads, strands, frontier_budget, kern, 0)
+        out = C.c_void_p()
+        _check(self.lib.fm_server_start(h.ptr, C.byref(p), C.byref(out)), h)
+        self.ptr = out
+
+    def submit(self, codes: np.ndarray, offs: np.ndarray, z: int, max_gaps: int = 0) -> int:
+        codes = np.ascontiguousarray(codes, dtype=np.uint8)
+        offs = np.ascontiguousarray(offs, dtype=np.uint32)
+        t = C.c_uint64(0)
+        _check(self.lib.fm_server_submit(self.ptr, codes.ctypes.data_as(C.c_void_p),
+                                         offs.ctypes.data_as(C.c_void_p), offs.size - 1, z,
+                                         max_gaps, C.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, wait_ms: int = 0):
+        """None while not done; else a dict with counts, offsets, pairs and times (ns)."""
+        r = fm_server_result()
+        rc = self.lib.fm_server_poll(self.ptr, ticket, wait_ms, C.byref(r))
+        if rc == FM_ETIMEOUT:
+            return None
+        _check(rc)
+        nq = r.n_queries
+        offsets = np.ctypeslib.as_array(r.offsets, shape=(nq + 1,)).copy()
+        tot = int(offsets[-1])
+        out = {"status": r.status,
+               "counts": (np.ctypeslib.as_array(r.counts, shape=(nq,)).copy() if nq
+                          else np.zeros(0, np.uint32)),
+               "offsets": offsets,
+               "pairs": (np.ctypeslib.as_array(r.pairs, shape=(2 * tot,)).reshape(tot, 2).copy()
+                         if tot else np.zeros((0, 2), np.uint32)),
+               "t_submit_ns": r.t_submit_ns, "t_start_ns": r.t_start_ns,
+               "t_done_ns": r.t_done_ns, "batch_reads": r.batch_reads}
+        _check(self.lib.fm_server_release(self.ptr, ticket))
+        return out
+
+    def wait(self, ticket: int, timeout_ms: int = 600_000):
+        res = self.poll(ticket, timeout_ms)
+        if res is None:
+            raise FmError(FM_ETIMEOUT, f"request {ticket} not done after {timeout_ms} ms")
+        return res
+
+    def stats(self):
+        a = np.zeros(4, dtype=np.uint64)
+        _check(self.lib.fm_server_stats(self.ptr, a.ctypes.data_as(C.c_void_p)))
+        return {"batches": int(a[0]), "reads": int(a[1]), "requests": int(a[2]),
+                "busy_ms": int(a[3])}
+
+    def stop(self):
+        if self.ptr and self.ptr.value:
+            self.lib.fm_server_stop(self.ptr)
+            self.ptr = C.c_void_p(None)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.stop()
 
 
 # ---------------------------------------------------------------------------------------------
