@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cfg3", action="store_true")
+    ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--autotune", type=int, default=1, help="1: tune interval/occupancy/chunk")
     ap.add_argument("--tune-reads", type=int, default=200_000)
     ap.add_argument("--tune-cache", default=None, help="JSON cache of tuning results")
@@ -362,6 +364,7 @@ def main():
         e2e = {"value": args.reads * args.steps * world / e_s, "unit": "reads/s",
                "h2d_bytes_per_step": codes_h.numel() + offs_h.numel() * 4,
                "d2h_bytes_per_step": int(d2h), "wall_s": time.perf_counter() - t0}
+    serving = None if args.skip_serving else bench_serving(args, fmocc, h, reads)
     h.close()
     del codes, offs, pairs
 
@@ -413,6 +416,7 @@ def main():
         "occ8": occ8,
         "exact": exact,
         "inexact_64mbp": cfg3,
+        "serving": serving,
         "cpu_baseline": cpu,
         "setup": notes,
     }
@@ -471,6 +475,66 @@ def bench_occ8(args, torch, fmocc, synth, dev, hbm_peak, peak_kind, flush, barri
                          "total_traffic_frac": (gather + io) / t / 1e9 / hbm_peak,
                          "blocks_per_query": blocks / args.occ_queries},
             "setup_s": setup_s}
+
+
+def bench_serving(args, fmocc, h, reads):
+    """Serving on the resident 2 Gbp index: requests of U[1, 4096] reads of the main read model,
+    mode uniform over {exact, z=1, z=2 with one gap}, both strands.  First the offline rate
+    (a backlog of requests submitted at once), then Poisson arrivals at 0.5x and 0.8x that rate
+    for a few seconds each; latency = completion - submission (library steady clock)."""
+    modes = [(0, 0), (1, 0), (2, 1)]
+    rng = np.random.default_rng(1811061275)
+    nr = len(reads)
+    cursor = [0]
+
+    def next_request():
+        m = int(rng.integers(1, 4097))
+        if cursor[0] + m > nr:
+            cursor[0] = 0
+        a = cursor[0]
+        cursor[0] += m
+        z, g = modes[int(rng.integers(0, 3))]
+        offs = reads.offs[a:a + m + 1]
+        return reads.codes[offs[0]:offs[-1]], offs - offs[0], z, g, m
+
+    out = {"requests": "U[1,4096] reads of 50-250 bp, mode uniform over exact / z=1 / z=2+1 gap",
+           "rates": []}
+    with fmocc.Server(h, max_batch_reads=262144, strands=2) as srv:
+        # offline: a backlog of requests
+        reqs = [next_request() for _ in range(200)]
+        t0 = time.perf_counter()
+        tk = [srv.submit(c, o, z, g) for c, o, z, g, _ in reqs]
+        res = [srv.wait(t) for t in tk]
+        dt = time.perf_counter() - t0
+        total = sum(r[4] for r in reqs)
+        offline = total / dt
+        out["offline_reads_per_s"] = offline
+        out["offline_batches"] = srv.stats()["batches"]
+        for load in (0.5, 0.8):
+            lam = load * offline / 2048.5            # requests per second
+            duration = args.serve_seconds
+            arrivals = np.cumsum(rng.exponential(1.0 / lam, size=int(lam * duration * 1.5) + 10))
+            arrivals = arrivals[arrivals < duration]
+            reqs = [next_request() for _ in range(arrivals.size)]
+            b0 = srv.stats()["batches"]
+            start = time.perf_counter()
+            tk = []
+            for (c, o, z, g, _), at in zip(reqs, arrivals):
+                delay = start + at - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tk.append(srv.submit(c, o, z, g))
+            res = [srv.wait(t) for t in tk]
+            end = time.perf_counter()
+            lat = np.array([(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r in res])
+            nreads = sum(r[4] for r in reqs)
+            out["rates"].append({"load": load, "offered_reads_per_s": load * offline,
+                                 "requests": len(reqs), "reads": nreads,
+                                 "achieved_reads_per_s": nreads / (end - start),
+                                 "p50_ms": float(np.percentile(lat, 50)),
+                                 "p99_ms": float(np.percentile(lat, 99)),
+                                 "batches": srv.stats()["batches"] - b0})
+    return out
 
 
 def bench_cfg3(args, torch, fmocc, synth, dev, flush, barrier, hbm_peak):
