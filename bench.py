@@ -365,6 +365,7 @@ def main():
                "h2d_bytes_per_step": codes_h.numel() + offs_h.numel() * 4,
                "d2h_bytes_per_step": int(d2h), "wall_s": time.perf_counter() - t0}
     serving = None if args.skip_serving else bench_serving(args, fmocc, h, reads)
+    ceil_main = gather_ceiling(torch, fmocc, dev, fmocc.fm_info(h)["n_blocks"] * bbytes, flush)
     h.close()
     del codes, offs, pairs
 
@@ -401,6 +402,9 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": None,
                      "kernel": "k_inexact_persistent", "kernel_ms": k_ms,
+                     "gather_ceiling": ceil_main,
+                     "blocks_per_s_over_gather_ceiling": (blocks_per_step / (k_ms / 1000) / 1e9
+                                                          / ceil_main["g_gathers_s"]),
                      "algorithmic_bytes": alg_bytes, "peak_kind": peak_kind,
                      "per_unit": f"{bbytes} B per checkpoint block read, "
                                  f"{blocks_per_step / max(nodes_per_step, 1):.3f} blocks per node, "
@@ -429,6 +433,32 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def gather_ceiling(torch, fmocc, dev, footprint, flush):
+    """Empirical random-gather ceiling: fm_probe_gather reads random 32-byte sectors of a
+    device buffer as large as the index (all SMs, full occupancy, 4 loads in flight per
+    thread); median of 5 launches."""
+    footprint = max(int(footprint) // 32 * 32, 1 << 20)
+    buf = torch.empty(footprint, dtype=torch.uint8, device=dev)
+    threads = torch.cuda.get_device_properties(dev).multi_processor_count * 2048
+    per = 64
+    sink = torch.empty(threads, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        fmocc.fm_probe_gather(buf, 32, threads, per, 7, sink)
+    ms = []
+    for r in range(5):
+        flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fmocc.fm_probe_gather(buf, 32, threads, per, 100 + r, sink)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = float(np.median(ms)) / 1000
+    del buf
+    return {"g_gathers_s": threads * per / t / 1e9, "granule_bytes": 32,
+            "useful_gb_s": threads * per * 32 / t / 1e9, "footprint_bytes": footprint}
 
 
 def bench_occ8(args, torch, fmocc, synth, dev, hbm_peak, peak_kind, flush, barrier,
@@ -462,6 +492,7 @@ def bench_occ8(args, torch, fmocc, synth, dev, hbm_peak, peak_kind, flush, barri
     t = max_over_ranks(float(np.mean(ms)) / 1000.0)
     bb = BLOCK_BYTES[I]
     gather = blocks * bb
+    ceil = gather_ceiling(torch, fmocc, dev, fmocc.fm_info(h)["n_blocks"] * bb, flush)
     io = args.occ_queries * 40.0
     h.close()
     return {"value": args.occ_queries * world / t / 1e9, "unit": "G 8-Occ/s",
@@ -473,7 +504,9 @@ def bench_occ8(args, torch, fmocc, synth, dev, hbm_peak, peak_kind, flush, barri
                          "peak_kind": peak_kind,
                          "gather_roofline_gq_s": hbm_peak * 1e9 / (gather / args.occ_queries) / 1e9,
                          "total_traffic_frac": (gather + io) / t / 1e9 / hbm_peak,
-                         "blocks_per_query": blocks / args.occ_queries},
+                         "blocks_per_query": blocks / args.occ_queries,
+                         "gather_ceiling": ceil,
+                         "frac_of_gather_ceiling": blocks / t / 1e9 / ceil["g_gathers_s"]},
             "setup_s": setup_s}
 
 

@@ -276,6 +276,15 @@ int fm_server_stats(fm_server *s, uint64_t out[4]);
  * freed too).  NULL is ignored. */
 int fm_server_stop(fm_server *s);
 
+/* Measurement probe (no counterpart in the paper): `threads` threads (a multiple of 256) each
+ * read `per_thread` (a multiple of 4) granules of `granule` bytes (32, 64 or 128) at uniformly
+ * random granule-aligned offsets of the device buffer buf[0, bytes), four at a time in flight,
+ * and write one folded word each to sink (device uint32[threads]).  The launch is enqueued on
+ * `stream` and not synchronised.  It gives the empirical random-gather ceiling of this device
+ * for the index gathers.  Errors: FM_EINVAL (alignment, sizes), FM_ECUDA. */
+int fm_probe_gather(const void *buf, uint64_t bytes, uint32_t granule, uint32_t threads,
+                    uint32_t per_thread, uint64_t seed, uint32_t *sink, void *stream);
+
 /* Tuning knobs of the search kernels (the autotuner writes them).  Zero fields keep the
  * current value.  Errors: FM_EINVAL for out-of-range values. */
 typedef struct fm_tuning {
@@ -286,6 +295,10 @@ typedef struct fm_tuning {
     uint32_t graphs;            /* 1: run the persistent search as a CUDA graph (captured on the
                                    first call with given buffers and sizes, replayed after);
                                    2: always launch eagerly */
+    uint32_t occ_per_thread;    /* fm_occ8 queries per thread: 1, 2 or 4 */
+    uint32_t l2_fetch_bytes;    /* 32, 64 or 128: the calling process's L2 fetch granularity
+                                   (cudaLimitMaxL2FetchGranularity of its CUDA context, set at
+                                   each compute call; it ends with the process) */
 } fm_tuning;
 
 int fm_set_tuning(fm_index *h, const fm_tuning *t);

@@ -122,6 +122,16 @@ void release(fm_index *h) {
     delete h;
 }
 
+// the context's L2 fetch granularity, when the tuning asks for one
+void apply_l2(fm_index *h) {
+    if (h->tune.l2_fetch) {
+        size_t cur = 0;
+        cudaDeviceGetLimit(&cur, cudaLimitMaxL2FetchGranularity);
+        if (cur != h->tune.l2_fetch) cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, h->tune.l2_fetch);
+        cudaGetLastError();
+    }
+}
+
 // reads the error word of a slot after synchronising the stream, and clears it
 int take_err(fm_index *h, ErrSlot slot, cudaStream_t st, uint32_t *out) {
     FM_CUDA_TRY(h, cudaMemcpyAsync(out, h->d_err + slot, 4, cudaMemcpyDeviceToHost, st));
@@ -380,6 +390,7 @@ int fm_occ8(fm_index *h, const uint32_t *k, const uint32_t *l, uint32_t *out8, u
     if (int rc = check_handle(h)) return rc;
     if (N && (!k || !l || !out8)) return set_error(h, FM_EINVAL, "null buffer");
     DeviceGuard g(h->device);
+    apply_l2(h);
     cudaStream_t st = (cudaStream_t)stream;
     FM_CUDA_TRY(h, cudaMemsetAsync(h->d_err + kErrOcc, 0, 4, st));
     if (int rc = launch_occ8(h, k, l, out8, N, st)) return rc;
@@ -433,6 +444,7 @@ int fm_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t
     if (!offsets || (n_reads && (!reads || !offs || !counts))) return set_error(h, FM_EINVAL, "null buffer");
     if (pair_capacity && !pairs) return set_error(h, FM_EINVAL, "pairs is NULL");
     DeviceGuard g(h->device);
+    apply_l2(h);
     cudaStream_t st = (cudaStream_t)stream;
     FM_CUDA_TRY(h, cudaMemsetAsync(h->d_err + kErrDcalc, 0, 8, st));   // dcalc and search words
     return run_inexact(h, reads, offs, n_reads, sp, counts, offsets, pairs, pair_capacity,
@@ -455,6 +467,12 @@ int fm_set_tuning(fm_index *h, const fm_tuning *t) {
     if (t->chunk) h->tune.chunk = t->chunk;
     if (t->plain_block) h->tune.plain_block = t->plain_block;
     if (t->graphs > 2) return set_error(h, FM_EINVAL, "graphs must be 0, 1 or 2");
+    if (t->occ_per_thread && t->occ_per_thread != 1 && t->occ_per_thread != 2 && t->occ_per_thread != 4)
+        return set_error(h, FM_EINVAL, "occ_per_thread must be 1, 2 or 4");
+    if (t->l2_fetch_bytes && t->l2_fetch_bytes != 32 && t->l2_fetch_bytes != 64 && t->l2_fetch_bytes != 128)
+        return set_error(h, FM_EINVAL, "l2_fetch_bytes must be 32, 64 or 128");
+    if (t->occ_per_thread) h->tune.occ_q = t->occ_per_thread;
+    if (t->l2_fetch_bytes) h->tune.l2_fetch = t->l2_fetch_bytes;
     if (t->graphs) h->use_graphs = t->graphs == 1;
     return FM_OK;
 }
@@ -467,6 +485,8 @@ int fm_get_tuning(const fm_index *h, fm_tuning *t) {
     t->chunk = h->tune.chunk;
     t->plain_block = h->tune.plain_block;
     t->graphs = h->use_graphs ? 1u : 2u;
+    t->occ_per_thread = h->tune.occ_q;
+    t->l2_fetch_bytes = h->tune.l2_fetch;
     return FM_OK;
 }
 

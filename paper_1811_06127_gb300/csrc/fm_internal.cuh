@@ -67,6 +67,8 @@ struct Tuning {
     uint32_t blocks_per_sm = 0;     // 0: from the occupancy calculator
     uint32_t chunk = 16;
     uint32_t plain_block = 128;
+    uint32_t occ_q = 2;
+    uint32_t l2_fetch = 0;   // 0: leave the context's limit alone
 };
 
 }  // namespace fm

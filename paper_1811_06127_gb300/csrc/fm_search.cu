@@ -212,12 +212,9 @@ int grid_occ(fm_index *h, uint64_t work, int block) {
 
 }  // namespace
 
-int launch_occ8(fm_index *h, const uint32_t *k, const uint32_t *l, uint32_t *out8, uint64_t N,
-                cudaStream_t st) {
-    if (N == 0) return FM_OK;
-    IndexView ix = view_fwd(h);
-    uint32_t *err = h->d_err + kErrOcc;
-    constexpr int Q = 2;
+template <int Q>
+static void occ8_q(fm_index *h, IndexView ix, const uint32_t *k, const uint32_t *l, uint32_t *out8,
+                   uint64_t N, uint32_t *err, cudaStream_t st) {
     const int block = 256;
     int grid = grid_occ(h, (N + Q - 1) / Q, block);
     switch (h->interval) {
@@ -225,6 +222,18 @@ int launch_occ8(fm_index *h, const uint32_t *k, const uint32_t *l, uint32_t *out
         case 64: k_occ8<64, Q><<<grid, block, 0, st>>>(ix, k, l, out8, N, err); break;
         case 128: k_occ8<128, Q><<<grid, block, 0, st>>>(ix, k, l, out8, N, err); break;
         default: k_occ8<256, Q><<<grid, block, 0, st>>>(ix, k, l, out8, N, err); break;
+    }
+}
+
+int launch_occ8(fm_index *h, const uint32_t *k, const uint32_t *l, uint32_t *out8, uint64_t N,
+                cudaStream_t st) {
+    if (N == 0) return FM_OK;
+    IndexView ix = view_fwd(h);
+    uint32_t *err = h->d_err + kErrOcc;
+    switch (h->tune.occ_q) {
+        case 1: occ8_q<1>(h, ix, k, l, out8, N, err, st); break;
+        case 4: occ8_q<4>(h, ix, k, l, out8, N, err, st); break;
+        default: occ8_q<2>(h, ix, k, l, out8, N, err, st); break;
     }
     FM_CUDA_TRY(h, cudaGetLastError());
     return FM_OK;

@@ -58,7 +58,8 @@ class fm_search_params(C.Structure):
 
 class fm_tuning(C.Structure):
     _fields_ = [("warps_per_block", C.c_uint32), ("blocks_per_sm", C.c_uint32),
-                ("chunk", C.c_uint32), ("plain_block", C.c_uint32), ("graphs", C.c_uint32)]
+                ("chunk", C.c_uint32), ("plain_block", C.c_uint32), ("graphs", C.c_uint32),
+                ("occ_per_thread", C.c_uint32), ("l2_fetch_bytes", C.c_uint32)]
 
 
 class fm_server_params(C.Structure):
@@ -79,7 +80,8 @@ class fm_server_result(C.Structure):
 EXPORTS = ["fm_build", "fm_free", "fm_last_error", "fm_info", "fm_get_bwt", "fm_save", "fm_load",
            "fm_occ8", "fm_exact", "fm_dcalc", "fm_inexact", "fm_inexact_fetch", "fm_set_tuning",
            "fm_get_tuning", "fm_inexact_noalloc", "fm_server_start", "fm_server_submit",
-           "fm_server_poll", "fm_server_release", "fm_server_stats", "fm_server_stop"]
+           "fm_server_poll", "fm_server_release", "fm_server_stats", "fm_server_stop",
+           "fm_probe_gather"]
 
 _lib = None
 
@@ -117,6 +119,7 @@ def load_library(path: str = LIB_PATH):
     lib.fm_server_release.argtypes = [P, u64]
     lib.fm_server_stats.argtypes = [P, P]
     lib.fm_server_stop.argtypes = [P]
+    lib.fm_probe_gather.argtypes = [P, u64, u32, u32, u32, u64, P, P]
     lib.fm_get_tuning.argtypes = [P, C.POINTER(fm_tuning)]
     for name in EXPORTS:
         f = getattr(lib, name)
@@ -365,9 +368,10 @@ def fm_inexact_fetch(h: Index, pairs: torch.Tensor, stream=None):
 
 
 def fm_set_tuning(h: Index, warps_per_block=0, blocks_per_sm=0, chunk=0, plain_block=0,
-                  graphs=0):
+                  graphs=0, occ_per_thread=0, l2_fetch_bytes=0):
     """Zero keeps a knob; graphs: 1 on, 2 off."""
-    t = fm_tuning(warps_per_block, blocks_per_sm, chunk, plain_block, graphs)
+    t = fm_tuning(warps_per_block, blocks_per_sm, chunk, plain_block, graphs, occ_per_thread,
+                  l2_fetch_bytes)
     _check(load_library().fm_set_tuning(h.ptr, C.byref(t)), h)
 
 
@@ -375,7 +379,20 @@ def fm_get_tuning(h: Index) -> dict:
     t = fm_tuning()
     _check(load_library().fm_get_tuning(h.ptr, C.byref(t)), h)
     return {"warps_per_block": t.warps_per_block, "blocks_per_sm": t.blocks_per_sm,
-            "chunk": t.chunk, "plain_block": t.plain_block, "graphs": t.graphs}
+            "chunk": t.chunk, "plain_block": t.plain_block, "graphs": t.graphs,
+            "occ_per_thread": t.occ_per_thread, "l2_fetch_bytes": t.l2_fetch_bytes}
+
+
+def fm_probe_gather(buf: torch.Tensor, granule: int, threads: int, per_thread: int,
+                    seed: int = 1, sink: torch.Tensor | None = None, stream=None):
+    """Random-gather probe over a CUDA buffer (measurement only)."""
+    if sink is None:
+        sink = torch.empty(threads, dtype=torch.int32, device=buf.device)
+    rc = load_library().fm_probe_gather(C.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size(),
+                                        granule, threads, per_thread, seed,
+                                        _dptr(sink, _U32, "sink"), _stream(stream))
+    _check(rc)
+    return sink
 
 
 class Server:
