@@ -40,6 +40,10 @@ METRIC = ("reads/s at z<=2 (batched vs plain kernel, bit-exact); 8-Occ Gq/s vs g
 SEED_EXACT, SEED_OCC, SEED_SEARCH = 1811061271, 1811061272, 1811061274
 # bytes of one checkpoint block per interval (fm_info reports the same)
 BLOCK_BYTES = {32: 32, 64: 32, 128: 64, 256: 96}
+# DRAM bytes (read + write) per launch of the search kernel from one ncu capture
+# (profiles/k_inexact_persistent_2gbp_10m_reads_dram.md), by (interval, reference bp, reads):
+# reported only when the run matches that configuration
+TRAFFIC_NCU = {(64, 2_000_000_000, 10_000_000): 7.65e12 + 3.47e9}
 
 
 def parse():
@@ -67,6 +71,9 @@ def parse():
     ap.add_argument("--cpu-sample-reads", type=int, default=200_000)
     ap.add_argument("--cpu-sample-ref", type=int, default=32_000_000)
     ap.add_argument("--log", default=None, help="also append the JSON line to this file")
+    ap.add_argument("--gather-sweep", action="store_true",
+                    help="only print the random-gather ceiling for 32/64/128-byte granules "
+                         "over 128 MB..8 GB buffers (one JSON line per point)")
     return ap.parse_args()
 
 
@@ -215,6 +222,8 @@ def main():
     import torch
     from paper_1811_06127_gb300 import fmocc, synth
 
+    if args.gather_sweep:
+        return gather_sweep(torch, fmocc)
     world, rank, local = dist_setup(args)
     torch.cuda.set_device(local)
     dist = None
@@ -400,7 +409,8 @@ def main():
                    "parallelism": f"replicas x{world} (read sharding)",
                    "l2": "flushed between timed steps (256 MB write); index 2x1 GB > L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None,
+                     "frac": achieved / hbm_peak,
+                     "traffic": TRAFFIC_NCU.get((args.interval, args.ref_n, args.reads)),
                      "kernel": "k_inexact_persistent", "kernel_ms": k_ms,
                      "gather_ceiling": ceil_main,
                      "blocks_per_s_over_gather_ceiling": (blocks_per_step / (k_ms / 1000) / 1e9
@@ -432,6 +442,39 @@ def main():
                 f.write(s + "\n")
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def gather_sweep(torch, fmocc):
+    """Random-gather throughput by granule and footprint (fm_probe_gather)."""
+    dev = torch.device("cuda", 0)
+    fmocc.load_library()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    big = torch.empty(8 << 30, dtype=torch.uint8, device=dev)
+    threads = torch.cuda.get_device_properties(dev).multi_processor_count * 2048
+    for size in (128 << 20, 512 << 20, 1 << 30, 2 << 30, 8 << 30):
+      buf = big[:size]
+      for inflight in (1, 4, 8):
+        for g in (32, 64, 128) if inflight < 8 else (32, 64):
+            per = 64 if g == 32 else 32
+            sink = torch.empty(threads, dtype=torch.int32, device=dev)
+            for _ in range(3):
+                fmocc.fm_probe_gather(buf, g, threads, per, 7, sink, inflight=inflight)
+            ms = []
+            for r in range(5):
+                flush.add_(1)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fmocc.fm_probe_gather(buf, g, threads, per, 100 + r, sink, inflight=inflight)
+                b.record()
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            t = float(np.median(ms)) / 1e3
+            n = threads * per
+            print(json.dumps({"footprint_MB": size >> 20, "granule": g, "inflight": inflight,
+                              "ms": t * 1e3,
+                              "G_gathers_s": n / t / 1e9, "useful_GB_s": n * g / t / 1e9}),
+                  flush=True)
     return 0
 
 

@@ -277,13 +277,15 @@ int fm_server_stats(fm_server *s, uint64_t out[4]);
 int fm_server_stop(fm_server *s);
 
 /* Measurement probe (no counterpart in the paper): `threads` threads (a multiple of 256) each
- * read `per_thread` (a multiple of 4) granules of `granule` bytes (32, 64 or 128) at uniformly
- * random granule-aligned offsets of the device buffer buf[0, bytes), four at a time in flight,
- * and write one folded word each to sink (device uint32[threads]).  The launch is enqueued on
+ * read `per_thread` (a multiple of `inflight`) granules of `granule` bytes (32, 64 or 128) at
+ * uniformly random granule-aligned offsets of the device buffer buf[0, bytes), `inflight`
+ * (1, 2, 4 or 8) at a time in flight, and write one folded word each to sink (device
+ * uint32[threads]).  The launch is enqueued on
  * `stream` and not synchronised.  It gives the empirical random-gather ceiling of this device
  * for the index gathers.  Errors: FM_EINVAL (alignment, sizes), FM_ECUDA. */
 int fm_probe_gather(const void *buf, uint64_t bytes, uint32_t granule, uint32_t threads,
-                    uint32_t per_thread, uint64_t seed, uint32_t *sink, void *stream);
+                    uint32_t per_thread, uint32_t inflight, uint64_t seed, uint32_t *sink,
+                    void *stream);
 
 /* Tuning knobs of the search kernels (the autotuner writes them).  Zero fields keep the
  * current value.  Errors: FM_EINVAL for out-of-range values. */

@@ -119,7 +119,7 @@ def load_library(path: str = LIB_PATH):
     lib.fm_server_release.argtypes = [P, u64]
     lib.fm_server_stats.argtypes = [P, P]
     lib.fm_server_stop.argtypes = [P]
-    lib.fm_probe_gather.argtypes = [P, u64, u32, u32, u32, u64, P, P]
+    lib.fm_probe_gather.argtypes = [P, u64, u32, u32, u32, u32, u64, P, P]
     lib.fm_get_tuning.argtypes = [P, C.POINTER(fm_tuning)]
     for name in EXPORTS:
         f = getattr(lib, name)
@@ -384,12 +384,13 @@ def fm_get_tuning(h: Index) -> dict:
 
 
 def fm_probe_gather(buf: torch.Tensor, granule: int, threads: int, per_thread: int,
-                    seed: int = 1, sink: torch.Tensor | None = None, stream=None):
+                    seed: int = 1, sink: torch.Tensor | None = None, stream=None,
+                    inflight: int = 4):
     """Random-gather probe over a CUDA buffer (measurement only)."""
     if sink is None:
         sink = torch.empty(threads, dtype=torch.int32, device=buf.device)
     rc = load_library().fm_probe_gather(C.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size(),
-                                        granule, threads, per_thread, seed,
+                                        granule, threads, per_thread, inflight, seed,
                                         _dptr(sink, _U32, "sink"), _stream(stream))
     _check(rc)
     return sink
