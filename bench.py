@@ -140,10 +140,8 @@ class Clocks:
 
 
 def dist_setup(args):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_1811_06127_gb300 import replicas
+    return replicas.env_rank()
 
 
 # ---------------------------------------------------------------------------------------------
@@ -235,17 +233,13 @@ def main():
     hbm_peak, peak_kind = peaks()
     notes = {}
 
+    from paper_1811_06127_gb300 import replicas
+
     def barrier():
         torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
+        replicas.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = replicas.max_over_ranks
 
     l2_flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB L2
 
@@ -257,7 +251,7 @@ def main():
     R = synth.repeat_text(SEED_SEARCH, args.ref_n)
     notes["ref_gen_s"] = time.time() - t0
     t0 = time.time()
-    reads = synth.sample_reads(SEED_SEARCH + 1000 * rank, R, args.reads, 50, 250, sub_rate=0.01,
+    reads = synth.sample_reads(replicas.shard_seed(SEED_SEARCH, rank), R, args.reads, 50, 250, sub_rate=0.01,
                                indel_rate=0.0005, both_strands=True)
     notes["reads_gen_s"] = time.time() - t0
     tuned = None
