@@ -369,6 +369,7 @@ def main():
                "d2h_bytes_per_step": int(d2h), "wall_s": time.perf_counter() - t0}
     serving = None if args.skip_serving else bench_serving(args, fmocc, h, reads)
     ceil_main = gather_ceiling(torch, fmocc, dev, fmocc.fm_info(h)["n_blocks"] * bbytes, flush)
+    locate = bench_locate(args, torch, fmocc, h, dev, flush)
     h.close()
     del codes, offs, pairs
 
@@ -425,6 +426,7 @@ def main():
         "exact": exact,
         "inexact_64mbp": cfg3,
         "serving": serving,
+        "locate": locate,
         "cpu_baseline": cpu,
         "setup": notes,
     }
@@ -545,6 +547,31 @@ def bench_occ8(args, torch, fmocc, synth, dev, hbm_peak, peak_kind, flush, barri
                          "gather_ceiling": ceil,
                          "frac_of_gather_ceiling": blocks / t / 1e9 / ceil["g_gathers_s"]},
             "setup_s": setup_s}
+
+
+def bench_locate(args, torch, fmocc, h, dev, flush):
+    """Locate (Eq. 4-5) of 2^24 uniform random rows of the 2 Gbp index: SA samples every 32
+    rows, one Psi^-1 step (one block gather) per walked row."""
+    n = fmocc.fm_info(h)["n"]
+    g = torch.Generator(device="cpu").manual_seed(1811061276)
+    rows = torch.randint(0, n + 1, (1 << 24,), generator=g, dtype=torch.int64).to(torch.int32).to(dev)
+    pos = torch.empty_like(rows)
+    steps = torch.zeros(1, dtype=torch.int64, device=dev)
+    for _ in range(2):
+        fmocc.fm_locate(h, rows, pos)
+    ms = []
+    for _ in range(3):
+        flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fmocc.fm_locate(h, rows, pos, steps=steps)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = float(np.median(ms)) / 1000
+    st = int(steps.item()) / 3
+    return {"rows": 1 << 24, "rows_per_s": (1 << 24) / t, "ms": t * 1000,
+            "steps_per_row": st / (1 << 24), "steps_per_s": st / t}
 
 
 def bench_serving(args, fmocc, h, reads):

@@ -140,6 +140,18 @@ typedef struct fm_profile {
     uint32_t reserved;
 } fm_profile;
 
+/* Locate (Sec. 2, Eq. 4-5): pos_out[q] = SA[rows[q]], the text position of the suffix in
+ * that row, recovered from the suffix array kept at rows that are multiples of 32
+ * (fm_info.sa_sample_rate) by applying Psi^-1(i) = C[BWT[i]] + Occ(BWT[i], i) (Eq. 4) until a
+ * sampled row (or the $ row, whose suffix starts at 0) is reached j steps later, then
+ * SA[row] = SA[sampled] + j (Eq. 5).  Every row of an interval from fm_exact/fm_inexact is one
+ * occurrence of the searched string at that position.
+ * rows: device uint32[N], each <= n.  pos_out: device uint32[N].  steps: optional device
+ * uint64 counter to which the total number of Psi^-1 steps is added.
+ * Errors: FM_EINVAL (a row above n: its position reads 0). */
+int fm_locate(fm_index *h, const uint32_t *rows, uint64_t N, uint32_t *pos_out, uint64_t *steps,
+              void *stream);
+
 /* Inexact search options. */
 typedef struct fm_search_params {
     uint32_t z;        /* differences allowed, 0..7 */

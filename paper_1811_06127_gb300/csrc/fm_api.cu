@@ -414,6 +414,21 @@ int fm_exact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n
     return FM_OK;
 }
 
+int fm_locate(fm_index *h, const uint32_t *rows, uint64_t N, uint32_t *pos_out, uint64_t *steps,
+              void *stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (N && (!rows || !pos_out)) return set_error(h, FM_EINVAL, "null buffer");
+    if (!h->d_sa_sample) return set_error(h, FM_EINVAL, "index holds no SA samples");
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    FM_CUDA_TRY(h, cudaMemsetAsync(h->d_err + kErrExact, 0, 4, st));
+    if (int rc = launch_locate(h, rows, N, pos_out, (unsigned long long *)steps, st)) return rc;
+    uint32_t errw = 0;
+    if (int rc = take_err(h, kErrExact, st, &errw)) return rc;
+    if (errw) return set_error(h, FM_EINVAL, "a row is above n");
+    return FM_OK;
+}
+
 int fm_dcalc(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
              uint32_t strands, uint8_t *D_out, void *stream) {
     if (int rc = check_handle(h)) return rc;

@@ -133,6 +133,8 @@ IndexView view_rev(const fm_index *h);
 
 int launch_occ8(fm_index *h, const uint32_t *k, const uint32_t *l, uint32_t *out8, uint64_t N,
                 cudaStream_t st);
+int launch_locate(fm_index *h, const uint32_t *rows, uint64_t N, uint32_t *pos,
+                  unsigned long long *steps, cudaStream_t st);
 int launch_exact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
                  uint32_t *k_out, uint32_t *l_out, cudaStream_t st);
 // D lower bound per query; qmeta (uint4 per query) and/or D_out (uint8 per position)

@@ -203,6 +203,53 @@ __global__ void __launch_bounds__(128) k_dcalc(IndexView rv, const uint8_t *__re
     }
 }
 
+// -------------------------------------------------------------------------------------------
+// Locate (Sec. 2, Eq. 4-5): SA[row] from the rows sampled every `rate` (SA[j*rate] kept) by
+// walking LF(i) = C[BWT[i]] + Occ(BWT[i], i), which moves to the row of the suffix one text
+// position earlier, so SA[row] = SA[LF^j(row)] + j at the first sampled row.  The $ row holds
+// suffix 0 (SA = 0) and ends a walk too.  One thread per row; every step is one block gather.
+// -------------------------------------------------------------------------------------------
+template <int I>
+__global__ void __launch_bounds__(256) k_locate(IndexView ix, const uint32_t *__restrict__ sa_sample,
+                                                uint32_t rate, const uint32_t *__restrict__ rows,
+                                                uint64_t N, uint32_t *__restrict__ pos,
+                                                unsigned long long *__restrict__ steps,
+                                                uint32_t *__restrict__ err) {
+    unsigned long long my_steps = 0;
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < N;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t i = rows[q];
+        if (i > ix.n) {
+            atomicOr(err, kErrDomain);
+            pos[q] = 0;
+            continue;
+        }
+        uint32_t j = 0;
+        for (;;) {
+            if (i % rate == 0) {
+                pos[q] = sa_sample[i / rate] + j;
+                break;
+            }
+            if (i == ix.dollar) {
+                pos[q] = j;
+                break;
+            }
+            const uint32_t jb = i / I;
+            Blk<I> B;
+            load_block<I>(ix.blocks, jb, i - jb * I + 1u, B);
+            const uint32_t b = sym_in<I>(B, jb, i);
+            const uint32_t cb = b == 0 ? ix.C[0] : (b == 1 ? ix.C[1] : (b == 2 ? ix.C[2] : ix.C[3]));
+            i = cb + rank1_in<I>(B, jb, i, ix.dollar, b) + 1u;   // Occ(b, i) = rank(b, i) + 1
+            ++j;
+        }
+        my_steps += j;
+    }
+    if (steps) {
+        for (int o = 16; o > 0; o >>= 1) my_steps += __shfl_down_sync(0xffffffffu, my_steps, o);
+        if ((threadIdx.x & 31) == 0 && my_steps) atomicAdd(steps, my_steps);
+    }
+}
+
 int grid_occ(fm_index *h, uint64_t work, int block) {
     uint64_t g = (work + block - 1) / block;
     uint64_t cap = (uint64_t)h->sms * (2048 / block) * 4;
@@ -234,6 +281,24 @@ int launch_occ8(fm_index *h, const uint32_t *k, const uint32_t *l, uint32_t *out
         case 1: occ8_q<1>(h, ix, k, l, out8, N, err, st); break;
         case 4: occ8_q<4>(h, ix, k, l, out8, N, err, st); break;
         default: occ8_q<2>(h, ix, k, l, out8, N, err, st); break;
+    }
+    FM_CUDA_TRY(h, cudaGetLastError());
+    return FM_OK;
+}
+
+int launch_locate(fm_index *h, const uint32_t *rows, uint64_t N, uint32_t *pos,
+                  unsigned long long *steps, cudaStream_t st) {
+    if (N == 0) return FM_OK;
+    IndexView ix = view_fwd(h);
+    uint32_t *err = h->d_err + kErrExact;
+    const int block = 256;
+    const int grid = grid_occ(h, N, block);
+    const uint32_t rate = (uint32_t)h->sa_rate;
+    switch (h->interval) {
+        case 32: k_locate<32><<<grid, block, 0, st>>>(ix, h->d_sa_sample, rate, rows, N, pos, steps, err); break;
+        case 64: k_locate<64><<<grid, block, 0, st>>>(ix, h->d_sa_sample, rate, rows, N, pos, steps, err); break;
+        case 128: k_locate<128><<<grid, block, 0, st>>>(ix, h->d_sa_sample, rate, rows, N, pos, steps, err); break;
+        default: k_locate<256><<<grid, block, 0, st>>>(ix, h->d_sa_sample, rate, rows, N, pos, steps, err); break;
     }
     FM_CUDA_TRY(h, cudaGetLastError());
     return FM_OK;

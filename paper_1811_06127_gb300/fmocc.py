@@ -81,7 +81,7 @@ EXPORTS = ["fm_build", "fm_free", "fm_last_error", "fm_info", "fm_get_bwt", "fm_
            "fm_occ8", "fm_exact", "fm_dcalc", "fm_inexact", "fm_inexact_fetch", "fm_set_tuning",
            "fm_get_tuning", "fm_inexact_noalloc", "fm_server_start", "fm_server_submit",
            "fm_server_poll", "fm_server_release", "fm_server_stats", "fm_server_stop",
-           "fm_probe_gather"]
+           "fm_probe_gather", "fm_locate"]
 
 _lib = None
 
@@ -107,6 +107,7 @@ def load_library(path: str = LIB_PATH):
     lib.fm_occ8.argtypes = [P, P, P, P, u64, P]
     lib.fm_exact.argtypes = [P, P, P, u32, P, P, P]
     lib.fm_dcalc.argtypes = [P, P, P, u32, u32, P, P]
+    lib.fm_locate.argtypes = [P, P, u64, P, P, P]
     lib.fm_inexact.argtypes = [P, P, P, u32, C.POINTER(fm_search_params), P, P, P, u64,
                                C.POINTER(C.c_uint64), P]
     lib.fm_inexact_fetch.argtypes = [P, P, u64, P]
@@ -284,6 +285,20 @@ def fm_exact(h: Index, reads: torch.Tensor, offs: torch.Tensor, k_out=None, l_ou
                                  _stream(stream))
     _check(rc, h)
     return k_out, l_out
+
+
+def fm_locate(h: Index, rows: torch.Tensor, pos_out: torch.Tensor | None = None,
+              steps: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """SA[row] for each row (int32 CUDA tensor of the same length)."""
+    N = rows.numel()
+    if pos_out is None:
+        pos_out = torch.empty(N, dtype=torch.int32, device=rows.device)
+    rc = load_library().fm_locate(h.ptr, _dptr(rows, _U32, "rows"), N,
+                                  _dptr(pos_out, _U32, "pos_out"),
+                                  _dptr(steps, _U64, "steps") if steps is not None else None,
+                                  _stream(stream))
+    _check(rc, h)
+    return pos_out
 
 
 def fm_dcalc(h: Index, reads: torch.Tensor, offs: torch.Tensor, strands: int = 1, D_out=None,
