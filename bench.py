@@ -43,7 +43,9 @@ BLOCK_BYTES = {32: 32, 64: 32, 128: 64, 256: 96}
 # DRAM bytes (read + write) per launch of the search kernel from one ncu capture
 # (profiles/k_inexact_persistent_2gbp_10m_reads_dram.md), by (interval, reference bp, reads):
 # reported only when the run matches that configuration
-TRAFFIC_NCU = {(64, 2_000_000_000, 10_000_000): 7.65e12 + 3.47e9}
+# keyed by (interval, reference bp, reads, canonical enumeration on); an entry is removed when
+# the kernel changes and added back from a fresh capture
+TRAFFIC_NCU = {}
 
 
 def parse():
@@ -66,6 +68,9 @@ def parse():
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--autotune", type=int, default=1, help="1: tune interval/occupancy/chunk")
+    ap.add_argument("--canonical", type=int, default=1, choices=[1, 2],
+                    help="1: enumerate canonical alignments (same interval sets, fewer nodes); "
+                         "2: every call of Listing 2")
     ap.add_argument("--tune-reads", type=int, default=200_000)
     ap.add_argument("--tune-cache", default=None, help="JSON cache of tuning results")
     ap.add_argument("--cpu-sample-reads", type=int, default=200_000)
@@ -267,6 +272,7 @@ def main():
     notes["build_s"] = time.time() - t0
     if tuned:
         autotune.apply(h, tuned)
+    fmocc.fm_set_tuning(h, canonical=args.canonical)
     del R
     codes_h = torch.from_numpy(reads.codes).pin_memory()
     offs_h = torch.from_numpy(reads.offs.view(np.int32)).pin_memory()
@@ -396,6 +402,8 @@ def main():
                                 "(41% GC, 20% copies of 500 families), 10M reads 50-250 bp, 1% "
                                 "subst + 0.05% indel, z=2 with <=1 gap, both strands, persistent "
                                 "kernel"),
+                   "enumeration": ("canonical alignments (the interval sets of Listing 2)"
+                                   if args.canonical == 1 else "every call of Listing 2"),
                    "reference_bp": args.ref_n, "reads_per_step": args.reads,
                    "queries_per_step": nq, "interval": args.interval,
                    "tuning": ({k: tuned[k] for k in ("interval", "warps_per_block",
@@ -405,7 +413,8 @@ def main():
                    "l2": "flushed between timed steps (256 MB write); index 2x1 GB > L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
-                     "traffic": TRAFFIC_NCU.get((args.interval, args.ref_n, args.reads)),
+                     "traffic": TRAFFIC_NCU.get((args.interval, args.ref_n, args.reads,
+                                                 args.canonical == 1)),
                      "kernel": "k_inexact_persistent", "kernel_ms": k_ms,
                      "gather_ceiling": ceil_main,
                      "blocks_per_s_over_gather_ceiling": (blocks_per_step / (k_ms / 1000) / 1e9

@@ -160,7 +160,8 @@ typedef struct fm_search_params {
                           queries q = 2r (read) and q = 2r+1 (reverse complement) */
     uint32_t kernel;   /* FM_KERNEL_* */
     uint64_t *stats;   /* optional device uint64[4], accumulated by each successful call:
-                          [0] nodes expanded (calls of InexRecur reaching the Occ step),
+                          [0] nodes expanded (calls of InexRecur reaching the Occ step; with
+                              fm_tuning.canonical on, those of the canonical enumeration),
                           [1] checkpoint blocks read by those expansions (1 when k and l+1
                               share a block, else 2), [2] intervals reported before
                               deduplication, [3] reserved */
@@ -313,6 +314,12 @@ typedef struct fm_tuning {
     uint32_t l2_fetch_bytes;    /* 32, 64 or 128: the calling process's L2 fetch granularity
                                    (cudaLimitMaxL2FetchGranularity of its CUDA context, set at
                                    each compute call; it ends with the process) */
+    uint32_t canonical;         /* 1 (default): the inexact search enumerates only canonical
+                                   alignments (an indel next to a mismatch, or inside a run of
+                                   one base, in one fixed order), so no reference string is
+                                   spelled twice by alignments of the same cost; the reported
+                                   intervals are those of Listing 2, the nodes fewer.  2: every
+                                   call of Listing 2 (stats then count its nodes exactly) */
 } fm_tuning;
 
 int fm_set_tuning(fm_index *h, const fm_tuning *t);

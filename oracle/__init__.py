@@ -255,13 +255,17 @@ class Index:
         return D
 
     def inexact(self, codes, offs, z: int, max_gaps: int = 0, strands: int = 1,
-                prune: bool = True, interval: int = 64, threads: int = 0):
-        """Listing 2 result sets: dict with counts, offsets, pairs (total x 2), nodes, blocks."""
+                prune: bool = True, interval: int = 64, threads: int = 0,
+                canonical: bool = False):
+        """Listing 2 result sets: dict with counts, offsets, pairs (total x 2), nodes, blocks.
+        canonical: enumerate canonical alignments only (same results; nodes and blocks are
+        those of that enumeration)."""
         codes = _u8(codes)
         offs = np.ascontiguousarray(offs, dtype=np.uint32)
         nr = offs.size - 1
         res = self.lib.or_inexact_batch(self.h, _p(codes), _p(offs), nr, strands, z, max_gaps,
-                                        1 if prune else 0, interval, threads)
+                                        (1 if prune else 0) | (2 if canonical else 0),
+                                        interval, threads)
         if not res:
             raise ValueError("or_inexact_batch")
         try:

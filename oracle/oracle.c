@@ -603,6 +603,61 @@ static void inex_recur(inex_ctx *X, int64_t i, int z, int gaps, int64_t k, int64
     }
 }
 
+/* Canonical enumeration (test instrumentation, not part of the paper's method): the same
+ * search, except that a call also knows the column that created it (last: 0 match or top
+ * call, 1 mismatch with reference symbol lb, 2 insertion, 3 deletion of lb) and skips the
+ * children that begin a non-canonical pair of adjacent columns:
+ *   after an insertion (of W[i+1]): no mismatch, no deletion, no match when W[i] = W[i+1];
+ *   after a deletion of lb: no insertion; when i >= 1 also no mismatch and no match of lb;
+ *   after a mismatch with lb at W[i+1]: no insertion when W[i] = lb, no deletion of W[i+1].
+ * Each skipped pair spells the same reference string as a canonical pair of no higher cost,
+ * so the reported intervals are unchanged.  A call counts as a node only when one of its
+ * Occ children (deletion, mismatch, match) is allowed by these rules and by z; a call with
+ * none passes through to its insertion child alone. */
+static void inex_canon(inex_ctx *X, int64_t i, int z, int gaps, int64_t k, int64_t l, int last,
+                       int lb) {
+    if (z < 0 || (X->prune && i >= 0 && z < X->D[i])) return;
+    if (i < 0) { /* a result, unless no reference symbol was used */
+        if (k > 0) pv_push(X->out, (uint32_t)k, (uint32_t)l);
+        return;
+    }
+    const uint8_t *W = X->W;
+    int may_ins = gaps < X->max_gaps, may_del = gaps < X->max_gaps && z >= 1;
+    int may_mis = z >= 1, may_match = 1, no_del_sym = -1;
+    if (last == 2) {
+        may_del = 0;
+        may_mis = 0;
+        if (W[i] == W[i + 1]) may_match = 0;
+    } else if (last == 3) {
+        may_ins = 0;
+        if (i >= 1) {
+            may_mis = 0;
+            if (W[i] == lb) may_match = 0;
+        }
+    } else if (last == 1) {
+        if (W[i] == lb) may_ins = 0;
+        no_del_sym = W[i + 1];
+    }
+    if (may_ins) inex_canon(X, i - 1, z - 1, gaps + 1, k, l, 2, 0);
+    if (!may_del && !may_mis && !may_match) return;
+    X->nodes++;
+    X->blocks += (k / X->interval == (l + 1) / X->interval) ? 1 : 2;
+    int64_t ok[4], ol[4];
+    or_occ4(X->ix, k - 1, ok);
+    or_occ4(X->ix, l, ol);
+    for (int b = 0; b < 4; ++b) {
+        int64_t k2 = X->ix->C[b] + ok[b] + 1;
+        int64_t l2 = X->ix->C[b] + ol[b];
+        if (k2 > l2) continue;
+        if (may_del && b != no_del_sym) inex_canon(X, i, z - 1, gaps + 1, k2, l2, 3, b);
+        if (b == W[i]) {
+            if (may_match) inex_canon(X, i - 1, z, gaps, k2, l2, 0, b);
+        } else if (may_mis) {
+            inex_canon(X, i - 1, z - 1, gaps, k2, l2, 1, b);
+        }
+    }
+}
+
 static int cmp_pair(const void *a, const void *b) {
     const uint32_t *x = (const uint32_t *)a, *y = (const uint32_t *)b;
     if (x[0] != y[0]) return x[0] < y[0] ? -1 : 1;
@@ -632,8 +687,11 @@ static void inex_one(void *a, int64_t q, int tid) {
         W[i] = strand ? (uint8_t)(3 - J->codes[s + m - 1 - i]) : J->codes[s + i];
     or_dcalc(J->ix, W, m, D);
     pairvec v = {NULL, 0, 0};
-    inex_ctx X = {J->ix, W, D, J->max_gaps, J->prune, J->interval, &v, 0, 0};
-    inex_recur(&X, m - 1, J->z, 0, 0, J->ix->n);
+    inex_ctx X = {J->ix, W, D, J->max_gaps, J->prune & 1, J->interval, &v, 0, 0};
+    if (J->prune & 2)
+        inex_canon(&X, m - 1, J->z, 0, 0, J->ix->n, 0, 0);
+    else
+        inex_recur(&X, m - 1, J->z, 0, 0, J->ix->n);
     if (v.size > 1) { /* sort and keep distinct intervals */
         qsort(v.pairs, (size_t)v.size, 2 * sizeof(uint32_t), cmp_pair);
         int64_t w = 1;

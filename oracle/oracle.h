@@ -100,7 +100,9 @@ void or_dcalc(const or_index *ix, const uint8_t *W, int64_t m, uint8_t *D);
  *   - the deletion, match and mismatch recursions all run only when k' <= l';
  *   - insertions and deletions are single-base columns, at most max_gaps of them in total
  *     (max_gaps = 0: mismatches only);
- *   - with prune != 0 a call returns nothing when z < D(i) (D(-1) = 0);
+ *   - with prune & 1 a call returns nothing when z < D(i) (D(-1) = 0);
+ *   - with prune & 2 the search enumerates canonical alignments only (test instrumentation,
+ *     not in the paper; oracle.c states the rules): same results, fewer nodes;
  *   - a call with i < 0 and z >= 0 reports {k, l} unless k = 0 (no reference symbol used);
  *   - the top call is InexRecur(W, m-1, z, 0, n).
  * Query q = r*strands + s searches read r (s = 0) or its reverse complement (s = 1).

@@ -475,19 +475,22 @@ int fm_inexact_fetch(fm_index *h, uint32_t *pairs, uint64_t pair_capacity, void 
 int fm_set_tuning(fm_index *h, const fm_tuning *t) {
     if (int rc = check_handle(h)) return rc;
     if (!t) return set_error(h, FM_EINVAL, "tuning is NULL");
+    // every value is checked before any is applied: a rejected call changes nothing
     if (t->warps_per_block > 8 || t->chunk > 32 || (t->plain_block && (t->plain_block % 32 || t->plain_block > 256)))
         return set_error(h, FM_EINVAL, "tuning value out of range");
-    if (t->warps_per_block) h->tune.warps_per_block = t->warps_per_block;
-    if (t->blocks_per_sm) h->tune.blocks_per_sm = t->blocks_per_sm;
-    if (t->chunk) h->tune.chunk = t->chunk;
-    if (t->plain_block) h->tune.plain_block = t->plain_block;
     if (t->graphs > 2) return set_error(h, FM_EINVAL, "graphs must be 0, 1 or 2");
     if (t->occ_per_thread && t->occ_per_thread != 1 && t->occ_per_thread != 2 && t->occ_per_thread != 4)
         return set_error(h, FM_EINVAL, "occ_per_thread must be 1, 2 or 4");
     if (t->l2_fetch_bytes && t->l2_fetch_bytes != 32 && t->l2_fetch_bytes != 64 && t->l2_fetch_bytes != 128)
         return set_error(h, FM_EINVAL, "l2_fetch_bytes must be 32, 64 or 128");
+    if (t->canonical > 2) return set_error(h, FM_EINVAL, "canonical must be 0, 1 or 2");
+    if (t->warps_per_block) h->tune.warps_per_block = t->warps_per_block;
+    if (t->blocks_per_sm) h->tune.blocks_per_sm = t->blocks_per_sm;
+    if (t->chunk) h->tune.chunk = t->chunk;
+    if (t->plain_block) h->tune.plain_block = t->plain_block;
     if (t->occ_per_thread) h->tune.occ_q = t->occ_per_thread;
     if (t->l2_fetch_bytes) h->tune.l2_fetch = t->l2_fetch_bytes;
+    if (t->canonical) h->tune.canon = t->canonical == 1 ? 1u : 0u;
     if (t->graphs) h->use_graphs = t->graphs == 1;
     return FM_OK;
 }
@@ -502,6 +505,7 @@ int fm_get_tuning(const fm_index *h, fm_tuning *t) {
     t->graphs = h->use_graphs ? 1u : 2u;
     t->occ_per_thread = h->tune.occ_q;
     t->l2_fetch_bytes = h->tune.l2_fetch;
+    t->canonical = h->tune.canon ? 1u : 2u;
     return FM_OK;
 }
 

@@ -1,14 +1,14 @@
 // Index construction on the device (Sec. 2: Eq. 1 suffix array, Eq. 2 BWT, C, and the
 // checkpointed occurrence table).  Runs once per index, off the search path.
 //
-// Suffix array by prefix doubling (Manber and Myers 1993), each round one radix sort of the
+// Suffix array by prefix doubling (Manber and Myers 1993), each pass one radix sort of the
 // n+1 suffixes by a 64-bit key:
-//   round 0: the first 27 symbols of each suffix in base 5 ($ = 0 beyond the end, A..T =
+//   pass 0: the first 27 symbols of each suffix in base 5 ($ = 0 beyond the end, A..T =
 //            1..4; 5^27 < 2^63), so most suffixes are told apart without any doubling;
-//   round r: key = (rank_h(i), rank_h(i+h) + 1) with rank_h the start of i's group after the
-//            previous round, h doubling from 27; a suffix whose first h symbols include $ is
+//   pass r: key = (rank_h(i), rank_h(i+h) + 1) with rank_h the start of i's group after the
+//            previous pass, h doubling from 27; a suffix whose first h symbols include $ is
 //            already alone in its group.
-// Rounds stop when every group is a singleton.  The radix sort and scans of this build path
+// Passes stop when every group is a singleton.  The radix sort and scans of this build path
 // are CUB's (header library shipped with the CUDA toolkit); the search path uses none.
 #include <cub/cub.cuh>
 
@@ -218,7 +218,7 @@ int build_index(fm_index *h, const uint8_t *d_codes_in, uint64_t n, bool reverse
 
         int end_bit = 63;   // 5^27 < 2^63
         uint64_t hlen = 27;
-        for (int round = 0; round < 64; ++round) {
+        for (int pass = 0; pass < 64; ++pass) {
             size_t tb = tmp_bytes;
             BTRY(cub::DeviceRadixSort::SortPairs(tmp, tb, dk, dv, (int)N, 0, end_bit, st));
             BTRY(cudaMemsetAsync(d_cnt, 0, 8, st));
@@ -233,12 +233,12 @@ int build_index(fm_index *h, const uint8_t *d_codes_in, uint64_t n, bool reverse
             if (heads == N) break;   // every suffix alone: dv.Current() is the SA
             k_scatter_rank<<<G, 256, 0, st>>>(dv.Current(), grp, N, rank);
             BTRY(cudaGetLastError());
-            // next round: keys (rank(i), rank(i+h)+1) into the current key buffer
+            // next pass: keys (rank(i), rank(i+h)+1) into the current key buffer
             k_keys_double<<<G, 256, 0, st>>>(rank, N, hlen, nbits, dk.Current(), dv.Current());
             BTRY(cudaGetLastError());
             end_bit = 2 * nbits;
             hlen *= 2;
-            if (round == 63) {
+            if (pass == 63) {
                 rc = set_error(h, FM_ECUDA, "suffix sorting did not converge");
                 goto done;
             }

@@ -46,6 +46,7 @@ struct SearchCfg {
     uint64_t raw_cap;
     unsigned long long *stats;   // nodes, blocks, raw
     uint32_t *err;
+    uint32_t canon;              // enumerate canonical alignments only (see expand)
 };
 
 __device__ __forceinline__ uint32_t d_at(const uint4 &mt, int i) {
@@ -60,11 +61,34 @@ __device__ __forceinline__ uint32_t w_at(const uint8_t *reads, const uint4 &mt, 
     return reads[mt.z + i];
 }
 
+// Node word y: bits 0-7 i, 8-11 z left, 12-15 indel columns used, 16-17 the operation that
+// created the node (kOpMatch also for a root), 18-19 its reference symbol (mismatch, deletion).
+constexpr uint32_t kOpMatch = 0u, kOpMis = 1u, kOpIns = 2u, kOpDel = 3u;
+
 // One expansion: the eight-Occ step of Listing 2 (rank(c, k) and rank(c, l+1) for c in ACGT
 // from one or two checkpoint blocks), then the children.  Every lane runs the same code, so
 // the block gathers of the whole warp are issued together.  Outputs the four child intervals
 // and two 9-bit masks: bit 0 insertion, bits 1..4 deletion with b = 0..3, bits 5..8
 // match/mismatch with b = 0..3; push: child kept as a node; leaf: child is a result.
+//
+// With c.canon set, only canonical alignments are enumerated.  Two alignments that differ by
+// where an indel sits next to a mismatch, or by which copy of a repeated base an indel takes,
+// spell the same reference string, and their search states coincide (or one has fewer
+// differences left and is dominated).  Each rewrite below keeps the spelled string, never
+// raises the cost or the indel count, and moves an indel one read position towards W[0] (or
+// lowers the cost), so rewriting ends, and every alignment within the bounds has a canonical
+// one spelling the same string.  Since a path to a result is never cut by the D bound (D(i)
+// bounds the differences any alignment of W[0..i] needs), the reported intervals are those of
+// Listing 2; only repeated subtrees go.  Forbidden, in processing order (i decreasing):
+//   insertion of W[i+1], then match of W[i] = W[i+1]   (same as match, then insertion)
+//   insertion, then mismatch or deletion               (mismatch/match first; or one mismatch)
+//   deletion b at i >= 1, then match of W[i] = b        (match, then deletion at i-1)
+//   deletion at i >= 1, then mismatch                  (mismatch/match, then deletion at i-1)
+//   deletion, then insertion                           (one mismatch or match)
+//   mismatch b at W[i+1], then insertion of W[i] = b   (insertion, then match: one less)
+//   mismatch at W[i+1], then deletion of b = W[i+1]    (deletion, then match: one less)
+// A node none of whose Occ children is allowed takes no Occ step and is not counted; a child
+// that could take no step at all is not created.
 template <int I>
 __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, const uint4 &mt,
                                        uint32_t k2[4], uint32_t l2[4], uint32_t &push,
@@ -75,51 +99,88 @@ __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, cons
     const uint32_t k = nd.z, l = nd.w;
     const uint32_t wi = w_at(c.reads, mt, (uint32_t)i);
     wi_out = wi;
-    const uint32_t pk = k, pl = l + 1u;
-    const uint32_t jk = pk / I, jl = pl / I;
-    const uint32_t ok = pk - jk * I, ol = pl - jl * I;
-    Blk<I> Bk, Bl;
-    if (jk == jl) {
-        load_block<I>(c.ix.blocks, jk, ok > ol ? ok : ol, Bk);
-        Bl = Bk;
-        nblocks = 1;
-    } else {
-        load_block<I>(c.ix.blocks, jk, ok, Bk);
-        load_block<I>(c.ix.blocks, jl, ol, Bl);
-        nblocks = 2;
+    bool ins_r = true, mis_r = true, del_r = true, match_r = true;
+    uint32_t del_keep = 0xfu;
+    uint32_t wp = 4u;   // W[i-1] when the rules need it, else a value no symbol has
+    if (c.canon) {
+        const uint32_t op = (nd.y >> 16) & 3u, pb = (nd.y >> 18) & 3u;
+        if (op == kOpIns || op == kOpMis) {
+            const uint32_t wn = w_at(c.reads, mt, (uint32_t)i + 1u);
+            if (op == kOpIns) {
+                del_r = false;
+                mis_r = false;
+                match_r = wi != wn;
+            } else {
+                ins_r = pb != wi;
+                del_keep = 0xfu & ~(1u << wn);
+            }
+        } else if (op == kOpDel) {
+            ins_r = false;
+            if (i >= 1) {
+                mis_r = false;
+                match_r = wi != pb;
+            }
+        }
+        if (i >= 1) wp = w_at(c.reads, mt, (uint32_t)i - 1u);
     }
-    uint32_t rk[4], rl[4];
-    rank4_in<I>(Bk, jk, pk, c.ix.dollar, rk);
-    rank4_in<I>(Bl, jl, pl, c.ix.dollar, rl);
+    const bool gap_ok = z >= 1u && g < c.max_gaps;
+    const bool need = (gap_ok && del_r) || (z >= 1u && mis_r) || match_r;
+    // a new indel child can take another indel only with a gap and a difference to spare
+    const bool more_gaps = g + 1u < c.max_gaps && z >= 2u;
+    uint32_t rk[4] = {0, 0, 0, 0}, rl[4] = {0, 0, 0, 0};
+    nblocks = 0;
+    if (need) {
+        const uint32_t pk = k, pl = l + 1u;
+        const uint32_t jk = pk / I, jl = pl / I;
+        const uint32_t ok = pk - jk * I, ol = pl - jl * I;
+        Blk<I> Bk, Bl;
+        if (jk == jl) {
+            load_block<I>(c.ix.blocks, jk, ok > ol ? ok : ol, Bk);
+            Bl = Bk;
+            nblocks = 1;
+        } else {
+            load_block<I>(c.ix.blocks, jk, ok, Bk);
+            load_block<I>(c.ix.blocks, jl, ol, Bl);
+            nblocks = 2;
+        }
+        rank4_in<I>(Bk, jk, pk, c.ix.dollar, rk);
+        rank4_in<I>(Bl, jl, pl, c.ix.dollar, rl);
+    }
     const uint32_t d_here = d_at(mt, i);
     const uint32_t d_next = d_at(mt, i - 1);
-    const bool gap_ok = z >= 1u && g < c.max_gaps;
-    const bool del_ok = gap_ok && z - 1u >= d_here;
+    const bool del_ok = gap_ok && del_r && z - 1u >= d_here;
     const bool last = i == 0;
     push = 0;
     leaf = 0;
-    // insertion: W[i] against no reference symbol, interval unchanged
-    if (gap_ok) {
+    // insertion: W[i] against no reference symbol, interval unchanged; the child at i-1 can
+    // only insert again when W[i-1] = W[i] (rules on)
+    if (gap_ok && ins_r) {
         if (last) {
             if (k >= 1u) leaf |= 1u;
-        } else if (z - 1u >= d_next) {
+        } else if (z - 1u >= d_next && (wp != wi || more_gaps)) {
             push |= 1u;
         }
     }
-    const bool mm_ok = z >= 1u && (last || z - 1u >= d_next);   // a mismatch child survives
-    const bool ma_ok = last || z >= d_next;                      // the match child survives
+    const bool mm_ok = z >= 1u && mis_r && (last || z - 1u >= d_next);   // a mismatch child survives
+    const bool ma_ok = match_r && (last || z >= d_next);                 // the match child survives
     uint32_t alive = 0;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         k2[b] = c.ix.C[b] + rk[b] + 1u;
         l2[b] = c.ix.C[b] + rl[b];
-        const bool ne = k2[b] <= l2[b];
+        const bool ne = need && k2[b] <= l2[b];
         alive |= (ne ? 1u : 0u) << b;
         const bool keep = (uint32_t)b == wi ? ma_ok : mm_ok;
         const uint32_t mm = (ne && keep) ? (32u << b) : 0u;
         if (last) leaf |= mm; else push |= mm;
     }
-    if (del_ok) push |= alive << 1;   // deletion of each b with a non-empty interval
+    if (del_ok) {
+        // deletion of each b with a non-empty interval; at i >= 1 the child deleting b = W[i]
+        // can only delete again (rules on)
+        uint32_t dm = alive & del_keep;
+        if (c.canon && !last && !more_gaps) dm &= ~(1u << wi);
+        push |= dm << 1;
+    }
 }
 
 // One call of InexRecur with no difference left (z = 0): only the match b = W[i] can continue,
@@ -169,18 +230,18 @@ __device__ __forceinline__ uint4 make_child(const uint4 &nd, int t, const uint32
     uint4 ch;
     ch.x = nd.x;
     if (t == 0) {
-        ch.y = (i - 1u) | ((z - 1u) << 8) | ((g + 1u) << 12);
+        ch.y = (i - 1u) | ((z - 1u) << 8) | ((g + 1u) << 12) | (kOpIns << 16);
         ch.z = nd.z;
         ch.w = nd.w;
     } else if (t <= 4) {
         const uint32_t b = (uint32_t)(t - 1);
-        ch.y = i | ((z - 1u) << 8) | ((g + 1u) << 12);
+        ch.y = i | ((z - 1u) << 8) | ((g + 1u) << 12) | (kOpDel << 16) | (b << 18);
         ch.z = pick4(k2, b);
         ch.w = pick4(l2, b);
     } else {
         const uint32_t b = (uint32_t)(t - 5);
         const uint32_t zc = b == wi ? z : z - 1u;
-        ch.y = (i - 1u) | (zc << 8) | (g << 12);
+        ch.y = (i - 1u) | (zc << 8) | (g << 12) | (b == wi ? 0u : (kOpMis << 16) | (b << 18));
         ch.z = pick4(k2, b);
         ch.w = pick4(l2, b);
     }
@@ -359,7 +420,7 @@ __global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk
         if (act) {
             mt = c.qmeta[nd.x];
             expand<I>(c, nd, mt, k2, l2, push, leaf, nb, wi);
-            my_nodes += 1;
+            my_nodes += nb ? 1u : 0u;
             my_blocks += nb;
         }
         // children with z' = 0 (every child but the match of a z = 1 node) go to E
@@ -480,7 +541,7 @@ __global__ void __launch_bounds__(256) k_inexact_plain(SearchCfg c, uint4 *stack
                     }
                 }
             }
-            my_nodes += 1;
+            my_nodes += nb ? 1u : 0u;
             my_blocks += nb;
             if (sp == 0 && !cur) have = false;
         }
@@ -957,7 +1018,7 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
     key.pair_capacity = pair_capacity; key.raw_cap = raw_cap; key.n_reads = n_reads;
     key.strands = sp->strands; key.z = sp->z; key.max_gaps = sp->max_gaps; key.interval = I;
     key.grid = (uint32_t)grid; key.block = (uint32_t)block; key.chunk = tu.chunk;
-    key.spill_cap = spill_cap; key.profile = prof ? 1u : 0u;
+    key.spill_cap = spill_cap; key.profile = prof ? 1u : 0u; key.canon = tu.canon;
 
     char *misc = (char *)h->s_misc.ptr;
     unsigned long long *d_raw_count = (unsigned long long *)misc;
@@ -1007,6 +1068,7 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
             c.raw_cap = raw_cap;
             c.stats = d_stats;
             c.err = h->d_err + kErrSearch;
+            c.canon = tu.canon;
             switch (I) {
                 case 32: crc = launch_search<32>(h, c, FM_KERNEL_PERSISTENT, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, nullptr, 0, 0, cs); break;
                 case 64: crc = launch_search<64>(h, c, FM_KERNEL_PERSISTENT, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, nullptr, 0, 0, cs); break;
@@ -1205,6 +1267,7 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
         c.raw_cap = raw_cap;
         c.stats = d_stats;
         c.err = h->d_err + kErrSearch;
+        c.canon = tu.canon;
         if (prof) FM_CUDA_TRY(h, cudaEventRecord(ev[1], st));
         switch (I) {
             case 32: rc = launch_search<32>(h, c, sp->kernel, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, (uint4 *)h->s_plain.ptr, cap, T, st); break;
@@ -1446,6 +1509,7 @@ int run_inexact_noalloc(fm_index *h, const uint8_t *reads, const uint32_t *offs,
     c.raw_cap = kNoAllocMaxRaw;
     c.stats = d_stats;
     c.err = h->d_err + kErrSearch;
+    c.canon = h->tune.canon;
     switch (h->interval) {
         case 32: rc = noalloc_launch<32>(h, c, stacks, st); break;
         case 64: rc = noalloc_launch<64>(h, c, stacks, st); break;

@@ -50,7 +50,7 @@ struct GraphKey {
     const void *reads, *offs, *counts, *offsets, *pairs, *stats;
     const void *qmeta, *raw, *spill, *group, *misc;
     uint64_t pair_capacity, raw_cap;
-    uint32_t n_reads, strands, z, max_gaps, interval, grid, block, chunk, spill_cap, profile;
+    uint32_t n_reads, strands, z, max_gaps, interval, grid, block, chunk, spill_cap, profile, canon;
     bool operator==(const GraphKey &o) const {
         return reads == o.reads && offs == o.offs && counts == o.counts && offsets == o.offsets &&
                pairs == o.pairs && stats == o.stats && qmeta == o.qmeta && raw == o.raw &&
@@ -58,7 +58,7 @@ struct GraphKey {
                pair_capacity == o.pair_capacity && raw_cap == o.raw_cap && n_reads == o.n_reads &&
                strands == o.strands && z == o.z && max_gaps == o.max_gaps &&
                interval == o.interval && grid == o.grid && block == o.block && chunk == o.chunk &&
-               spill_cap == o.spill_cap && profile == o.profile;
+               spill_cap == o.spill_cap && profile == o.profile && canon == o.canon;
     }
 };
 
@@ -68,6 +68,7 @@ struct Tuning {
     uint32_t chunk = 16;
     uint32_t plain_block = 128;
     uint32_t occ_q = 2;
+    uint32_t canon = 1;      // inexact search enumerates canonical alignments only
     uint32_t l2_fetch = 0;   // 0: leave the context's limit alone
 };
 

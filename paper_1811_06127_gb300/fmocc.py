@@ -59,7 +59,8 @@ class fm_search_params(C.Structure):
 class fm_tuning(C.Structure):
     _fields_ = [("warps_per_block", C.c_uint32), ("blocks_per_sm", C.c_uint32),
                 ("chunk", C.c_uint32), ("plain_block", C.c_uint32), ("graphs", C.c_uint32),
-                ("occ_per_thread", C.c_uint32), ("l2_fetch_bytes", C.c_uint32)]
+                ("occ_per_thread", C.c_uint32), ("l2_fetch_bytes", C.c_uint32),
+                ("canonical", C.c_uint32)]
 
 
 class fm_server_params(C.Structure):
@@ -383,10 +384,10 @@ def fm_inexact_fetch(h: Index, pairs: torch.Tensor, stream=None):
 
 
 def fm_set_tuning(h: Index, warps_per_block=0, blocks_per_sm=0, chunk=0, plain_block=0,
-                  graphs=0, occ_per_thread=0, l2_fetch_bytes=0):
-    """Zero keeps a knob; graphs: 1 on, 2 off."""
+                  graphs=0, occ_per_thread=0, l2_fetch_bytes=0, canonical=0):
+    """Zero keeps a knob; graphs and canonical: 1 on, 2 off."""
     t = fm_tuning(warps_per_block, blocks_per_sm, chunk, plain_block, graphs, occ_per_thread,
-                  l2_fetch_bytes)
+                  l2_fetch_bytes, canonical)
     _check(load_library().fm_set_tuning(h.ptr, C.byref(t)), h)
 
 
@@ -395,7 +396,8 @@ def fm_get_tuning(h: Index) -> dict:
     _check(load_library().fm_get_tuning(h.ptr, C.byref(t)), h)
     return {"warps_per_block": t.warps_per_block, "blocks_per_sm": t.blocks_per_sm,
             "chunk": t.chunk, "plain_block": t.plain_block, "graphs": t.graphs,
-            "occ_per_thread": t.occ_per_thread, "l2_fetch_bytes": t.l2_fetch_bytes}
+            "occ_per_thread": t.occ_per_thread, "l2_fetch_bytes": t.l2_fetch_bytes,
+            "canonical": t.canonical}
 
 
 def fm_probe_gather(buf: torch.Tensor, granule: int, threads: int, per_thread: int,

@@ -25,7 +25,11 @@ def case():
     R = synth.repeat_text(1811061280, 300_000, families=30, min_len=300, max_len=3000)
     reads = synth.sample_reads(81, R, 600, 40, 200, sub_rate=0.01, indel_rate=0.002,
                                both_strands=True, random_frac=0.05)
-    want = oracle.Index(R, "sais").inexact(reads.codes, reads.offs, 2, 1, strands=2)
+    ix = oracle.Index(R, "sais")
+    want = ix.inexact(reads.codes, reads.offs, 2, 1, strands=2, canonical=True)
+    plain = ix.inexact(reads.codes, reads.offs, 2, 1, strands=2)
+    for key in ("counts", "offsets", "pairs"):
+        assert np.array_equal(want[key], plain[key])
     return R, reads, want
 
 
@@ -91,4 +95,16 @@ def test_graph_off_and_truncation(fm, case):
         c, o, p = fm.fm_inexact(h, codes, offs, 2, 1, strands=2, counts=counts,
                                 offsets=offsets, pairs=small)
         _check(want, c, o, p)
+    h.close()
+
+
+def test_rejected_tuning_changes_nothing(fm):
+    h = fm.fm_build(synth.uniform_text(5, 5000))
+    before = fm.fm_get_tuning(h)
+    for bad in ({"warps_per_block": 4, "graphs": 3}, {"chunk": 8, "occ_per_thread": 3},
+                {"blocks_per_sm": 2, "l2_fetch_bytes": 48}, {"warps_per_block": 9}):
+        with pytest.raises(fm.FmError) as ei:
+            fm.fm_set_tuning(h, **bad)
+        assert ei.value.code == fm.FM_EINVAL
+        assert fm.fm_get_tuning(h) == before
     h.close()

@@ -180,21 +180,34 @@ def test_dcalc_matches_oracle(fm, interval):
     h.close()
 
 
-def _inexact_case(fm, R, reads, z, gaps, interval, kernels=("plain", "persistent")):
+def _inexact_case(fm, R, reads, z, gaps, interval, kernels=("plain", "persistent"),
+                  modes=("canonical", "listing")):
+    """Both kernels, with the canonical enumeration (default) and with every call of Listing 2:
+    result sets equal the oracle's Listing 2 sets, and node and block counts equal the
+    oracle's for the same enumeration."""
     h = fm.fm_build(R, interval=interval)
     ix = oracle.Index(R, "sais")
-    want = ix.inexact(reads.codes, reads.offs, z, gaps, strands=2, interval=interval)
+    want_c = ix.inexact(reads.codes, reads.offs, z, gaps, strands=2, interval=interval,
+                        canonical=True)
+    # the two enumerations report the same sets (pinned on the CPU); Listing 2's own run is
+    # skipped where its repeated subtrees make it too slow
+    want = ix.inexact(reads.codes, reads.offs, z, gaps, strands=2, interval=interval) \
+        if "listing" in modes else want_c
     codes, offs = fm.to_device_reads(reads)
-    for kern in kernels:
-        stats = torch.zeros(4, dtype=torch.int64, device="cuda")
-        counts, offsets, pairs = fm.fm_inexact(h, codes, offs, z, gaps, strands=2, kernel=kern,
-                                               stats=stats)
-        assert np.array_equal(_u32(counts), want["counts"]), kern
-        assert np.array_equal(offsets.cpu().numpy().astype(np.uint64), want["offsets"]), kern
-        assert np.array_equal(_u32(pairs), want["pairs"]), kern
-        st = stats.cpu().numpy()
-        assert st[0] == want["nodes"].sum(), kern
-        assert st[1] == want["blocks"].sum(), kern
+    for mode in modes:
+        fm.fm_set_tuning(h, canonical=1 if mode == "canonical" else 2)
+        ref = want_c if mode == "canonical" else want
+        for kern in kernels:
+            stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+            counts, offsets, pairs = fm.fm_inexact(h, codes, offs, z, gaps, strands=2,
+                                                   kernel=kern, stats=stats)
+            assert np.array_equal(_u32(counts), want["counts"]), (kern, mode)
+            assert np.array_equal(offsets.cpu().numpy().astype(np.uint64), want["offsets"]), \
+                (kern, mode)
+            assert np.array_equal(_u32(pairs), want["pairs"]), (kern, mode)
+            st = stats.cpu().numpy()
+            assert st[0] == ref["nodes"].sum(), (kern, mode)
+            assert st[1] == ref["blocks"].sum(), (kern, mode)
     h.close()
 
 
@@ -217,7 +230,8 @@ def test_inexact_intervals(fm, interval):
 def test_inexact_edge_reads(fm):
     """Length-0, length-1, length-255 reads, all-A reads and reads over a homopolymer text.
     (Over a homopolymer the literal recursion of Listing 2 reaches the same state by very many
-    indel placements, so the gap budget is kept small for the long reads.)"""
+    indel placements, so the gap budget is kept small for the long reads; the canonical
+    enumeration takes each placement once and runs z = 3 with 3 gaps on the long reads.)"""
     R = _text("homopolymer", 777)
     short = [np.zeros(0, np.uint8), np.array([0], np.uint8), np.array([3], np.uint8),
              np.zeros(12, np.uint8), np.array([0, 1], np.uint8), synth.uniform_text(4, 20)]
@@ -232,6 +246,19 @@ def test_inexact_edge_reads(fm):
     for z, g in ((0, 0), (2, 0), (2, 1)):
         _inexact_case(fm, R, batch(short + long_), z, g, 64)
     _inexact_case(fm, R, batch(short), 3, 3, 64)
+    _inexact_case(fm, R, batch(short + long_), 3, 3, 64, modes=("canonical",))
+
+
+def test_canonical_knob(fm):
+    h = fm.fm_build(_text("uniform", 5000))
+    assert fm.fm_get_tuning(h)["canonical"] == 1
+    fm.fm_set_tuning(h, canonical=2)
+    assert fm.fm_get_tuning(h)["canonical"] == 2
+    with pytest.raises(fm.FmError) as ei:
+        fm.fm_set_tuning(h, canonical=3)
+    assert ei.value.code == fm.FM_EINVAL
+    assert fm.fm_get_tuning(h)["canonical"] == 2
+    h.close()
 
 
 def test_inexact_truncation_and_fetch(fm):

@@ -70,6 +70,16 @@ MUTANTS = [
      "            if (p + d >= n) { /* suffix reaches $ first: smaller */\n                rel = -1;",
      "            if (p + d >= n) { /* suffix reaches $ first: smaller */\n                rel = 1;"),
     ("hamming window inclusive bound", "        if (mm <= z) hits++;", "        if (mm < z) hits++;"),
+    ("canonical: no match after any insertion",
+     "        if (W[i] == W[i + 1]) may_match = 0;", "        may_match = 0;"),
+    ("canonical: mismatch allowed after an insertion",
+     "        may_del = 0;\n        may_mis = 0;\n", "        may_del = 0;\n"),
+    ("canonical: deletion rule also at W[0]",
+     "        may_ins = 0;\n        if (i >= 1) {", "        may_ins = 0;\n        if (i >= 0) {"),
+    ("canonical: no insertion after any mismatch",
+     "        if (W[i] == lb) may_ins = 0;", "        may_ins = 0;"),
+    ("canonical: pass-through call counted as a node",
+     "    if (!may_del && !may_mis && !may_match) return;\n", ""),
 ]
 
 

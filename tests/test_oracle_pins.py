@@ -320,19 +320,47 @@ def test_dcalc_definition_and_lower_bound():
 # Listing 2
 # --------------------------------------------------------------------------------------------
 
-def brute_inexact(text, w, z, gaps, prune=False, interval=4):
+def canonical_pair_ok(prev, col, i, w):
+    """Whether column col may follow column prev in a canonical script (prev = None at the
+    start).  Columns: ("I",) insertion of w[i], ("D", b) deletion of reference symbol b,
+    ("M", b) match or mismatch with b against w[i]; prev was taken at read position i + 1
+    (insertion, match, mismatch) or i (deletion)."""
+    if prev is None or (prev[0] == "M" and prev[1] == w[i + 1]):
+        return True
+    if prev[0] == "I":      # shift the insertion left; mismatch or match first
+        return col[0] == "I" or (col[0] == "M" and col[1] == w[i] and w[i] != w[i + 1])
+    if prev[0] == "D":      # shift the deletion left (not past w[0]); no deletion+insertion
+        if col[0] == "I":
+            return False
+        if col[0] == "M" and i >= 1:
+            return col[1] == w[i] and w[i] != prev[1]
+        return True
+    # prev is a mismatch with prev[1] at w[i+1]
+    if col[0] == "I":
+        return w[i] != prev[1]
+    if col[0] == "D":
+        return col[1] != w[i + 1]
+    return True
+
+
+def brute_inexact(text, w, z, gaps, prune=False, interval=4, canonical=False):
     """Enumerate every alignment column script of Listing 2's grammar (processing w from its
     right end): insertion (consume w[i]), deletion (emit a reference symbol, i unchanged),
     match/mismatch (emit b, consume w[i]); cost <= z, indel columns <= gaps; stop at i < 0.
     Returns the set of intervals of the reference-side strings that occur in text, and the
     number of script prefixes (states) that reach i >= 0 with an occurring reference string
     (and, with prune, z_left >= D(i)) together with their checkpoint blocks of the given
-    width at rank positions k and l+1."""
+    width at rank positions k and l+1.  canonical: only scripts whose adjacent columns pass
+    canonical_pair_ok; a state counts only when a deletion (needs a gap and a difference
+    left), a mismatch (needs a difference left) or the match may follow it."""
     strings = set()
     D = brute_D(text, w)
     stats = [0, 0]
 
-    def rec(i, zl, g, x):
+    def ok(prev, col, i):
+        return not canonical or canonical_pair_ok(prev, col, i, w)
+
+    def rec(i, zl, g, x, prev):
         if zl < 0:
             return
         if x and x not in text:
@@ -343,17 +371,24 @@ def brute_inexact(text, w, z, gaps, prune=False, interval=4):
             if x:
                 strings.add(x)
             return
+        if g < gaps and ok(prev, ("I",), i):
+            rec(i - 1, zl - 1, g + 1, x, ("I",))
+        occ_child = any((col[0] == "D" and g < gaps and zl >= 1) or
+                        (col[0] == "M" and (col[1] == w[i] or zl >= 1))
+                        for col in [("D", b) for b in SYM] + [("M", b) for b in SYM]
+                        if ok(prev, col, i))
+        if not occ_child:
+            return
         k, l = brute_interval(text, x) if x else (0, len(text))
         stats[0] += 1
         stats[1] += 1 if k // interval == (l + 1) // interval else 2
-        if g < gaps:
-            rec(i - 1, zl - 1, g + 1, x)
         for b in SYM:
-            if g < gaps:
-                rec(i, zl - 1, g + 1, b + x)
-            rec(i - 1, zl - (b != w[i]), g, b + x)
+            if g < gaps and ok(prev, ("D", b), i):
+                rec(i, zl - 1, g + 1, b + x, ("D", b))
+            if ok(prev, ("M", b), i):
+                rec(i - 1, zl - (b != w[i]), g, b + x, ("M", b))
 
-    rec(len(w) - 1, z, 0, "")
+    rec(len(w) - 1, z, 0, "", None)
     out = set()
     for x in strings:
         k, l = brute_interval(text, x)
@@ -392,6 +427,8 @@ def test_inexact_bruteforce_tiny():
             for gaps in (0, 1, 2):
                 res = ix.inexact(codes, offs, z, gaps, strands=1, prune=True, interval=4)
                 res_np = ix.inexact(codes, offs, z, gaps, strands=1, prune=False, interval=4)
+                res_c = ix.inexact(codes, offs, z, gaps, strands=1, prune=True, interval=4,
+                                   canonical=True)
                 for q, W in enumerate(ws):
                     w = "".join(SYM[c] for c in W)
                     got = _pairs_of(res, q)
@@ -401,8 +438,76 @@ def test_inexact_bruteforce_tiny():
                     assert (int(res["nodes"][q]), int(res["blocks"][q])) == (nodes, blocks)
                     _, nodes, blocks = brute_inexact(text, w, z, gaps, prune=False)
                     assert (int(res_np["nodes"][q]), int(res_np["blocks"][q])) == (nodes, blocks)
+                    # canonical enumeration: Listing 2's intervals, the brute-force counts
+                    want_c, nodes_c, blocks_c = brute_inexact(text, w, z, gaps, prune=True,
+                                                              canonical=True)
+                    assert want_c == want, (text, w, z, gaps)
+                    assert _pairs_of(res_c, q) == want
+                    assert (int(res_c["nodes"][q]), int(res_c["blocks"][q])) == \
+                        (nodes_c, blocks_c), (text, w, z, gaps)
+                    assert nodes_c <= nodes
                     cases += 1
     assert cases > 500
+
+
+def _runs_text(rng, n):
+    parts, total = [], 0
+    while total < n:
+        r = np.full(int(rng.integers(1, 6)), int(rng.integers(0, 4)), dtype=np.uint8)
+        parts.append(r)
+        total += r.size
+    return np.concatenate(parts)[:n]
+
+
+def test_canonical_bruteforce_runs():
+    """Texts and reads made of runs of one base (where indels can sit in several places and
+    still spell one string), z up to 3: the canonical enumeration reports Listing 2's
+    intervals and its node and block counts equal the brute-force canonical scripts'."""
+    rng = np.random.default_rng(23)
+    cases = 0
+    for _ in range(12):
+        R = _runs_text(rng, int(rng.integers(10, 40)))
+        text = "".join(SYM[c] for c in R)
+        ix = oracle.Index(R, "naive")
+        ws = [_runs_text(rng, int(rng.integers(1, 7))) for _ in range(3)]
+        codes = np.concatenate(ws).astype(np.uint8)
+        offs = np.concatenate([[0], np.cumsum([w.size for w in ws])]).astype(np.uint32)
+        for z, gaps in ((1, 1), (2, 1), (2, 2), (3, 2), (3, 3)):
+            res = ix.inexact(codes, offs, z, gaps, strands=1, interval=4)
+            res_c = ix.inexact(codes, offs, z, gaps, strands=1, interval=4, canonical=True)
+            for q, W in enumerate(ws):
+                w = "".join(SYM[c] for c in W)
+                want, nodes_c, blocks_c = brute_inexact(text, w, z, gaps, prune=True,
+                                                        canonical=True)
+                assert _pairs_of(res_c, q) == _pairs_of(res, q) == want, (text, w, z, gaps)
+                assert (int(res_c["nodes"][q]), int(res_c["blocks"][q])) == (nodes_c, blocks_c)
+                cases += 1
+    assert cases >= 150
+
+
+@pytest.mark.parametrize("kind", ["runs", "homopolymer", "periodic", "repeat"])
+def test_canonical_same_results(kind):
+    """Canonical enumeration = Listing 2's result sets (both strands, z <= 3, gaps <= 3)
+    on texts where the same string is spelled by many scripts; it never expands more."""
+    rng = np.random.default_rng(29)
+    if kind == "runs":
+        R = _runs_text(rng, 4000)
+    elif kind == "homopolymer":
+        R = np.zeros(400, np.uint8)
+    elif kind == "periodic":
+        R = np.array([0, 1] * 1000, np.uint8)
+    else:
+        R = synth.repeat_text(31, 60_000, families=8, min_len=300, max_len=1500)
+    ix = oracle.Index(R, "sais")
+    reads = synth.sample_reads(37, R, 60, 1, 30, sub_rate=0.05, indel_rate=0.03,
+                               both_strands=True, random_frac=0.1)
+    for z, gaps in ((1, 1), (2, 1), (2, 2), (3, 1), (3, 3)):
+        a = ix.inexact(reads.codes, reads.offs, z, gaps, strands=2)
+        b = ix.inexact(reads.codes, reads.offs, z, gaps, strands=2, canonical=True)
+        for key in ("counts", "offsets", "pairs"):
+            assert np.array_equal(a[key], b[key]), (kind, z, gaps, key)
+        assert (b["nodes"] <= a["nodes"]).all()
+        assert b["nodes"].sum() < a["nodes"].sum()
 
 
 def test_inexact_hamming_identity_and_z0():
