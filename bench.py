@@ -43,9 +43,9 @@ BLOCK_BYTES = {32: 32, 64: 32, 128: 64, 256: 96}
 # DRAM bytes (read + write) per launch of the search kernel from one ncu capture
 # (profiles/k_inexact_persistent_2gbp_10m_reads_dram.md), by (interval, reference bp, reads):
 # reported only when the run matches that configuration
-# keyed by (interval, reference bp, reads, canonical enumeration on); an entry is removed when
-# the kernel changes and added back from a fresh capture
-TRAFFIC_NCU = {(64, 2_000_000_000, 10_000_000, True): 6.149307580416e12 + 1.235636736e9}
+# keyed by (interval, reference bp, reads, canonical enumeration on, interval-table depth); an
+# entry is removed when the kernel changes and added back from a fresh capture
+TRAFFIC_NCU = {}
 
 
 def parse():
@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--canonical", type=int, default=1, choices=[1, 2],
                     help="1: enumerate canonical alignments (same interval sets, fewer nodes); "
                          "2: every call of Listing 2")
+    ap.add_argument("--kmer-depth", type=int, default=0xFE,
+                    help="interval tables of short strings: 1..14 levels, 254 automatic "
+                         "(floor(log4(n+1)) - 2), 255 none")
     ap.add_argument("--tune-reads", type=int, default=200_000)
     ap.add_argument("--tune-cache", default=None, help="JSON cache of tuning results")
     ap.add_argument("--cpu-sample-reads", type=int, default=200_000)
@@ -272,7 +275,9 @@ def main():
     notes["build_s"] = time.time() - t0
     if tuned:
         autotune.apply(h, tuned)
-    fmocc.fm_set_tuning(h, canonical=args.canonical)
+    fmocc.fm_set_tuning(h, canonical=args.canonical, kmer_depth=args.kmer_depth)
+    kdepth = fmocc.fm_get_tuning(h)["kmer_depth"]
+    kdepth = 0 if kdepth == fmocc.KMER_OFF else kdepth
     del R
     codes_h = torch.from_numpy(reads.codes).pin_memory()
     offs_h = torch.from_numpy(reads.offs.view(np.int32)).pin_memory()
@@ -319,11 +324,12 @@ def main():
     st = stats.cpu().numpy()
     nodes_per_step = st[0] / args.steps
     blocks_per_step = st[1] / args.steps
+    tables_per_step = st[3] / args.steps   # 32-byte interval-table sectors
     bbytes = BLOCK_BYTES[args.interval]
     value = args.reads * args.steps * world / total_s
     # dominant kernel: the persistent search kernel, its own event-timed duration per launch
     k_ms = float(np.mean(search_ms))
-    alg_bytes = blocks_per_step * bbytes
+    alg_bytes = blocks_per_step * bbytes + tables_per_step * 32
     achieved = alg_bytes / (k_ms / 1000.0) / 1e9
     same = bool(torch.equal(p1, ref_pairs) and torch.equal(o1, ref_offsets))
 
@@ -404,6 +410,9 @@ def main():
                                 "kernel"),
                    "enumeration": ("canonical alignments (the interval sets of Listing 2)"
                                    if args.canonical == 1 else "every call of Listing 2"),
+                   "interval_tables": (f"strings of length <= {kdepth} expanded from tables "
+                                       f"({(2 << (2 * kdepth)) * 8 / 1e6:.0f} MB)"
+                                       if kdepth else "none"),
                    "reference_bp": args.ref_n, "reads_per_step": args.reads,
                    "queries_per_step": nq, "interval": args.interval,
                    "tuning": ({k: tuned[k] for k in ("interval", "warps_per_block",
@@ -414,18 +423,21 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
                      "traffic": TRAFFIC_NCU.get((args.interval, args.ref_n, args.reads,
-                                                 args.canonical == 1)),
+                                                 args.canonical == 1, kdepth)),
                      "kernel": "k_inexact_persistent", "kernel_ms": k_ms,
                      "gather_ceiling": ceil_main,
                      "blocks_per_s_over_gather_ceiling": (blocks_per_step / (k_ms / 1000) / 1e9
                                                           / ceil_main["g_gathers_s"]),
                      "algorithmic_bytes": alg_bytes, "peak_kind": peak_kind,
-                     "per_unit": f"{bbytes} B per checkpoint block read, "
-                                 f"{blocks_per_step / max(nodes_per_step, 1):.3f} blocks per node, "
-                                 f"{nodes_per_step / nq:.1f} nodes per query"},
+                     "per_unit": f"{bbytes} B per checkpoint block read and 32 B per "
+                                 f"interval-table sector read; "
+                                 f"{blocks_per_step / max(nodes_per_step, 1):.3f} blocks and "
+                                 f"{tables_per_step / max(nodes_per_step, 1):.3f} table sectors "
+                                 f"per node, {nodes_per_step / nq:.1f} nodes per query"},
         "gpu_launches": launches,
         "clocks": clocks,
         "search": {"nodes_per_step": nodes_per_step, "blocks_per_step": blocks_per_step,
+                   "table_sectors_per_step": tables_per_step,
                    "intervals_per_step": int(ref_offsets[-1].item()),
                    "bit_exact_repeat": same, "step_ms": step_ms,
                    "profile_last": prof.as_dict()},

@@ -164,7 +164,8 @@ typedef struct fm_search_params {
                               fm_tuning.canonical on, those of the canonical enumeration),
                           [1] checkpoint blocks read by those expansions (1 when k and l+1
                               share a block, else 2), [2] intervals reported before
-                              deduplication, [3] reserved */
+                              deduplication, [3] interval-table sectors read (32 bytes each;
+                              see fm_tuning.kmer_depth) */
     fm_profile *profile; /* optional host pointer, filled by a successful call */
 } fm_search_params;
 
@@ -320,7 +321,25 @@ typedef struct fm_tuning {
                                    spelled twice by alignments of the same cost; the reported
                                    intervals are those of Listing 2, the nodes fewer.  2: every
                                    call of Listing 2 (stats then count its nodes exactly) */
+    uint32_t kmer_depth;        /* interval tables of short strings (Sec. 4.2 leaves the
+                                   memory-bound search to better cache locality of the
+                                   FM-index; this is one such method): for every string X of
+                                   length j <= depth, the interval Listing 1 reaches after
+                                   reading X, and whether X occurs.  Search nodes whose string
+                                   is shorter than depth are expanded from the tables, with no
+                                   checkpoint-block read; exact search starts depth steps in.
+                                   Results, and node counts, are unchanged; stats[1] counts
+                                   only checkpoint blocks.  Values: 1..14 the depth
+                                   (2 x 4^depth x 8 bytes of device memory, built on the first
+                                   search that needs them); FM_KMER_AUTO (default) the depth
+                                   floor(log4(n + 1)) - 2, clamped to [0, 14] (13 at n = 2e9,
+                                   1.07 GB);
+                                   FM_KMER_OFF none.  fm_get_tuning reports the depth in effect
+                                   (FM_KMER_OFF for none) */
 } fm_tuning;
+
+#define FM_KMER_AUTO 0xfeu
+#define FM_KMER_OFF 0xffu
 
 int fm_set_tuning(fm_index *h, const fm_tuning *t);
 int fm_get_tuning(const fm_index *h, fm_tuning *t);

@@ -112,6 +112,8 @@ void release(fm_index *h) {
     cudaFree(h->d_rev);
     cudaFree(h->d_sa_sample);
     cudaFree(h->d_err);
+    cudaFree(h->d_kt);
+    cudaFree(h->d_kbits);
     fm::Scratch *ss[] = {&h->s_qmeta, &h->s_raw, &h->s_spill, &h->s_group, &h->s_scan, &h->s_plain,
                          &h->s_misc};
     for (auto *s : ss) cudaFree(s->ptr);
@@ -239,6 +241,7 @@ int fm_info(const fm_index *h, fm_info_t *out) {
     out->n_blocks = h->n_blocks;
     out->sa_sample_rate = h->sa_rate;
     out->bytes_device = h->n_blocks * h->bbytes * (h->has_rev ? 2 : 1) + h->n_sa_sample * 4;
+    if (h->kt_depth) out->bytes_device += (2ull << (2 * h->kt_depth)) * (8 + 1.0 / 8);
     out->has_reverse = h->has_rev ? 1 : 0;
     out->device = h->device;
     return FM_OK;
@@ -484,6 +487,8 @@ int fm_set_tuning(fm_index *h, const fm_tuning *t) {
     if (t->l2_fetch_bytes && t->l2_fetch_bytes != 32 && t->l2_fetch_bytes != 64 && t->l2_fetch_bytes != 128)
         return set_error(h, FM_EINVAL, "l2_fetch_bytes must be 32, 64 or 128");
     if (t->canonical > 2) return set_error(h, FM_EINVAL, "canonical must be 0, 1 or 2");
+    if (t->kmer_depth > fm::kMaxKmerDepth && t->kmer_depth != FM_KMER_AUTO && t->kmer_depth != FM_KMER_OFF)
+        return set_error(h, FM_EINVAL, "kmer_depth must be 0, 1..14, FM_KMER_AUTO or FM_KMER_OFF");
     if (t->warps_per_block) h->tune.warps_per_block = t->warps_per_block;
     if (t->blocks_per_sm) h->tune.blocks_per_sm = t->blocks_per_sm;
     if (t->chunk) h->tune.chunk = t->chunk;
@@ -491,6 +496,7 @@ int fm_set_tuning(fm_index *h, const fm_tuning *t) {
     if (t->occ_per_thread) h->tune.occ_q = t->occ_per_thread;
     if (t->l2_fetch_bytes) h->tune.l2_fetch = t->l2_fetch_bytes;
     if (t->canonical) h->tune.canon = t->canonical == 1 ? 1u : 0u;
+    if (t->kmer_depth) h->tune.kmer = t->kmer_depth;
     if (t->graphs) h->use_graphs = t->graphs == 1;
     return FM_OK;
 }
@@ -506,6 +512,8 @@ int fm_get_tuning(const fm_index *h, fm_tuning *t) {
     t->occ_per_thread = h->tune.occ_q;
     t->l2_fetch_bytes = h->tune.l2_fetch;
     t->canonical = h->tune.canon ? 1u : 2u;
+    const uint32_t kd = fm::kmer_depth_for(h);
+    t->kmer_depth = kd ? kd : FM_KMER_OFF;
     return FM_OK;
 }
 

@@ -62,8 +62,20 @@ __device__ __forceinline__ uint32_t w_at(const uint8_t *reads, const uint4 &mt, 
 }
 
 // Node word y: bits 0-7 i, 8-11 z left, 12-15 indel columns used, 16-17 the operation that
-// created the node (kOpMatch also for a root), 18-19 its reference symbol (mismatch, deletion).
+// created the node (kOpMatch also for a root), 18-19 its reference symbol (mismatch, deletion),
+// 20-23 the length d of the node's reference string X and bit 24 (kShallow) set while
+// d < the interval-table depth.  A shallow node holds code(X) in z (w unused) instead of X's
+// interval: its children come from the tables' occurrence bits, and at the table depth from
+// one 32-byte sector of intervals, with no checkpoint block read.
 constexpr uint32_t kOpMatch = 0u, kOpMis = 1u, kOpIns = 2u, kOpDel = 3u;
+constexpr uint32_t kShallow = 1u << 24;
+constexpr uint32_t kDepthBits = 15u << 20;
+// step cost word of expand / exact_step: checkpoint blocks read in bits 0-15, interval-table
+// sectors read in bits 16-31; accumulated per thread as blocks + (sectors << 32)
+constexpr uint32_t kTabRead = 1u << 16;
+__device__ __forceinline__ unsigned long long step_cost(uint32_t nb) {
+    return (unsigned long long)(nb & 0xffffu) + ((unsigned long long)(nb >> 16) << 32);
+}
 
 // One expansion: the eight-Occ step of Listing 2 (rank(c, k) and rank(c, l+1) for c in ACGT
 // from one or two checkpoint blocks), then the children.  Every lane runs the same code, so
@@ -92,7 +104,8 @@ constexpr uint32_t kOpMatch = 0u, kOpMis = 1u, kOpIns = 2u, kOpDel = 3u;
 template <int I>
 __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, const uint4 &mt,
                                        uint32_t k2[4], uint32_t l2[4], uint32_t &push,
-                                       uint32_t &leaf, uint32_t &nblocks, uint32_t &wi_out) {
+                                       uint32_t &leaf, uint32_t &nblocks, uint32_t &counted,
+                                       uint32_t &wi_out) {
     const int i = (int)(nd.y & 255u);
     const uint32_t z = (nd.y >> 8) & 15u;
     const uint32_t g = (nd.y >> 12) & 15u;
@@ -127,9 +140,25 @@ __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, cons
     const bool need = (gap_ok && del_r) || (z >= 1u && mis_r) || match_r;
     // a new indel child can take another indel only with a gap and a difference to spare
     const bool more_gaps = g + 1u < c.max_gaps && z >= 2u;
-    uint32_t rk[4] = {0, 0, 0, 0}, rl[4] = {0, 0, 0, 0};
+    const bool shallow = (nd.y & kShallow) != 0u;
+    const uint32_t d = (nd.y >> 20) & 15u;
+    uint32_t alive = 0;   // bit b: the child string bX occurs
     nblocks = 0;
-    if (need) {
+    counted = need ? 1u : 0u;
+    if (need && shallow) {
+        // k holds code(X); the children's codes are 4 code(X) + b
+        alive = kt_occ4(c.ix, d + 1u, k);
+        if (d + 1u < c.ix.kdepth) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                k2[b] = 4u * k + (uint32_t)b;
+                l2[b] = 0u;
+            }
+        } else {
+            kt_get4(c.ix, d + 1u, k, k2, l2);
+            nblocks = kTabRead;
+        }
+    } else if (need) {
         const uint32_t pk = k, pl = l + 1u;
         const uint32_t jk = pk / I, jl = pl / I;
         const uint32_t ok = pk - jk * I, ol = pl - jl * I;
@@ -143,8 +172,15 @@ __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, cons
             load_block<I>(c.ix.blocks, jl, ol, Bl);
             nblocks = 2;
         }
+        uint32_t rk[4], rl[4];
         rank4_in<I>(Bk, jk, pk, c.ix.dollar, rk);
         rank4_in<I>(Bl, jl, pl, c.ix.dollar, rl);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            k2[b] = c.ix.C[b] + rk[b] + 1u;
+            l2[b] = c.ix.C[b] + rl[b];
+            alive |= (k2[b] <= l2[b] ? 1u : 0u) << b;
+        }
     }
     const uint32_t d_here = d_at(mt, i);
     const uint32_t d_next = d_at(mt, i - 1);
@@ -156,20 +192,16 @@ __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, cons
     // only insert again when W[i-1] = W[i] (rules on)
     if (gap_ok && ins_r) {
         if (last) {
-            if (k >= 1u) leaf |= 1u;
+            if (shallow ? d >= 1u : k >= 1u) leaf |= 1u;   // X non-empty
         } else if (z - 1u >= d_next && (wp != wi || more_gaps)) {
             push |= 1u;
         }
     }
     const bool mm_ok = z >= 1u && mis_r && (last || z - 1u >= d_next);   // a mismatch child survives
     const bool ma_ok = match_r && (last || z >= d_next);                 // the match child survives
-    uint32_t alive = 0;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-        k2[b] = c.ix.C[b] + rk[b] + 1u;
-        l2[b] = c.ix.C[b] + rl[b];
-        const bool ne = need && k2[b] <= l2[b];
-        alive |= (ne ? 1u : 0u) << b;
+        const bool ne = (alive >> b) & 1u;
         const bool keep = (uint32_t)b == wi ? ma_ok : mm_ok;
         const uint32_t mm = (ne && keep) ? (32u << b) : 0u;
         if (last) leaf |= mm; else push |= mm;
@@ -194,27 +226,44 @@ __device__ __forceinline__ void exact_step(const SearchCfg &c, const uint4 &nd, 
     const uint32_t i = nd.y & 255u;
     const uint32_t b = w_at(c.reads, mt, i);
     const uint32_t k = nd.z, l = nd.w;
-    const uint32_t pk = k, pl = l + 1u;
-    const uint32_t jk = pk / I, jl = pl / I;
-    const uint32_t ok = pk - jk * I, ol = pl - jl * I;
-    Blk<I> Bk, Bl;
-    if (jk == jl) {
-        load_block<I>(c.ix.blocks, jk, ok > ol ? ok : ol, Bk);
-        Bl = Bk;
-        nblocks = 1;
+    uint32_t k2 = 0u, l2 = 0u, ybits = nd.y & 0xf000u;   // z = 0, created by a match
+    bool alive;
+    if (nd.y & kShallow) {
+        const uint32_t d = (nd.y >> 20) & 15u, code = 4u * k + b;
+        nblocks = 0;
+        alive = kt_occ1(c.ix, d + 1u, code) != 0u;
+        if (d + 1u < c.ix.kdepth && i > 0u) {
+            k2 = code;
+            ybits |= kShallow | ((d + 1u) << 20);
+        } else if (alive) {   // the table depth, or a result (its interval)
+            const uint2 kl = kt_get(c.ix, d + 1u, code);
+            k2 = kl.x;
+            l2 = kl.y;
+            nblocks = kTabRead;
+        }
     } else {
-        load_block<I>(c.ix.blocks, jk, ok, Bk);
-        load_block<I>(c.ix.blocks, jl, ol, Bl);
-        nblocks = 2;
+        const uint32_t pk = k, pl = l + 1u;
+        const uint32_t jk = pk / I, jl = pl / I;
+        const uint32_t ok = pk - jk * I, ol = pl - jl * I;
+        Blk<I> Bk, Bl;
+        if (jk == jl) {
+            load_block<I>(c.ix.blocks, jk, ok > ol ? ok : ol, Bk);
+            Bl = Bk;
+            nblocks = 1;
+        } else {
+            load_block<I>(c.ix.blocks, jk, ok, Bk);
+            load_block<I>(c.ix.blocks, jl, ol, Bl);
+            nblocks = 2;
+        }
+        // C[b] by select: a runtime index into the parameter struct would copy it to local memory
+        const uint32_t cb = b == 0 ? c.ix.C[0] : (b == 1 ? c.ix.C[1] : (b == 2 ? c.ix.C[2] : c.ix.C[3]));
+        k2 = cb + rank1_in<I>(Bk, jk, pk, c.ix.dollar, b) + 1u;
+        l2 = cb + rank1_in<I>(Bl, jl, pl, c.ix.dollar, b);
+        alive = k2 <= l2;
     }
-    // C[b] by select: a runtime index into the parameter struct would copy it to local memory
-    const uint32_t cb = b == 0 ? c.ix.C[0] : (b == 1 ? c.ix.C[1] : (b == 2 ? c.ix.C[2] : c.ix.C[3]));
-    const uint32_t k2 = cb + rank1_in<I>(Bk, jk, pk, c.ix.dollar, b) + 1u;
-    const uint32_t l2 = cb + rank1_in<I>(Bl, jl, pl, c.ix.dollar, b);
-    const bool alive = k2 <= l2;
     is_leaf = alive && i == 0u;
     survive = alive && i > 0u && d_at(mt, (int)i - 1) == 0u;
-    out = make_uint4(nd.x, (i - 1u) | (nd.y & 0xf000u), k2, l2);
+    out = make_uint4(nd.x, (i - 1u) | ybits, k2, l2);
 }
 
 __device__ __forceinline__ uint32_t pick4(const uint32_t v[4], uint32_t b) {
@@ -223,42 +272,51 @@ __device__ __forceinline__ uint32_t pick4(const uint32_t v[4], uint32_t b) {
 
 // child number t (0 insertion, 1..4 deletion, 5..8 match/mismatch) of node nd
 __device__ __forceinline__ uint4 make_child(const uint4 &nd, int t, const uint32_t k2[4],
-                                            const uint32_t l2[4], uint32_t wi) {
+                                            const uint32_t l2[4], uint32_t wi, uint32_t kdepth) {
     const uint32_t i = nd.y & 255u;
     const uint32_t z = (nd.y >> 8) & 15u;
     const uint32_t g = (nd.y >> 12) & 15u;
+    const uint32_t d = (nd.y >> 20) & 15u;
+    // a child one symbol longer stays shallow below the table depth
+    const uint32_t sh = ((nd.y & kShallow) && d + 1u < kdepth) ? (kShallow | ((d + 1u) << 20)) : 0u;
     uint4 ch;
     ch.x = nd.x;
     if (t == 0) {
-        ch.y = (i - 1u) | ((z - 1u) << 8) | ((g + 1u) << 12) | (kOpIns << 16);
+        ch.y = (i - 1u) | ((z - 1u) << 8) | ((g + 1u) << 12) | (kOpIns << 16) |
+               (nd.y & (kShallow | kDepthBits));
         ch.z = nd.z;
         ch.w = nd.w;
     } else if (t <= 4) {
         const uint32_t b = (uint32_t)(t - 1);
-        ch.y = i | ((z - 1u) << 8) | ((g + 1u) << 12) | (kOpDel << 16) | (b << 18);
+        ch.y = i | ((z - 1u) << 8) | ((g + 1u) << 12) | (kOpDel << 16) | (b << 18) | sh;
         ch.z = pick4(k2, b);
         ch.w = pick4(l2, b);
     } else {
         const uint32_t b = (uint32_t)(t - 5);
         const uint32_t zc = b == wi ? z : z - 1u;
-        ch.y = (i - 1u) | (zc << 8) | (g << 12) | (b == wi ? 0u : (kOpMis << 16) | (b << 18));
+        ch.y = (i - 1u) | (zc << 8) | (g << 12) | (b == wi ? 0u : (kOpMis << 16) | (b << 18)) | sh;
         ch.z = pick4(k2, b);
         ch.w = pick4(l2, b);
     }
     return ch;
 }
 
-__device__ __forceinline__ uint32_t leaf_k(const uint4 &nd, int t, const uint32_t k2[4]) {
-    return t == 0 ? nd.z : pick4(k2, (uint32_t)(t - 1) & 3u);
-}
-__device__ __forceinline__ uint32_t leaf_l(const uint4 &nd, int t, const uint32_t l2[4]) {
-    return t == 0 ? nd.w : pick4(l2, (uint32_t)(t - 1) & 3u);
+// interval of leaf child t (0 insertion, 5..8 match/mismatch) of node nd
+__device__ __forceinline__ uint2 leaf_of(const SearchCfg &c, const uint4 &nd, int t,
+                                         const uint32_t k2[4], const uint32_t l2[4]) {
+    const bool sh = (nd.y & kShallow) != 0u;
+    const uint32_t d = (nd.y >> 20) & 15u;
+    if (t == 0) return sh ? kt_get(c.ix, d, nd.z) : make_uint2(nd.z, nd.w);
+    const uint32_t b = (uint32_t)(t - 1) & 3u;
+    if (sh && d + 1u < c.ix.kdepth) return kt_get(c.ix, d + 1u, pick4(k2, b));
+    return make_uint2(pick4(k2, b), pick4(l2, b));
 }
 
 __device__ __forceinline__ uint4 root_of(const SearchCfg &c, uint32_t q, const uint4 &mt,
                                          bool &ok) {
     const uint32_t m = mt.w & 255u;
     ok = m >= 1u && c.z >= d_at(mt, (int)m - 1);
+    if (c.ix.kdepth) return make_uint4(q, (m - 1u) | (c.z << 8) | kShallow, 0u, 0u);   // X empty
     return make_uint4(q, (m - 1u) | (c.z << 8), 0u, c.ix.n);
 }
 
@@ -288,8 +346,10 @@ __device__ __forceinline__ void emit_leaves(const SearchCfg &c, int lane, bool a
     while (mset) {
         const int t = __ffs(mset) - 1;
         mset &= mset - 1;
-        if (pos < c.raw_cap)
-            c.raw[pos] = make_uint4(nd.x, leaf_k(nd, t, k2), leaf_l(nd, t, l2), 0u);
+        if (pos < c.raw_cap) {
+            const uint2 kl = leaf_of(c, nd, t, k2, l2);
+            c.raw[pos] = make_uint4(nd.x, kl.x, kl.y, 0u);
+        }
         ++pos;
     }
 }
@@ -368,12 +428,12 @@ __global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk
                 if (a0) {
                     exact_step<I>(c, n0, m0, c0, s0, f0, b0);
                     my_nodes += 1;
-                    my_blocks += b0;
+                    my_blocks += step_cost(b0);
                 }
                 if (a1) {
                     exact_step<I>(c, n1, m1, c1, s1, f1, b1);
                     my_nodes += 1;
-                    my_blocks += b1;
+                    my_blocks += step_cost(b1);
                 }
             }
             const uint32_t bal0 = __ballot_sync(FULL, s0);
@@ -419,9 +479,10 @@ __global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk
         uint32_t k2[4] = {0, 0, 0, 0}, l2[4] = {0, 0, 0, 0}, push = 0, leaf = 0, nb = 0, wi = 0;
         if (act) {
             mt = c.qmeta[nd.x];
-            expand<I>(c, nd, mt, k2, l2, push, leaf, nb, wi);
-            my_nodes += nb ? 1u : 0u;
-            my_blocks += nb;
+            uint32_t cn = 0;
+            expand<I>(c, nd, mt, k2, l2, push, leaf, nb, cn, wi);
+            my_nodes += cn;
+            my_blocks += step_cost(nb);
         }
         // children with z' = 0 (every child but the match of a z = 1 node) go to E
         const uint32_t z = (nd.y >> 8) & 15u;
@@ -451,7 +512,7 @@ __global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk
             while (mset) {
                 const int t = __ffs(mset) - 1;
                 mset &= mset - 1;
-                const uint4 chd = make_child(nd, t, k2, l2, wi);
+                const uint4 chd = make_child(nd, t, k2, l2, wi, c.ix.kdepth);
                 if ((emask >> t) & 1u) st[stk - 1 - (epos++)] = chd;
                 else st[gpos++] = chd;
             }
@@ -469,7 +530,8 @@ __global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk
         }
         if (lane == 0) {
             atomicAdd(c.stats + 0, my_nodes);
-            atomicAdd(c.stats + 1, my_blocks);
+            atomicAdd(c.stats + 1, my_blocks & 0xffffffffull);
+            atomicAdd(c.stats + 3, my_blocks >> 32);
         }
     }
 }
@@ -509,6 +571,7 @@ __global__ void __launch_bounds__(256) k_inexact_plain(SearchCfg c, uint4 *stack
         if (!__any_sync(FULL, act)) break;
         uint4 nd = make_uint4(0, 0, 0, 0);
         uint32_t k2[4] = {0, 0, 0, 0}, l2[4] = {0, 0, 0, 0}, push = 0, leaf = 0, nb = 0, wi = 0;
+        uint32_t counted = 1;   // an exact step is always a counted node
         bool ex_leaf = false;
         uint4 ex_out = make_uint4(0, 0, 0, 0);
         if (act) {
@@ -528,21 +591,21 @@ __global__ void __launch_bounds__(256) k_inexact_plain(SearchCfg c, uint4 *stack
                     cur = true;
                 }
             } else {
-                expand<I>(c, nd, mt, k2, l2, push, leaf, nb, wi);
+                expand<I>(c, nd, mt, k2, l2, push, leaf, nb, counted, wi);
                 uint32_t mset = push;
                 while (mset) {
                     const int t = __ffs(mset) - 1;
                     mset &= mset - 1;
                     if (sp < cap) {
-                        stacks[(size_t)sp * T + tid] = make_child(nd, t, k2, l2, wi);
+                        stacks[(size_t)sp * T + tid] = make_child(nd, t, k2, l2, wi, c.ix.kdepth);
                         ++sp;
                     } else {
                         atomicOr(c.err, kErrStack);
                     }
                 }
             }
-            my_nodes += nb ? 1u : 0u;
-            my_blocks += nb;
+            my_nodes += counted;
+            my_blocks += step_cost(nb);
             if (sp == 0 && !cur) have = false;
         }
         emit_leaves(c, lane, act, nd, leaf, k2, l2);
@@ -563,7 +626,8 @@ __global__ void __launch_bounds__(256) k_inexact_plain(SearchCfg c, uint4 *stack
         }
         if (lane == 0) {
             atomicAdd(c.stats + 0, my_nodes);
-            atomicAdd(c.stats + 1, my_blocks);
+            atomicAdd(c.stats + 1, my_blocks & 0xffffffffull);
+            atomicAdd(c.stats + 3, my_blocks >> 32);
         }
     }
 }
@@ -736,6 +800,7 @@ __global__ void k_add_stats(const unsigned long long *__restrict__ in,
         out[0] += in[0];
         out[1] += in[1];
         out[2] += *raw;
+        out[3] += in[3];
     }
 }
 
@@ -1019,6 +1084,7 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
     key.strands = sp->strands; key.z = sp->z; key.max_gaps = sp->max_gaps; key.interval = I;
     key.grid = (uint32_t)grid; key.block = (uint32_t)block; key.chunk = tu.chunk;
     key.spill_cap = spill_cap; key.profile = prof ? 1u : 0u; key.canon = tu.canon;
+    key.kt = h->d_kt; key.kdepth = h->kt_depth;
 
     char *misc = (char *)h->s_misc.ptr;
     unsigned long long *d_raw_count = (unsigned long long *)misc;
@@ -1161,6 +1227,7 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
 int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
                 const fm_search_params *sp, uint32_t *counts, uint64_t *offsets, uint32_t *pairs,
                 uint64_t pair_capacity, uint64_t *pairs_needed, cudaStream_t st) {
+    if (int krc = ensure_kmer(h, st)) return krc;
     if (h->use_graphs && sp->kernel != FM_KERNEL_PLAIN && n_reads > 0) {
         bool fallback = true;
         const int grc = run_inexact_graph(h, reads, offs, n_reads, sp, counts, offsets, pairs,

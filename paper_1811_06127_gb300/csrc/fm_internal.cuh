@@ -37,6 +37,15 @@ struct IndexView {
     uint32_t n;              // reference length
     uint32_t dollar;         // row holding $
     uint32_t C[5];
+    // Interval tables of short strings (0 levels: none).  For every string X of length j <= kdepth,
+    // with code(X) = sum_t X[t] 4^t (X[0], the symbol a backward step prepends last, least
+    // significant, so the four one-symbol extensions bX of X have the consecutive codes
+    // 4 code(X) + b): kt[4^j + code(X)] = the interval Listing 1 reaches from [0, n] after
+    // reading X (also when empty: k = l + 1 is its insertion point), and bit 4^j + code(X) of
+    // kbits = X occurs (k <= l).
+    const uint2 *kt;
+    const uint32_t *kbits;
+    uint32_t kdepth;
 };
 
 // Per-search device pointers (scratch owned by the handle).
@@ -48,9 +57,10 @@ struct Scratch {
 // What a captured search graph depends on; a call with another key captures a new graph.
 struct GraphKey {
     const void *reads, *offs, *counts, *offsets, *pairs, *stats;
-    const void *qmeta, *raw, *spill, *group, *misc;
+    const void *qmeta, *raw, *spill, *group, *misc, *kt;
     uint64_t pair_capacity, raw_cap;
-    uint32_t n_reads, strands, z, max_gaps, interval, grid, block, chunk, spill_cap, profile, canon;
+    uint32_t n_reads, strands, z, max_gaps, interval, grid, block, chunk, spill_cap, profile, canon,
+        kdepth;
     bool operator==(const GraphKey &o) const {
         return reads == o.reads && offs == o.offs && counts == o.counts && offsets == o.offsets &&
                pairs == o.pairs && stats == o.stats && qmeta == o.qmeta && raw == o.raw &&
@@ -58,7 +68,8 @@ struct GraphKey {
                pair_capacity == o.pair_capacity && raw_cap == o.raw_cap && n_reads == o.n_reads &&
                strands == o.strands && z == o.z && max_gaps == o.max_gaps &&
                interval == o.interval && grid == o.grid && block == o.block && chunk == o.chunk &&
-               spill_cap == o.spill_cap && profile == o.profile && canon == o.canon;
+               spill_cap == o.spill_cap && profile == o.profile && canon == o.canon && kt == o.kt &&
+               kdepth == o.kdepth;
     }
 };
 
@@ -69,6 +80,7 @@ struct Tuning {
     uint32_t plain_block = 128;
     uint32_t occ_q = 2;
     uint32_t canon = 1;      // inexact search enumerates canonical alignments only
+    uint32_t kmer = FM_KMER_AUTO;   // interval-table depth setting (FM_KMER_AUTO, FM_KMER_OFF, 1..14)
     uint32_t l2_fetch = 0;   // 0: leave the context's limit alone
 };
 
@@ -90,6 +102,9 @@ struct fm_index {
     uint64_t sa_rate = 32;
     uint64_t n_sa_sample = 0;
     uint32_t *d_err = nullptr;       // device error word (1 word per call kind)
+    uint2 *d_kt = nullptr;           // interval tables of short strings (forward index)
+    uint32_t *d_kbits = nullptr;     // their occurrence bits
+    uint32_t kt_depth = 0;           // levels built (0: none)
     // grow-on-demand scratch of the search calls
     fm::Scratch s_qmeta, s_raw, s_spill, s_group, s_scan, s_plain, s_misc;
     fm::Tuning tune;
@@ -138,6 +153,10 @@ int launch_locate(fm_index *h, const uint32_t *rows, uint64_t N, uint32_t *pos,
                   unsigned long long *steps, cudaStream_t st);
 int launch_exact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
                  uint32_t *k_out, uint32_t *l_out, cudaStream_t st);
+// interval tables: the depth the tuning asks for on this index, and (re)building them to it
+uint32_t kmer_depth_for(const fm_index *h);
+int ensure_kmer(fm_index *h, cudaStream_t st);
+constexpr uint32_t kMaxKmerDepth = 14;
 // D lower bound per query; qmeta (uint4 per query) and/or D_out (uint8 per position)
 int launch_dcalc(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
                  uint32_t strands, uint4 *qmeta, uint8_t *D_out, cudaStream_t st);
@@ -221,6 +240,29 @@ __device__ __forceinline__ void load_block(const uint8_t *blocks, uint32_t j, ui
             B.w[7] = u64of(e.z, e.w);
         }
     }
+}
+
+// Interval-table access (see IndexView): level j starts at entry (and bit) 4^j.
+__device__ __forceinline__ uint32_t kt_base(uint32_t j) { return 1u << (2u * j); }
+__device__ __forceinline__ uint2 kt_get(const IndexView &ix, uint32_t j, uint32_t code) {
+    return __ldg(ix.kt + kt_base(j) + code);
+}
+// occurrence bits of the four extensions 4c .. 4c+3 at level j >= 1 (bit b: extension b)
+__device__ __forceinline__ uint32_t kt_occ4(const IndexView &ix, uint32_t j, uint32_t c) {
+    const uint32_t bit = kt_base(j) + 4u * c;
+    return (__ldg(ix.kbits + (bit >> 5)) >> (bit & 31u)) & 15u;
+}
+__device__ __forceinline__ uint32_t kt_occ1(const IndexView &ix, uint32_t j, uint32_t code) {
+    const uint32_t bit = kt_base(j) + code;
+    return (__ldg(ix.kbits + (bit >> 5)) >> (bit & 31u)) & 1u;
+}
+// intervals of the four extensions 4c .. 4c+3 at level j >= 1: one 32-byte sector
+__device__ __forceinline__ void kt_get4(const IndexView &ix, uint32_t j, uint32_t c, uint32_t k[4],
+                                        uint32_t l[4]) {
+    uint4 a, b;
+    ldg256(ix.kt + kt_base(j) + 4u * c, a, b);
+    k[0] = a.x; l[0] = a.y; k[1] = a.z; l[1] = a.w;
+    k[2] = b.x; l[2] = b.y; k[3] = b.z; l[3] = b.w;
 }
 
 // Mask of the low `width` bits (width in [0, 32]).

@@ -17,12 +17,18 @@ IndexView view_fwd(const fm_index *h) {
     v.n = (uint32_t)h->n;
     v.dollar = (uint32_t)h->dollar;
     for (int i = 0; i < 5; ++i) v.C[i] = (uint32_t)h->C[i];
+    v.kt = h->d_kt;
+    v.kbits = h->d_kbits;
+    v.kdepth = h->kt_depth;
     return v;
 }
 
 IndexView view_rev(const fm_index *h) {
     IndexView v = view_fwd(h);
     v.blocks = h->d_rev;
+    v.kt = nullptr;
+    v.kbits = nullptr;
+    v.kdepth = 0;
     v.dollar = (uint32_t)h->rev_dollar;
     return v;
 }
@@ -103,7 +109,27 @@ __global__ void __launch_bounds__(128) k_exact(IndexView ix, const uint8_t *__re
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
         const uint32_t s = offs[r], e = offs[r + 1];
         uint32_t k = 0, l = ix.n;
-        for (uint32_t i = e; i > s; --i) {
+        // the last j0 symbols at once from the interval tables (their state is Listing 1's
+        // after those j0 steps, insertion points included)
+        const uint32_t j0 = e - s < ix.kdepth ? e - s : ix.kdepth;
+        uint32_t code = 0, bad = 0;
+        for (uint32_t t = 0; t < j0; ++t) {
+            const uint32_t b = reads[e - j0 + t];
+            bad |= b;
+            code |= (b & 3u) << (2u * t);
+        }
+        if (bad > 3u) {
+            atomicOr(err, kErrDomain);
+            kout[r] = 0;
+            lout[r] = ix.n;
+            continue;
+        }
+        if (j0) {
+            const uint2 kl = kt_get(ix, j0, code);
+            k = kl.x;
+            l = kl.y;
+        }
+        for (uint32_t i = e - j0; i > s; --i) {
             const uint32_t b = reads[i - 1];
             if (b > 3u) {
                 atomicOr(err, kErrDomain);
@@ -250,6 +276,47 @@ __global__ void __launch_bounds__(256) k_locate(IndexView ix, const uint32_t *__
     }
 }
 
+// -------------------------------------------------------------------------------------------
+// Interval tables of short strings.  Level j+1 from level j: one eight-Occ step per string X of
+// length j gives the four extensions bX (codes 4 code(X) + b), by Listing 1's formula whether or
+// not X occurs, so every entry is Listing 1's state after reading its string.
+// -------------------------------------------------------------------------------------------
+template <int I>
+__global__ void __launch_bounds__(256) k_kmer_level(IndexView ix, uint2 *__restrict__ kt, uint32_t j) {
+    const uint32_t cnt = 1u << (2u * j);
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < cnt; c += gridDim.x * blockDim.x) {
+        const uint2 kl = kt[cnt + c];
+        const uint32_t pk = kl.x, pl = kl.y + 1u;
+        const uint32_t jk = pk / I, jl = pl / I;
+        Blk<I> Bk, Bl;
+        load_block<I>(ix.blocks, jk, pk - jk * I, Bk);
+        load_block<I>(ix.blocks, jl, pl - jl * I, Bl);
+        uint32_t rk[4], rl[4];
+        rank4_in<I>(Bk, jk, pk, ix.dollar, rk);
+        rank4_in<I>(Bl, jl, pl, ix.dollar, rl);
+        uint2 *out = kt + 4u * cnt + 4u * c;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) out[b] = make_uint2(ix.C[b] + rk[b] + 1u, ix.C[b] + rl[b]);
+    }
+}
+
+// occurrence bits: bit t (t in [4^j, 2 4^j), j <= L) = entry t is non-empty; other bits 0
+__global__ void __launch_bounds__(256) k_kmer_bits(const uint2 *__restrict__ kt, uint32_t *__restrict__ bits,
+                                                   uint32_t nwords, uint32_t L) {
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += gridDim.x * blockDim.x) {
+        uint32_t word = 0;
+        for (uint32_t u = 0; u < 32u; ++u) {
+            const uint32_t t = 32u * w + u;
+            if (t == 0u) continue;
+            const uint32_t j = (31u - (uint32_t)__clz(t)) >> 1;
+            if (j > L || t >= (2u << (2u * j))) continue;
+            const uint2 kl = kt[t];
+            if (kl.x <= kl.y) word |= 1u << u;
+        }
+        bits[w] = word;
+    }
+}
+
 int grid_occ(fm_index *h, uint64_t work, int block) {
     uint64_t g = (work + block - 1) / block;
     uint64_t cap = (uint64_t)h->sms * (2048 / block) * 4;
@@ -304,9 +371,61 @@ int launch_locate(fm_index *h, const uint32_t *rows, uint64_t N, uint32_t *pos,
     return FM_OK;
 }
 
+uint32_t kmer_depth_for(const fm_index *h) {
+    const uint32_t set = h->tune.kmer;
+    if (set == FM_KMER_OFF) return 0;
+    if (set != FM_KMER_AUTO) return set < kMaxKmerDepth ? set : kMaxKmerDepth;
+    uint32_t lg = 0;   // floor(log4(n + 1))
+    while (lg < 31 && (1ull << (2 * (lg + 1))) <= h->n + 1) ++lg;
+    const uint32_t d = lg > 2 ? lg - 2 : 0;
+    return d < kMaxKmerDepth ? d : kMaxKmerDepth;
+}
+
+int ensure_kmer(fm_index *h, cudaStream_t st) {
+    const uint32_t L = kmer_depth_for(h);
+    if (L == h->kt_depth) return FM_OK;
+    FM_CUDA_TRY(h, cudaStreamSynchronize(st));   // no kernel of this stream reads the old tables
+    cudaFree(h->d_kt);
+    cudaFree(h->d_kbits);
+    h->d_kt = nullptr;
+    h->d_kbits = nullptr;
+    h->kt_depth = 0;
+    if (L == 0) return FM_OK;
+    const uint64_t entries = 2ull << (2 * L);
+    const uint64_t nwords = (entries + 31) / 32;
+    if (cudaMalloc(&h->d_kt, entries * sizeof(uint2)) != cudaSuccess ||
+        cudaMalloc(&h->d_kbits, nwords * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->d_kt);
+        h->d_kt = nullptr;
+        h->d_kbits = nullptr;
+        return set_error(h, FM_ENOMEM, "interval tables: out of device memory");
+    }
+    const uint2 root = make_uint2(0u, (uint32_t)h->n);   // the empty string: [0, n]
+    FM_CUDA_TRY(h, cudaMemcpyAsync(h->d_kt + 1, &root, sizeof(root), cudaMemcpyHostToDevice, st));
+    IndexView ix = view_fwd(h);
+    for (uint32_t j = 0; j < L; ++j) {
+        const int block = 256;
+        const int grid = grid_occ(h, 1ull << (2 * j), block);
+        switch (h->interval) {
+            case 32: k_kmer_level<32><<<grid, block, 0, st>>>(ix, h->d_kt, j); break;
+            case 64: k_kmer_level<64><<<grid, block, 0, st>>>(ix, h->d_kt, j); break;
+            case 128: k_kmer_level<128><<<grid, block, 0, st>>>(ix, h->d_kt, j); break;
+            default: k_kmer_level<256><<<grid, block, 0, st>>>(ix, h->d_kt, j); break;
+        }
+        FM_CUDA_TRY(h, cudaGetLastError());
+    }
+    k_kmer_bits<<<grid_occ(h, nwords, 256), 256, 0, st>>>(h->d_kt, h->d_kbits, (uint32_t)nwords, L);
+    FM_CUDA_TRY(h, cudaGetLastError());
+    FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+    h->kt_depth = L;
+    return FM_OK;
+}
+
 int launch_exact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
                  uint32_t *k_out, uint32_t *l_out, cudaStream_t st) {
     if (n_reads == 0) return FM_OK;
+    if (int rc = ensure_kmer(h, st)) return rc;
     IndexView ix = view_fwd(h);
     uint32_t *err = h->d_err + kErrExact;
     const int block = 128;

@@ -52,6 +52,7 @@ def test_graph_replay_matches_oracle(fm, case):
     nq = 2 * len(reads)
     counts, offsets, pairs = _bufs(nq, 4 * nq + 1024)
     stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+    fm.fm_set_tuning(h, kmer_depth=fm.KMER_OFF)   # block totals as the oracle counts them
     kinds = []
     for _ in range(4):
         prof = fm.fm_profile()
@@ -64,6 +65,14 @@ def test_graph_replay_matches_oracle(fm, case):
     st = stats.cpu().numpy()
     assert st[0] == 4 * want["nodes"].sum()
     assert st[1] == 4 * want["blocks"].sum()
+    # interval tables on: a new graph, results and nodes unchanged
+    fm.fm_set_tuning(h, kmer_depth=fm.KMER_AUTO)
+    stats.zero_()
+    for _ in range(2):
+        c, o, p = fm.fm_inexact(h, codes, offs, 2, 1, strands=2, stats=stats, counts=counts,
+                                offsets=offsets, pairs=pairs)
+        _check(want, c, o, p)
+    assert stats.cpu().numpy()[0] == 2 * want["nodes"].sum()
     # new output buffers: a new graph is captured, results unchanged
     counts2, offsets2, pairs2 = _bufs(nq, 4 * nq + 1024)
     prof = fm.fm_profile()
@@ -102,7 +111,8 @@ def test_rejected_tuning_changes_nothing(fm):
     h = fm.fm_build(synth.uniform_text(5, 5000))
     before = fm.fm_get_tuning(h)
     for bad in ({"warps_per_block": 4, "graphs": 3}, {"chunk": 8, "occ_per_thread": 3},
-                {"blocks_per_sm": 2, "l2_fetch_bytes": 48}, {"warps_per_block": 9}):
+                {"blocks_per_sm": 2, "l2_fetch_bytes": 48}, {"warps_per_block": 9},
+                {"chunk": 4, "kmer_depth": 15}, {"canonical": 2, "kmer_depth": 0x80}):
         with pytest.raises(fm.FmError) as ei:
             fm.fm_set_tuning(h, **bad)
         assert ei.value.code == fm.FM_EINVAL

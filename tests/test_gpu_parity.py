@@ -153,6 +153,31 @@ def test_exact_matches_oracle(fm, interval):
     h.close()
 
 
+@pytest.mark.parametrize("depth", [1, 2, 6, 9, 11])
+def test_exact_interval_tables(fm, depth):
+    """Listing 1 started from the interval tables: every string of length <= 6 (so every table
+    entry of levels <= 6, occurring or not: the empty ones hold the insertion point), and
+    ragged reads shorter and longer than the table depth, equal the oracle's search."""
+    R = synth.repeat_text(41, 200_000, families=20, min_len=300, max_len=3000)
+    h = fm.fm_build(R)
+    fm.fm_set_tuning(h, kmer_depth=depth)
+    assert fm.fm_get_tuning(h)["kmer_depth"] == depth
+    ix = oracle.Index(R, "sais")
+    words = [np.array([(c >> (2 * t)) & 3 for t in range(j)], np.uint8)
+             for j in range(0, 7) for c in range(4 ** j)]
+    codes = np.concatenate(words).astype(np.uint8)
+    offs = np.concatenate([[0], np.cumsum([w.size for w in words])]).astype(np.uint32)
+    every = synth.Reads(codes, offs)
+    ragged = synth.sample_reads(43, R, 2000, 0, 40, sub_rate=0.05, random_frac=0.3)
+    for rd in (every, ragged):
+        c, o = fm.to_device_reads(rd)
+        k, l = fm.fm_exact(h, c, o)
+        kw, lw = ix.exact(rd.codes, rd.offs)
+        assert np.array_equal(_u32(k), kw)
+        assert np.array_equal(_u32(l), lw)
+    h.close()
+
+
 def test_exact_bad_code(fm):
     h = fm.fm_build(_text("uniform", 1000))
     codes = torch.tensor([0, 1, 7, 2], dtype=torch.uint8, device="cuda")
@@ -181,10 +206,11 @@ def test_dcalc_matches_oracle(fm, interval):
 
 
 def _inexact_case(fm, R, reads, z, gaps, interval, kernels=("plain", "persistent"),
-                  modes=("canonical", "listing")):
-    """Both kernels, with the canonical enumeration (default) and with every call of Listing 2:
-    result sets equal the oracle's Listing 2 sets, and node and block counts equal the
-    oracle's for the same enumeration."""
+                  modes=("canonical", "listing"), kmers=(0xFE, 0xFF)):   # tables auto, off
+    """Both kernels, with the canonical enumeration (default) and with every call of Listing 2,
+    with and without interval tables: result sets equal the oracle's Listing 2 sets, node
+    counts equal the oracle's for the same enumeration, and so do block counts without tables
+    (with tables, nodes shorter than the table depth read no checkpoint block)."""
     h = fm.fm_build(R, interval=interval)
     ix = oracle.Index(R, "sais")
     want_c = ix.inexact(reads.codes, reads.offs, z, gaps, strands=2, interval=interval,
@@ -195,19 +221,26 @@ def _inexact_case(fm, R, reads, z, gaps, interval, kernels=("plain", "persistent
         if "listing" in modes else want_c
     codes, offs = fm.to_device_reads(reads)
     for mode in modes:
-        fm.fm_set_tuning(h, canonical=1 if mode == "canonical" else 2)
-        ref = want_c if mode == "canonical" else want
-        for kern in kernels:
-            stats = torch.zeros(4, dtype=torch.int64, device="cuda")
-            counts, offsets, pairs = fm.fm_inexact(h, codes, offs, z, gaps, strands=2,
-                                                   kernel=kern, stats=stats)
-            assert np.array_equal(_u32(counts), want["counts"]), (kern, mode)
-            assert np.array_equal(offsets.cpu().numpy().astype(np.uint64), want["offsets"]), \
-                (kern, mode)
-            assert np.array_equal(_u32(pairs), want["pairs"]), (kern, mode)
-            st = stats.cpu().numpy()
-            assert st[0] == ref["nodes"].sum(), (kern, mode)
-            assert st[1] == ref["blocks"].sum(), (kern, mode)
+        for kmer in kmers:
+            fm.fm_set_tuning(h, canonical=1 if mode == "canonical" else 2, kmer_depth=kmer)
+            ref = want_c if mode == "canonical" else want
+            for kern in kernels:
+                stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+                counts, offsets, pairs = fm.fm_inexact(h, codes, offs, z, gaps, strands=2,
+                                                       kernel=kern, stats=stats)
+                tag = (kern, mode, kmer)
+                assert np.array_equal(_u32(counts), want["counts"]), tag
+                assert np.array_equal(offsets.cpu().numpy().astype(np.uint64),
+                                      want["offsets"]), tag
+                assert np.array_equal(_u32(pairs), want["pairs"]), tag
+                st = stats.cpu().numpy()
+                assert st[0] == ref["nodes"].sum(), tag
+                if fm.fm_get_tuning(h)["kmer_depth"] == fm.KMER_OFF:
+                    assert st[1] == ref["blocks"].sum(), tag
+                    assert st[3] == 0, tag
+                else:
+                    assert st[1] <= ref["blocks"].sum(), tag
+                    assert st[3] <= st[0], tag   # at most one table sector per node
     h.close()
 
 
@@ -218,6 +251,16 @@ def test_inexact_matches_oracle(fm, z, gaps):
     reads = synth.sample_reads(31 + z, R, n_reads, 20, 150, sub_rate=0.01, indel_rate=0.003,
                                both_strands=True, random_frac=0.05)
     _inexact_case(fm, R, reads, z, gaps, 64)
+
+
+@pytest.mark.parametrize("depth", [1, 3, 7, 10, 13, 14])
+def test_inexact_interval_table_depths(fm, depth):
+    """Tables of every depth, up to deeper than the strings of the search's first steps on this
+    text: same intervals and nodes as the oracle, and no more checkpoint blocks."""
+    R = synth.repeat_text(47, 300_000, families=30, min_len=300, max_len=3000)
+    reads = synth.sample_reads(48, R, 300, 1, 150, sub_rate=0.02, indel_rate=0.005,
+                               both_strands=True, random_frac=0.05)
+    _inexact_case(fm, R, reads, 2, 1, 64, modes=("canonical",), kmers=(depth,))
 
 
 @pytest.mark.parametrize("interval", [32, 128, 256])
