@@ -218,7 +218,9 @@ __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, cons
 // One call of InexRecur with no difference left (z = 0): only the match b = W[i] can continue,
 // so the eight-Occ step reduces to rank(W[i], k) and rank(W[i], l+1), i.e. one step of
 // Listing 1.  The single child replaces the node (out), or the interval is a result (leaf at
-// i = 0), or the branch ends (empty interval, or D(i-1) > 0).
+// i = 0), or the branch ends (empty interval).  The child needs no D test: every node is
+// created with z >= D(i), D never decreases with i, so here D(i-1) <= D(i) = 0.  Only mt.z
+// and mt.w (read start, length and strand) are used.
 template <int I>
 __device__ __forceinline__ void exact_step(const SearchCfg &c, const uint4 &nd, const uint4 &mt,
                                            uint4 &out, bool &survive, bool &is_leaf,
@@ -262,7 +264,7 @@ __device__ __forceinline__ void exact_step(const SearchCfg &c, const uint4 &nd, 
         alive = k2 <= l2;
     }
     is_leaf = alive && i == 0u;
-    survive = alive && i > 0u && d_at(mt, (int)i - 1) == 0u;
+    survive = alive && i > 0u;
     out = make_uint4(nd.x, (i - 1u) | ybits, k2, l2);
 }
 
@@ -410,49 +412,80 @@ __global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk
             }
         }
         if (etop >= 32 || (etop > 0 && gtop == 0 && stop == 0)) {
-            // exact steps: up to 64 E nodes, two per lane, their gathers in flight together
-            const int take = etop < 64 ? etop : 64;
-            const bool a0 = lane < take, a1 = lane + 32 < take;
+            // Exact steps: each lane runs up to two chains (slots 0 and 1) with their read
+            // start and length in registers, their gathers in flight together.  A chain stays
+            // in its slot from step to step; a slot whose chain ended (empty interval, or a
+            // result at i = 0) is refilled from E.  The phase ends when fewer than 32 chains
+            // run and E is empty (unless nothing else is left to do), and the survivors go
+            // back to E (fewer than 32, so E stays below 32 for the next G step).
             uint4 n0 = make_uint4(0, 0, 0, 0), n1 = make_uint4(0, 0, 0, 0);
-            if (a0) n0 = st[stk - etop + lane];
-            if (a1) n1 = st[stk - etop + 32 + lane];
-            etop -= take;
-            __syncwarp();
-            uint4 c0 = make_uint4(0, 0, 0, 0), c1 = make_uint4(0, 0, 0, 0);
-            bool s0 = false, s1 = false, f0 = false, f1 = false;
-            {
-                uint4 m0 = make_uint4(0, 0, 0, 0), m1 = make_uint4(0, 0, 0, 0);
-                if (a0) m0 = c.qmeta[n0.x];
-                if (a1) m1 = c.qmeta[n1.x];
+            uint2 r0 = make_uint2(0, 0), r1 = make_uint2(0, 0);   // qmeta .z, .w
+            bool a0 = false, a1 = false;
+            for (;;) {
+                // refill free slots from E (slot 0 first)
+                {
+                    const uint32_t f0 = __ballot_sync(FULL, !a0), f1 = __ballot_sync(FULL, !a1);
+                    const int nf0 = __popc(f0);
+                    const int t0 = nf0 < etop ? nf0 : etop;
+                    const int p0 = __popc(f0 & lt_mask);
+                    if (!a0 && p0 < t0) {
+                        n0 = st[stk - etop + p0];
+                        const uint4 m = c.qmeta[n0.x];
+                        r0 = make_uint2(m.z, m.w);
+                        a0 = true;
+                    }
+                    const int rest = etop - t0;
+                    const int t1 = __popc(f1) < rest ? __popc(f1) : rest;
+                    const int p1 = __popc(f1 & lt_mask);
+                    if (!a1 && p1 < t1) {
+                        n1 = st[stk - etop + t0 + p1];
+                        const uint4 m = c.qmeta[n1.x];
+                        r1 = make_uint2(m.z, m.w);
+                        a1 = true;
+                    }
+                    etop -= t0 + t1;
+                    __syncwarp();
+                }
+                uint4 c0 = make_uint4(0, 0, 0, 0), c1 = make_uint4(0, 0, 0, 0);
+                bool s0 = false, s1 = false, e0 = false, e1 = false;
                 uint32_t b0 = 0, b1 = 0;
                 if (a0) {
-                    exact_step<I>(c, n0, m0, c0, s0, f0, b0);
+                    exact_step<I>(c, n0, make_uint4(0, 0, r0.x, r0.y), c0, s0, e0, b0);
                     my_nodes += 1;
                     my_blocks += step_cost(b0);
                 }
                 if (a1) {
-                    exact_step<I>(c, n1, m1, c1, s1, f1, b1);
+                    exact_step<I>(c, n1, make_uint4(0, 0, r1.x, r1.y), c1, s1, e1, b1);
                     my_nodes += 1;
                     my_blocks += step_cost(b1);
                 }
+                const uint32_t lb0 = __ballot_sync(FULL, e0), lb1 = __ballot_sync(FULL, e1);
+                if (lb0 | lb1) {
+                    unsigned long long base = 0;
+                    if (lane == 0)
+                        base = atomicAdd(c.raw_count, (unsigned long long)(__popc(lb0) + __popc(lb1)));
+                    base = __shfl_sync(FULL, base, 0);
+                    const uint64_t q0 = base + __popc(lb0 & lt_mask);
+                    const uint64_t q1 = base + __popc(lb0) + __popc(lb1 & lt_mask);
+                    if (e0 && q0 < c.raw_cap) c.raw[q0] = make_uint4(n0.x, c0.z, c0.w, 0u);
+                    if (e1 && q1 < c.raw_cap) c.raw[q1] = make_uint4(n1.x, c1.z, c1.w, 0u);
+                }
+                if (s0) n0 = c0;
+                if (s1) n1 = c1;
+                a0 = s0;
+                a1 = s1;
+                const int live = __popc(__ballot_sync(FULL, a0)) + __popc(__ballot_sync(FULL, a1));
+                if (live == 0 && etop == 0) break;
+                if (live < 32 && etop == 0 && !(gtop == 0 && stop == 0 && qdone)) {
+                    // survivors back to E
+                    const uint32_t v0 = __ballot_sync(FULL, a0), v1 = __ballot_sync(FULL, a1);
+                    if (a0) st[stk - 1 - (etop + __popc(v0 & lt_mask))] = n0;
+                    if (a1) st[stk - 1 - (etop + __popc(v0) + __popc(v1 & lt_mask))] = n1;
+                    etop += __popc(v0) + __popc(v1);
+                    __syncwarp();
+                    break;
+                }
             }
-            const uint32_t bal0 = __ballot_sync(FULL, s0);
-            const uint32_t bal1 = __ballot_sync(FULL, s1);
-            if (s0) st[stk - 1 - (etop + __popc(bal0 & lt_mask))] = c0;
-            if (s1) st[stk - 1 - (etop + __popc(bal0) + __popc(bal1 & lt_mask))] = c1;
-            etop += __popc(bal0) + __popc(bal1);
-            const uint32_t lb0 = __ballot_sync(FULL, f0), lb1 = __ballot_sync(FULL, f1);
-            if (lb0 | lb1) {
-                unsigned long long base = 0;
-                if (lane == 0)
-                    base = atomicAdd(c.raw_count, (unsigned long long)(__popc(lb0) + __popc(lb1)));
-                base = __shfl_sync(FULL, base, 0);
-                const uint64_t p0 = base + __popc(lb0 & lt_mask);
-                const uint64_t p1 = base + __popc(lb0) + __popc(lb1 & lt_mask);
-                if (f0 && p0 < c.raw_cap) c.raw[p0] = make_uint4(n0.x, c0.z, c0.w, 0u);
-                if (f1 && p1 < c.raw_cap) c.raw[p1] = make_uint4(n1.x, c1.z, c1.w, 0u);
-            }
-            __syncwarp();
             continue;
         }
         if (gtop == 0 && stop > 0) {
