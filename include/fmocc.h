@@ -167,6 +167,15 @@ typedef struct fm_search_params {
                               deduplication, [3] interval-table sectors read (32 bytes each;
                               see fm_tuning.kmer_depth) */
     fm_profile *profile; /* optional host pointer, filled by a successful call */
+    uint8_t *costs;    /* optional device uint8[pair_capacity]: for each reported interval, the
+                          fewest differences (mismatch and single-symbol indel columns) among
+                          the alignments of Listing 2 that reach it; written beside pairs */
+    uint32_t best;     /* 1: report, per query, only the intervals of its minimum cost (the
+                          best hits); counts and offsets then describe those.  0: all */
+    uint32_t reserved; /* must be 0 */
+    /* With costs or best set, FM_ETRUNC leaves counts and offsets complete and the call must
+     * be repeated with a larger pairs (and costs) buffer: fm_inexact_fetch does not apply.
+     * fm_inexact_noalloc and the serving calls accept neither (FM_EINVAL). */
 } fm_search_params;
 
 #define FM_KERNEL_AUTO 0u       /* the persistent kernel */

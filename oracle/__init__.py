@@ -38,6 +38,7 @@ def build(force: bool = False, extra_flags=(), out: str | None = None) -> str:
 class _Results(C.Structure):
     _fields_ = [("nq", C.c_int64), ("counts", C.POINTER(C.c_uint32)),
                 ("offsets", C.POINTER(C.c_uint64)), ("pairs", C.POINTER(C.c_uint32)),
+                ("costs", C.POINTER(C.c_uint8)),
                 ("nodes", C.POINTER(C.c_uint64)), ("blocks", C.POINTER(C.c_uint64)),
                 ("total", C.c_uint64)]
 
@@ -257,7 +258,8 @@ class Index:
     def inexact(self, codes, offs, z: int, max_gaps: int = 0, strands: int = 1,
                 prune: bool = True, interval: int = 64, threads: int = 0,
                 canonical: bool = False):
-        """Listing 2 result sets: dict with counts, offsets, pairs (total x 2), nodes, blocks.
+        """Listing 2 result sets: dict with counts, offsets, pairs (total x 2), costs (per
+        interval the fewest differences of the alignments reaching it), nodes, blocks.
         canonical: enumerate canonical alignments only (same results; nodes and blocks are
         those of that enumeration)."""
         codes = _u8(codes)
@@ -277,6 +279,7 @@ class Index:
                 "offsets": np.ctypeslib.as_array(r.offsets, shape=(nq + 1,)).copy(),
                 "pairs": np.ctypeslib.as_array(r.pairs, shape=(max(2 * tot, 2),))[:2 * tot]
                 .reshape(tot, 2).copy(),
+                "costs": np.ctypeslib.as_array(r.costs, shape=(max(tot, 1),))[:tot].copy(),
                 "nodes": np.ctypeslib.as_array(r.nodes, shape=(max(nq, 1),))[:nq].copy(),
                 "blocks": np.ctypeslib.as_array(r.blocks, shape=(max(nq, 1),))[:nq].copy(),
             }

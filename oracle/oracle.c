@@ -551,17 +551,18 @@ void or_dcalc(const or_index *ix, const uint8_t *W, int64_t m, uint8_t *D) {
  * Listing 2 (InexRecur) with D pruning, set semantics
  * ---------------------------------------------------------------------------------------- */
 typedef struct {
-    uint32_t *pairs; /* k, l */
+    uint32_t *pairs; /* k, l, cost (differences the alignment used) */
     int64_t size, cap;
 } pairvec;
 
-static void pv_push(pairvec *v, uint32_t k, uint32_t l) {
+static void pv_push(pairvec *v, uint32_t k, uint32_t l, uint32_t cost) {
     if (v->size == v->cap) {
         v->cap = v->cap ? 2 * v->cap : 64;
-        v->pairs = (uint32_t *)realloc(v->pairs, sizeof(uint32_t) * 2 * (size_t)v->cap);
+        v->pairs = (uint32_t *)realloc(v->pairs, sizeof(uint32_t) * 3 * (size_t)v->cap);
     }
-    v->pairs[2 * v->size] = k;
-    v->pairs[2 * v->size + 1] = l;
+    v->pairs[3 * v->size] = k;
+    v->pairs[3 * v->size + 1] = l;
+    v->pairs[3 * v->size + 2] = cost;
     v->size++;
 }
 
@@ -572,13 +573,14 @@ typedef struct {
     int max_gaps, prune, interval;
     pairvec *out;
     uint64_t nodes, blocks;
+    int z0; /* the differences allowed at the top call; a result's cost is z0 - z */
 } inex_ctx;
 
 static void inex_recur(inex_ctx *X, int64_t i, int z, int gaps, int64_t k, int64_t l) {
     if (z < 0) return;
     if (X->prune && i >= 0 && z < X->D[i]) return;
     if (i < 0) {
-        if (k >= 1) pv_push(X->out, (uint32_t)k, (uint32_t)l);
+        if (k >= 1) pv_push(X->out, (uint32_t)k, (uint32_t)l, (uint32_t)(X->z0 - z));
         return;
     }
     X->nodes++;
@@ -618,7 +620,7 @@ static void inex_canon(inex_ctx *X, int64_t i, int z, int gaps, int64_t k, int64
                        int lb) {
     if (z < 0 || (X->prune && i >= 0 && z < X->D[i])) return;
     if (i < 0) { /* a result, unless no reference symbol was used */
-        if (k > 0) pv_push(X->out, (uint32_t)k, (uint32_t)l);
+        if (k > 0) pv_push(X->out, (uint32_t)k, (uint32_t)l, (uint32_t)(X->z0 - z));
         return;
     }
     const uint8_t *W = X->W;
@@ -658,11 +660,16 @@ static void inex_canon(inex_ctx *X, int64_t i, int z, int gaps, int64_t k, int64
     }
 }
 
-static int cmp_pair(const void *a, const void *b) {
+/* order of (k, l, cost) triples; same_interval compares (k, l) only */
+static int cmp_triple(const void *a, const void *b) {
     const uint32_t *x = (const uint32_t *)a, *y = (const uint32_t *)b;
-    if (x[0] != y[0]) return x[0] < y[0] ? -1 : 1;
-    if (x[1] != y[1]) return x[1] < y[1] ? -1 : 1;
+    for (int t = 0; t < 3; ++t)
+        if (x[t] != y[t]) return x[t] < y[t] ? -1 : 1;
     return 0;
+}
+
+static int same_interval(const uint32_t *x, const uint32_t *y) {
+    return x[0] == y[0] && x[1] == y[1];
 }
 
 typedef struct {
@@ -687,18 +694,21 @@ static void inex_one(void *a, int64_t q, int tid) {
         W[i] = strand ? (uint8_t)(3 - J->codes[s + m - 1 - i]) : J->codes[s + i];
     or_dcalc(J->ix, W, m, D);
     pairvec v = {NULL, 0, 0};
-    inex_ctx X = {J->ix, W, D, J->max_gaps, J->prune & 1, J->interval, &v, 0, 0};
+    inex_ctx X = {J->ix, W, D, J->max_gaps, J->prune & 1, J->interval, &v, 0, 0, J->z};
     if (J->prune & 2)
         inex_canon(&X, m - 1, J->z, 0, 0, J->ix->n, 0, 0);
     else
         inex_recur(&X, m - 1, J->z, 0, 0, J->ix->n);
     if (v.size > 1) { /* sort and keep distinct intervals */
-        qsort(v.pairs, (size_t)v.size, 2 * sizeof(uint32_t), cmp_pair);
+        /* each interval once, with the fewest differences any of its alignments used (the
+         * first of its run after sorting by cost too) */
+        qsort(v.pairs, (size_t)v.size, 3 * sizeof(uint32_t), cmp_triple);
         int64_t w = 1;
         for (int64_t i = 1; i < v.size; ++i)
-            if (cmp_pair(&v.pairs[2 * i], &v.pairs[2 * (w - 1)]) != 0) {
-                v.pairs[2 * w] = v.pairs[2 * i];
-                v.pairs[2 * w + 1] = v.pairs[2 * i + 1];
+            if (!same_interval(&v.pairs[3 * i], &v.pairs[3 * (w - 1)])) {
+                v.pairs[3 * w] = v.pairs[3 * i];
+                v.pairs[3 * w + 1] = v.pairs[3 * i + 1];
+                v.pairs[3 * w + 2] = v.pairs[3 * i + 2];
                 ++w;
             }
         v.size = w;
@@ -735,10 +745,14 @@ or_results *or_inexact_batch(const or_index *ix, const uint8_t *codes, const uin
     res->offsets[nq] = total;
     res->total = total;
     res->pairs = (uint32_t *)malloc(sizeof(uint32_t) * 2 * (size_t)(total > 0 ? total : 1));
+    res->costs = (uint8_t *)malloc((size_t)(total > 0 ? total : 1));
     for (int64_t q = 0; q < nq; ++q) {
-        if (pq[q].size)
-            memcpy(res->pairs + 2 * res->offsets[q], pq[q].pairs,
-                   sizeof(uint32_t) * 2 * (size_t)pq[q].size);
+        for (int64_t t = 0; t < pq[q].size; ++t) {
+            const uint64_t o = res->offsets[q] + (uint64_t)t;
+            res->pairs[2 * o] = pq[q].pairs[3 * t];
+            res->pairs[2 * o + 1] = pq[q].pairs[3 * t + 1];
+            res->costs[o] = (uint8_t)pq[q].pairs[3 * t + 2];
+        }
         free(pq[q].pairs);
     }
     free(pq);
@@ -750,6 +764,7 @@ void or_results_free(or_results *res) {
     free(res->counts);
     free(res->offsets);
     free(res->pairs);
+    free(res->costs);
     free(res->nodes);
     free(res->blocks);
     free(res);

@@ -114,6 +114,8 @@ typedef struct or_results {
     uint32_t *counts;   /* [nq] intervals per query */
     uint64_t *offsets;  /* [nq+1] exclusive prefix sum of counts */
     uint32_t *pairs;    /* [2*total] k, l */
+    uint8_t *costs;     /* [total] per interval, the fewest differences (mismatch and indel
+                           columns) among the alignments that reached it */
     uint64_t *nodes;    /* [nq] */
     uint64_t *blocks;   /* [nq] */
     uint64_t total;

@@ -331,10 +331,10 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
     return v;
 }
 
-// append this warp's leaves to the raw buffer
+// append this warp's leaves to the raw buffer: (query, k, l, differences used)
 __device__ __forceinline__ void emit_leaves(const SearchCfg &c, int lane, bool act,
                                             const uint4 &nd, uint32_t leaf, const uint32_t k2[4],
-                                            const uint32_t l2[4]) {
+                                            const uint32_t l2[4], uint32_t wi) {
     if (!__any_sync(FULL, act && leaf != 0u)) return;
     const int lc = act ? __popc(leaf) : 0;
     const int incl = warp_incl_scan(lc, lane);
@@ -350,7 +350,9 @@ __device__ __forceinline__ void emit_leaves(const SearchCfg &c, int lane, bool a
         mset &= mset - 1;
         if (pos < c.raw_cap) {
             const uint2 kl = leaf_of(c, nd, t, k2, l2);
-            c.raw[pos] = make_uint4(nd.x, kl.x, kl.y, 0u);
+            // z left after the leaf column: the match keeps z, insertion and mismatch spend one
+            const uint32_t zl = ((nd.y >> 8) & 15u) - ((t >= 5 && (uint32_t)(t - 5) == wi) ? 0u : 1u);
+            c.raw[pos] = make_uint4(nd.x, kl.x, kl.y, c.z - zl);
         }
         ++pos;
     }
@@ -467,8 +469,8 @@ __global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk
                     base = __shfl_sync(FULL, base, 0);
                     const uint64_t q0 = base + __popc(lb0 & lt_mask);
                     const uint64_t q1 = base + __popc(lb0) + __popc(lb1 & lt_mask);
-                    if (e0 && q0 < c.raw_cap) c.raw[q0] = make_uint4(n0.x, c0.z, c0.w, 0u);
-                    if (e1 && q1 < c.raw_cap) c.raw[q1] = make_uint4(n1.x, c1.z, c1.w, 0u);
+                    if (e0 && q0 < c.raw_cap) c.raw[q0] = make_uint4(n0.x, c0.z, c0.w, c.z);
+                    if (e1 && q1 < c.raw_cap) c.raw[q1] = make_uint4(n1.x, c1.z, c1.w, c.z);
                 }
                 if (s0) n0 = c0;
                 if (s1) n1 = c1;
@@ -552,7 +554,7 @@ __global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk
         }
         gtop += gtot;
         etop += etot;
-        emit_leaves(c, lane, act, nd, leaf, k2, l2);
+        emit_leaves(c, lane, act, nd, leaf, k2, l2, wi);
         __syncwarp();
     }
     if (c.stats) {
@@ -641,14 +643,14 @@ __global__ void __launch_bounds__(256) k_inexact_plain(SearchCfg c, uint4 *stack
             my_blocks += step_cost(nb);
             if (sp == 0 && !cur) have = false;
         }
-        emit_leaves(c, lane, act, nd, leaf, k2, l2);
+        emit_leaves(c, lane, act, nd, leaf, k2, l2, wi);
         const uint32_t lb = __ballot_sync(FULL, ex_leaf);
         if (lb) {
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(c.raw_count, (unsigned long long)__popc(lb));
             base = __shfl_sync(FULL, base, 0);
             const uint64_t pos = base + __popc(lb & ((1u << lane) - 1u));
-            if (ex_leaf && pos < c.raw_cap) c.raw[pos] = make_uint4(nd.x, ex_out.z, ex_out.w, 0u);
+            if (ex_leaf && pos < c.raw_cap) c.raw[pos] = make_uint4(nd.x, ex_out.z, ex_out.w, c.z);
         }
     }
     if (c.stats) {
@@ -819,6 +821,90 @@ __global__ void k_compact(uint32_t nq, const uint32_t *__restrict__ ucnt,
             const uint64_t x = seg[t];
             dst[2 * t] = (uint32_t)(x >> 32);
             dst[2 * t + 1] = (uint32_t)x;
+        }
+    }
+}
+
+// Fewest differences per reported interval: each raw result finds its interval in its query's
+// sorted distinct list (binary search) and lowers that interval's cost (cost32 starts at ~0).
+__global__ void k_mincost(const uint4 *__restrict__ raw, const unsigned long long *__restrict__ d_R,
+                          uint64_t cap, const uint64_t *__restrict__ start,
+                          const uint32_t *__restrict__ ucnt, const uint64_t *__restrict__ grouped,
+                          const uint64_t *__restrict__ uoff, uint32_t *__restrict__ cost32) {
+    const uint64_t R = *d_R < cap ? *d_R : cap;
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < R;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 v = raw[e];
+        const uint64_t key = ((uint64_t)v.y << 32) | v.z;
+        const uint64_t *seg = grouped + start[v.x];
+        uint32_t lo = 0, hi = ucnt[v.x];
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (seg[mid] < key) lo = mid + 1; else hi = mid;
+        }
+        if (lo < ucnt[v.x] && seg[lo] == key) atomicMin(cost32 + uoff[v.x] + lo, v.w);
+    }
+}
+
+// costs of all distinct intervals, in output order (nothing unless they fit the capacity)
+__global__ void k_cost_out(const uint64_t *__restrict__ total, const uint32_t *__restrict__ cost32,
+                           uint8_t *__restrict__ costs, uint64_t capacity) {
+    const uint64_t n = *total;
+    if (n > capacity) return;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n;
+         t += (uint64_t)gridDim.x * blockDim.x)
+        costs[t] = (uint8_t)cost32[t];
+}
+
+// best hits, warp per query: the query's minimum cost and how many of its intervals have it
+__global__ void k_best_count(uint32_t nq, const uint32_t *__restrict__ ucnt,
+                             const uint64_t *__restrict__ uoff, const uint32_t *__restrict__ cost32,
+                             uint32_t *__restrict__ bcnt, uint32_t *__restrict__ qmin) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += warps) {
+        const uint32_t u = ucnt[q];
+        const uint32_t *cs = cost32 + uoff[q];
+        uint32_t mn = 0xffffffffu;
+        for (uint32_t t = lane; t < u; t += 32) mn = min(mn, cs[t]);
+        mn = __reduce_min_sync(FULL, mn);
+        uint32_t k = 0;
+        for (uint32_t t = lane; t < u; t += 32) k += cs[t] == mn ? 1u : 0u;
+        k = __reduce_add_sync(FULL, k);
+        if (lane == 0) {
+            bcnt[q] = k;
+            qmin[q] = mn;
+        }
+    }
+}
+
+// best hits, warp per query: its minimum-cost intervals (and costs) at boff[q], in order
+__global__ void k_best_compact(uint32_t nq, const uint32_t *__restrict__ ucnt,
+                               const uint64_t *__restrict__ start, const uint64_t *__restrict__ uoff,
+                               const uint64_t *__restrict__ grouped, const uint32_t *__restrict__ cost32,
+                               const uint32_t *__restrict__ qmin, const uint64_t *__restrict__ boff,
+                               uint32_t *__restrict__ pairs, uint8_t *__restrict__ costs,
+                               uint64_t capacity) {
+    if (boff[nq] > capacity) return;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += warps) {
+        const uint32_t u = ucnt[q], mn = qmin[q];
+        const uint64_t *seg = grouped + start[q];
+        const uint32_t *cs = cost32 + uoff[q];
+        uint64_t at = boff[q];
+        for (uint32_t base = 0; base < u; base += 32) {
+            const uint32_t t = base + lane;
+            const bool keep = t < u && cs[t] == mn;
+            const uint32_t bal = __ballot_sync(FULL, keep);
+            if (keep) {
+                const uint64_t o = at + __popc(bal & ((1u << lane) - 1u));
+                const uint64_t x = seg[t];
+                pairs[2 * o] = (uint32_t)(x >> 32);
+                pairs[2 * o + 1] = (uint32_t)x;
+                if (costs) costs[o] = (uint8_t)mn;
+            }
+            at += __popc(bal);
         }
     }
 }
@@ -1261,7 +1347,8 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
                 const fm_search_params *sp, uint32_t *counts, uint64_t *offsets, uint32_t *pairs,
                 uint64_t pair_capacity, uint64_t *pairs_needed, cudaStream_t st) {
     if (int krc = ensure_kmer(h, st)) return krc;
-    if (h->use_graphs && sp->kernel != FM_KERNEL_PLAIN && n_reads > 0) {
+    const bool want_cost = sp->costs != nullptr || sp->best;   // eager path only
+    if (h->use_graphs && sp->kernel != FM_KERNEL_PLAIN && n_reads > 0 && !want_cost) {
         bool fallback = true;
         const int grc = run_inexact_graph(h, reads, offs, n_reads, sp, counts, offsets, pairs,
                                           pair_capacity, pairs_needed, st, &fallback);
@@ -1407,7 +1494,10 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
                          off_start = (off_large + (size_t)nq * 4 + 15) / 16 * 16,
                          off_uoff = off_start + ((size_t)nq + 1) * 8,
                          off_tiles = off_uoff + ((size_t)nq + 1) * 8, off_grp = off_tiles + ntiles * 8,
-                         off_tmp = off_grp + (R ? R : 1) * 8, total = off_tmp + (R ? R : 1) * 8;
+                         off_tmp = off_grp + (R ? R : 1) * 8, off_cost = off_tmp + (R ? R : 1) * 8,
+                         off_bcnt = off_cost + (R ? R : 1) * 4, off_qmin = off_bcnt + (size_t)nq * 4,
+                         off_boff = (off_qmin + (size_t)nq * 4 + 15) / 16 * 16,
+                         total = want_cost ? off_boff + ((size_t)nq + 1) * 8 : off_cost;
             h->last_valid = false;
             if ((rc = ensure_scratch(h, h->s_group, total))) return rc;
             char *gb = (char *)h->s_group.ptr;
@@ -1436,12 +1526,34 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
                 ++launches;
             }
             if ((rc = scan_u32(h, ucnt, nq, uoff, tiles, st))) return rc;
-            FM_CUDA_TRY(h, cudaMemcpyAsync(offsets, uoff, ((size_t)nq + 1) * 8, cudaMemcpyDeviceToDevice, st));
-            k_copy_counts<<<grid_cap(h, nq, 256), 256, 0, st>>>(nq, ucnt, counts);
+            launches += 3u;
+            // fewest differences per interval, and the best hits
+            uint32_t *cost32 = (uint32_t *)(gb + off_cost), *bcnt = (uint32_t *)(gb + off_bcnt),
+                     *qmin = (uint32_t *)(gb + off_qmin);
+            uint64_t *boff = (uint64_t *)(gb + off_boff);
+            if (want_cost) {
+                FM_CUDA_TRY(h, cudaMemsetAsync(cost32, 0xff, (R ? R : 1) * 4, st));
+                if (R) {
+                    k_mincost<<<grid_cap(h, R, 256), 256, 0, st>>>(raw, d_raw_count, raw_cap, start, ucnt,
+                                                                  grouped, uoff, cost32);
+                    ++launches;
+                }
+                if (sp->best) {
+                    k_best_count<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, st>>>(nq, ucnt, uoff, cost32,
+                                                                                       bcnt, qmin);
+                    FM_CUDA_TRY(h, cudaGetLastError());
+                    if ((rc = scan_u32(h, bcnt, nq, boff, tiles, st))) return rc;
+                    launches += 4u;
+                }
+            }
+            const uint32_t *out_cnt = sp->best ? bcnt : ucnt;
+            const uint64_t *out_off = sp->best ? boff : uoff;
+            FM_CUDA_TRY(h, cudaMemcpyAsync(offsets, out_off, ((size_t)nq + 1) * 8, cudaMemcpyDeviceToDevice, st));
+            k_copy_counts<<<grid_cap(h, nq, 256), 256, 0, st>>>(nq, out_cnt, counts);
             FM_CUDA_TRY(h, cudaGetLastError());
-            launches += 3u + 1u;
+            launches += 1u;
             uint64_t need = 0;
-            FM_CUDA_TRY(h, cudaMemcpyAsync(&need, uoff + nq, 8, cudaMemcpyDeviceToHost, st));
+            FM_CUDA_TRY(h, cudaMemcpyAsync(&need, out_off + nq, 8, cudaMemcpyDeviceToHost, st));
             FM_CUDA_TRY(h, cudaStreamSynchronize(st));
             if (pairs_needed) *pairs_needed = need;
             h->last_nq = nq;
@@ -1450,7 +1562,7 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
             h->last_off_start = off_start;
             h->last_off_uoff = off_uoff;
             h->last_off_grp = off_grp;
-            h->last_valid = true;
+            h->last_valid = !want_cost;   // fm_inexact_fetch serves plain interval sets only
             if (sp->stats) {
                 k_add_stats<<<1, 32, 0, st>>>(d_stats, d_raw_count, (unsigned long long *)sp->stats,
                                               raw_cap, h->d_err);
@@ -1463,10 +1575,19 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
                                                    " below the " + std::to_string(need) + " intervals found");
             }
             if (need) {
-                k_compact<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, st>>>(nq, ucnt, start, uoff, grouped, pairs,
-                                                                                pair_capacity);
+                if (sp->best) {
+                    k_best_compact<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, st>>>(
+                        nq, ucnt, start, uoff, grouped, cost32, qmin, boff, pairs, sp->costs,
+                        pair_capacity);
+                } else {
+                    k_compact<<<grid_cap(h, (uint64_t)nq * 32, 256), 256, 0, st>>>(nq, ucnt, start, uoff, grouped, pairs,
+                                                                                    pair_capacity);
+                    if (sp->costs)
+                        k_cost_out<<<grid_cap(h, need ? need : 1, 256), 256, 0, st>>>(uoff + nq, cost32, sp->costs,
+                                                                                     pair_capacity);
+                }
                 FM_CUDA_TRY(h, cudaGetLastError());
-                ++launches;
+                launches += sp->costs && !sp->best ? 2u : 1u;
             }
             if ((rc = finish_profile(h, prof, ev, launches, st))) return rc;
             uint32_t derr = 0;
@@ -1562,6 +1683,8 @@ int run_inexact_noalloc(fm_index *h, const uint8_t *reads, const uint32_t *offs,
                         uint32_t n_reads, const fm_search_params *sp, uint32_t *counts,
                         uint64_t *offsets, uint32_t *pairs, uint64_t pair_capacity,
                         uint64_t *pairs_needed, cudaStream_t st) {
+    if (sp->costs || sp->best)
+        return set_error(h, FM_EINVAL, "fm_inexact_noalloc reports interval sets only (no costs, no best)");
     const uint64_t nq64 = (uint64_t)n_reads * sp->strands;
     if (nq64 > kNoAllocMaxQueries)
         return set_error(h, FM_EINVAL, "fm_inexact_noalloc: " + std::to_string(nq64) +

@@ -54,7 +54,8 @@ class fm_profile(C.Structure):
 class fm_search_params(C.Structure):
     _fields_ = [("z", C.c_uint32), ("max_gaps", C.c_uint32), ("strands", C.c_uint32),
                 ("kernel", C.c_uint32), ("stats", C.c_void_p),
-                ("profile", C.POINTER(fm_profile))]
+                ("profile", C.POINTER(fm_profile)), ("costs", C.c_void_p),
+                ("best", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class fm_tuning(C.Structure):
@@ -318,9 +319,12 @@ def fm_dcalc(h: Index, reads: torch.Tensor, offs: torch.Tensor, strands: int = 1
 def fm_inexact(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int, max_gaps: int = 0,
                strands: int = 1, kernel="auto", stats: torch.Tensor | None = None,
                pair_capacity: int | None = None, counts=None, offsets=None, pairs=None,
-               profile: fm_profile | None = None, stream=None):
+               profile: fm_profile | None = None, stream=None, costs=False, best=False):
     """Listing 2 interval sets.  Returns (counts int32[nq], offsets int64[nq+1],
-    pairs int32[total, 2]); on FM_ETRUNC the pairs buffer is regrown and fetched again."""
+    pairs int32[total, 2]), plus costs uint8[total] (per interval the fewest differences) when
+    ``costs`` is True or a uint8 tensor; ``best`` keeps only each query's minimum-cost
+    intervals.  On FM_ETRUNC the pairs buffer is regrown and fetched again (or, with costs or
+    best, the call is repeated with larger buffers)."""
     lib = load_library()
     nr = offs.numel() - 1
     nq = nr * strands
@@ -334,20 +338,43 @@ def fm_inexact(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int, max_ga
         cap = pair_capacity if pair_capacity is not None else 4 * nq + 1024
         pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=dev)
     cap = pairs.shape[0]
-    sp = fm_search_params(z, max_gaps, strands, kern,
-                          _dptr(stats, _U64, "stats") if stats is not None else None,
-                          C.pointer(profile) if profile is not None else None)
-    need = C.c_uint64(0)
-    rc = lib.fm_inexact(h.ptr, _dptr(reads, _U8, "reads"), _dptr(offs, _U32, "offs"), nr,
-                        C.byref(sp), _dptr(counts, _U32, "counts"),
-                        _dptr(offsets, _U64, "offsets"), _dptr(pairs, _U32, "pairs"), cap,
-                        C.byref(need), _stream(stream))
-    if rc == FM_ETRUNC:
-        pairs = torch.empty((max(int(need.value), 1), 2), dtype=torch.int32, device=dev)
+    want_costs = costs is not False and costs is not None
+    if want_costs and not isinstance(costs, torch.Tensor):
+        costs = torch.empty(max(cap, 1), dtype=torch.uint8, device=dev)
+    if want_costs and costs.numel() < cap:
+        raise ValueError("costs must hold pair capacity entries")
+
+    def call():
+        sp = fm_search_params(z, max_gaps, strands, kern,
+                              _dptr(stats, _U64, "stats") if stats is not None else None,
+                              C.pointer(profile) if profile is not None else None,
+                              _dptr(costs, _U8, "costs") if want_costs else None,
+                              1 if best else 0, 0)
+        need = C.c_uint64(0)
+        rc = lib.fm_inexact(h.ptr, _dptr(reads, _U8, "reads"), _dptr(offs, _U32, "offs"), nr,
+                            C.byref(sp), _dptr(counts, _U32, "counts"),
+                            _dptr(offsets, _U64, "offsets"), _dptr(pairs, _U32, "pairs"),
+                            pairs.shape[0], C.byref(need), _stream(stream))
+        return rc, int(need.value)
+
+    rc, need = call()
+    if rc == FM_ETRUNC and (want_costs or best):
+        # counts and offsets are complete; repeat with buffers of the needed size
+        pairs = torch.empty((max(need, 1), 2), dtype=torch.int32, device=dev)
+        if want_costs:
+            costs = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+        if stats is not None:
+            raise FmError(FM_ETRUNC, "pair capacity below the intervals found (stats would "
+                                     "count the search twice)")
+        rc, need = call()
+    elif rc == FM_ETRUNC:
+        pairs = torch.empty((max(need, 1), 2), dtype=torch.int32, device=dev)
         rc = lib.fm_inexact_fetch(h.ptr, _dptr(pairs, _U32, "pairs"), pairs.shape[0],
                                   _stream(stream))
     _check(rc, h)
-    return counts[:nq], offsets, pairs[:int(need.value)]
+    if want_costs:
+        return counts[:nq], offsets, pairs[:need], costs[:need]
+    return counts[:nq], offsets, pairs[:need]
 
 
 def fm_inexact_noalloc(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int,
@@ -367,7 +394,7 @@ def fm_inexact_noalloc(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int
         offsets = torch.empty(nq + 1, dtype=torch.int64, device=dev)
     if pairs is None:
         pairs = torch.empty((4 * nq + 1024, 2), dtype=torch.int32, device=dev)
-    sp = fm_search_params(z, max_gaps, strands, FM_KERNEL_PERSISTENT, None, None)
+    sp = fm_search_params(z, max_gaps, strands, FM_KERNEL_PERSISTENT, None, None, None, 0, 0)
     need = C.c_uint64(0)
     rc = lib.fm_inexact_noalloc(h.ptr, _dptr(reads, _U8, "reads"), _dptr(offs, _U32, "offs"), nr,
                                 C.byref(sp), _dptr(counts, _U32, "counts"),

@@ -52,3 +52,38 @@ def test_host_side_argument_errors(lib):
     assert b"interval" in lib.fm_last_error(None)
     assert lib.fm_occ8(None, None, None, None, 0, None) == fmocc.FM_EINVAL
     assert lib.fm_inexact(None, None, None, 0, None, None, None, None, 0, None, None) == fmocc.FM_EINVAL
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every public struct of include/fmocc.h has, in the ctypes binding, the C compiler's size
+    and the same offset for every field (a drift between the two corrupts arguments)."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_1811_06127_gb300 import fmocc
+
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = [fmocc.fm_params, fmocc.fm_info_t, fmocc.fm_profile, fmocc.fm_search_params,
+               fmocc.fm_tuning, fmocc.fm_server_params, fmocc.fm_server_result]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fmocc.h"', 'int main(void) {']
+    for st in structs:
+        name = st.__name__
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in st._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c11", "-I", inc, "-o", str(exe), str(src)], check=True)
+    got = dict(line.rsplit(" ", 1) for line in
+               subprocess.run([str(exe)], capture_output=True, text=True, check=True)
+               .stdout.splitlines())
+    for st in structs:
+        name = st.__name__
+        assert int(got[f"{name} size"]) == ctypes.sizeof(st), name
+        for field, _ in st._fields_:
+            assert int(got[f"{name} {field}"]) == getattr(st, field).offset, (name, field)

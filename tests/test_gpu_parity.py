@@ -253,6 +253,84 @@ def test_inexact_matches_oracle(fm, z, gaps):
     _inexact_case(fm, R, reads, z, gaps, 64)
 
 
+def _best_of(want):
+    """Per query, the intervals of its minimum cost (from the oracle's sets and costs)."""
+    counts, pairs, costs = [], [], []
+    o = want["offsets"]
+    for q in range(want["counts"].size):
+        c = want["costs"][o[q]:o[q + 1]]
+        keep = c == c.min() if c.size else np.zeros(0, bool)
+        counts.append(int(keep.sum()))
+        pairs.append(want["pairs"][o[q]:o[q + 1]][keep])
+        costs.append(c[keep])
+    offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.uint64)
+    return (np.array(counts, np.uint32), offsets, np.concatenate(pairs).reshape(-1, 2),
+            np.concatenate(costs))
+
+
+@pytest.mark.parametrize("z,gaps", [(1, 0), (2, 0), (2, 1), (2, 2), (3, 1)])
+def test_inexact_costs_and_best_hits(fm, z, gaps):
+    """Per interval the fewest differences of its alignments, and best-hit reporting (only each
+    query's minimum-cost intervals): equal to the oracle's, for both kernels, with the
+    canonical enumeration and interval tables (the defaults) and without them."""
+    R = synth.repeat_text(1811061273, 300_000, families=30, min_len=300, max_len=3000)
+    reads = synth.sample_reads(61 + z, R, 300 if z < 3 else 80, 1, 150, sub_rate=0.015,
+                               indel_rate=0.005, both_strands=True, random_frac=0.05)
+    h = fm.fm_build(R)
+    want = oracle.Index(R, "sais").inexact(reads.codes, reads.offs, z, gaps, strands=2)
+    bc, bo, bp, bcost = _best_of(want)
+    codes, offs = fm.to_device_reads(reads)
+    for tuning in ({}, {"canonical": 2, "kmer_depth": fm.KMER_OFF}):
+        if tuning:
+            fm.fm_set_tuning(h, **tuning)
+        for kern in ("plain", "persistent"):
+            tag = (kern, tuning)
+            c, o, p, cs = fm.fm_inexact(h, codes, offs, z, gaps, strands=2, kernel=kern,
+                                        costs=True)
+            assert np.array_equal(_u32(c), want["counts"]), tag
+            assert np.array_equal(o.cpu().numpy().astype(np.uint64), want["offsets"]), tag
+            assert np.array_equal(_u32(p), want["pairs"]), tag
+            assert np.array_equal(cs.cpu().numpy(), want["costs"]), tag
+            c, o, p, cs = fm.fm_inexact(h, codes, offs, z, gaps, strands=2, kernel=kern,
+                                        costs=True, best=True)
+            assert np.array_equal(_u32(c), bc), tag
+            assert np.array_equal(o.cpu().numpy().astype(np.uint64), bo), tag
+            assert np.array_equal(_u32(p), bp), tag
+            assert np.array_equal(cs.cpu().numpy(), bcost), tag
+            c, o, p = fm.fm_inexact(h, codes, offs, z, gaps, strands=2, kernel=kern, best=True)
+            assert np.array_equal(_u32(p), bp), tag
+    # too small a buffer: counts and offsets complete, the binding repeats the call
+    c, o, p, cs = fm.fm_inexact(h, codes, offs, z, gaps, strands=2, costs=True, pair_capacity=2)
+    assert np.array_equal(_u32(p), want["pairs"])
+    assert np.array_equal(cs.cpu().numpy(), want["costs"])
+    h.close()
+
+
+def test_costs_rejected_where_unsupported(fm):
+    R = synth.uniform_text(7, 2000)
+    h = fm.fm_build(R)
+    reads = synth.sample_reads(8, R, 10, 10, 20)
+    codes, offs = fm.to_device_reads(reads)
+    sp = fm.fm_search_params(1, 0, 1, fm.FM_KERNEL_PERSISTENT, None, None, None, 1, 0)
+    counts = torch.empty(10, dtype=torch.int32, device="cuda")
+    offsets = torch.empty(11, dtype=torch.int64, device="cuda")
+    pairs = torch.empty((100, 2), dtype=torch.int32, device="cuda")
+    need = fm.C.c_uint64(0)
+    lib = fm.load_library()
+    rc = lib.fm_inexact_noalloc(h.ptr, fm._dptr(codes, fm._U8, "r"), fm._dptr(offs, fm._U32, "o"),
+                                10, fm.C.byref(sp), fm._dptr(counts, fm._U32, "c"),
+                                fm._dptr(offsets, fm._U64, "f"), fm._dptr(pairs, fm._U32, "p"), 100,
+                                fm.C.byref(need), None)
+    assert rc == fm.FM_EINVAL
+    sp.best, sp.reserved = 2, 0
+    rc = lib.fm_inexact(h.ptr, fm._dptr(codes, fm._U8, "r"), fm._dptr(offs, fm._U32, "o"), 10,
+                        fm.C.byref(sp), fm._dptr(counts, fm._U32, "c"),
+                        fm._dptr(offsets, fm._U64, "f"), fm._dptr(pairs, fm._U32, "p"), 100,
+                        fm.C.byref(need), None)
+    assert rc == fm.FM_EINVAL
+    h.close()
+
+
 @pytest.mark.parametrize("depth", [1, 3, 7, 10, 13, 14])
 def test_inexact_interval_table_depths(fm, depth):
     """Tables of every depth, up to deeper than the strings of the search's first steps on this

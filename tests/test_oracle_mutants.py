@@ -57,8 +57,9 @@ MUTANTS = [
      "if (X->prune && i >= 1 && z < X->D[i - 1]) return;"),
     ("no dedup of intervals", "    if (v.size > 1) { /* sort and keep distinct intervals */",
      "    if (0) { /* sort and keep distinct intervals */"),
-    ("empty match reported", "        if (k >= 1) pv_push(X->out, (uint32_t)k, (uint32_t)l);",
-     "        pv_push(X->out, (uint32_t)k, (uint32_t)l);"),
+    ("empty match reported",
+     "        if (k >= 1) pv_push(X->out, (uint32_t)k, (uint32_t)l, (uint32_t)(X->z0 - z));",
+     "        pv_push(X->out, (uint32_t)k, (uint32_t)l, (uint32_t)(X->z0 - z));"),
     ("D window keeps the failing symbol", "            z++;\n            lo = 0;\n            hi = ix->n + 1;\n            d = 0;",
      "            z++;\n            lo = 0;\n            hi = ix->n + 1;\n            d = 0;\n            narrow(ix, &lo, &hi, 0, W[i]);\n            d = 1;"),
     ("D counts every failing extension twice", "            z++;\n            lo = 0;",
@@ -70,6 +71,11 @@ MUTANTS = [
      "            if (p + d >= n) { /* suffix reaches $ first: smaller */\n                rel = -1;",
      "            if (p + d >= n) { /* suffix reaches $ first: smaller */\n                rel = 1;"),
     ("hamming window inclusive bound", "        if (mm <= z) hits++;", "        if (mm < z) hits++;"),
+    ("cost counts the differences left",
+     "        if (k >= 1) pv_push(X->out, (uint32_t)k, (uint32_t)l, (uint32_t)(X->z0 - z));",
+     "        if (k >= 1) pv_push(X->out, (uint32_t)k, (uint32_t)l, (uint32_t)z);"),
+    ("dedup keeps an arbitrary cost", "    for (int t = 0; t < 3; ++t)\n        if (x[t] != y[t])",
+     "    for (int t = 0; t < 2; ++t)\n        if (x[t] != y[t])"),
     ("canonical: no match after any insertion",
      "        if (W[i] == W[i + 1]) may_match = 0;", "        may_match = 0;"),
     ("canonical: mismatch allowed after an insertion",

@@ -352,8 +352,9 @@ def brute_inexact(text, w, z, gaps, prune=False, interval=4, canonical=False):
     (and, with prune, z_left >= D(i)) together with their checkpoint blocks of the given
     width at rank positions k and l+1.  canonical: only scripts whose adjacent columns pass
     canonical_pair_ok; a state counts only when a deletion (needs a gap and a difference
-    left), a mismatch (needs a difference left) or the match may follow it."""
-    strings = set()
+    left), a mismatch (needs a difference left) or the match may follow it.  The fourth value
+    maps each interval to the fewest differences of the scripts that reach it."""
+    strings = {}
     D = brute_D(text, w)
     stats = [0, 0]
 
@@ -369,7 +370,7 @@ def brute_inexact(text, w, z, gaps, prune=False, interval=4, canonical=False):
             return
         if i < 0:
             if x:
-                strings.add(x)
+                strings[x] = min(strings.get(x, 99), z - zl)
             return
         if g < gaps and ok(prev, ("I",), i):
             rec(i - 1, zl - 1, g + 1, x, ("I",))
@@ -389,12 +390,12 @@ def brute_inexact(text, w, z, gaps, prune=False, interval=4, canonical=False):
                 rec(i - 1, zl - (b != w[i]), g, b + x, ("M", b))
 
     rec(len(w) - 1, z, 0, "", None)
-    out = set()
-    for x in strings:
+    cost = {}
+    for x, c in strings.items():
         k, l = brute_interval(text, x)
         if k <= l:
-            out.add((k, l))
-    return sorted(out), stats[0], stats[1]
+            cost[(k, l)] = min(cost.get((k, l), 99), c)
+    return sorted(cost), stats[0], stats[1], cost
 
 
 def _pairs_of(res, q):
@@ -433,20 +434,25 @@ def test_inexact_bruteforce_tiny():
                     w = "".join(SYM[c] for c in W)
                     got = _pairs_of(res, q)
                     assert got == _pairs_of(res_np, q)
-                    want, nodes, blocks = brute_inexact(text, w, z, gaps, prune=True)
+                    want, nodes, blocks, cost = brute_inexact(text, w, z, gaps, prune=True)
                     assert got == want, (text, w, z, gaps)
+                    # fewest differences per interval
+                    o = res["offsets"]
+                    assert [int(c) for c in res["costs"][o[q]:o[q + 1]]] == \
+                        [cost[p] for p in want], (text, w, z, gaps)
                     assert (int(res["nodes"][q]), int(res["blocks"][q])) == (nodes, blocks)
-                    _, nodes, blocks = brute_inexact(text, w, z, gaps, prune=False)
+                    _, nodes, blocks, _ = brute_inexact(text, w, z, gaps, prune=False)
                     assert (int(res_np["nodes"][q]), int(res_np["blocks"][q])) == (nodes, blocks)
                     # canonical enumeration: Listing 2's intervals, the brute-force counts
-                    want_c, nodes_c, blocks_c = brute_inexact(text, w, z, gaps, prune=True,
-                                                              canonical=True)
-                    assert want_c == want, (text, w, z, gaps)
+                    want_c, nodes_c, blocks_c, cost_c = brute_inexact(text, w, z, gaps,
+                                                                      prune=True, canonical=True)
+                    assert want_c == want and cost_c == cost, (text, w, z, gaps)
                     assert _pairs_of(res_c, q) == want
                     assert (int(res_c["nodes"][q]), int(res_c["blocks"][q])) == \
                         (nodes_c, blocks_c), (text, w, z, gaps)
                     assert nodes_c <= nodes
                     cases += 1
+                assert np.array_equal(res_c["costs"], res["costs"])
     assert cases > 500
 
 
@@ -477,8 +483,8 @@ def test_canonical_bruteforce_runs():
             res_c = ix.inexact(codes, offs, z, gaps, strands=1, interval=4, canonical=True)
             for q, W in enumerate(ws):
                 w = "".join(SYM[c] for c in W)
-                want, nodes_c, blocks_c = brute_inexact(text, w, z, gaps, prune=True,
-                                                        canonical=True)
+                want, nodes_c, blocks_c, _ = brute_inexact(text, w, z, gaps, prune=True,
+                                                           canonical=True)
                 assert _pairs_of(res_c, q) == _pairs_of(res, q) == want, (text, w, z, gaps)
                 assert (int(res_c["nodes"][q]), int(res_c["blocks"][q])) == (nodes_c, blocks_c)
                 cases += 1
@@ -504,7 +510,7 @@ def test_canonical_same_results(kind):
     for z, gaps in ((1, 1), (2, 1), (2, 2), (3, 1), (3, 3)):
         a = ix.inexact(reads.codes, reads.offs, z, gaps, strands=2)
         b = ix.inexact(reads.codes, reads.offs, z, gaps, strands=2, canonical=True)
-        for key in ("counts", "offsets", "pairs"):
+        for key in ("counts", "offsets", "pairs", "costs"):
             assert np.array_equal(a[key], b[key]), (kind, z, gaps, key)
         assert (b["nodes"] <= a["nodes"]).all()
         assert b["nodes"].sum() < a["nodes"].sum()
@@ -525,10 +531,16 @@ def test_inexact_hamming_identity_and_z0():
             pairs = _pairs_of(res, q)
             total = sum(b - a + 1 for a, b in pairs)
             assert total == oracle.hamming_count(R, W, 2)
+            # mismatches only: an interval's cost is the Hamming distance of W to its string
+            o = res["offsets"]
+            for (a, _), c in zip(pairs, res["costs"][o[q]:o[q + 1]]):
+                p = int(ix.sa[a])
+                assert int(c) == int((R[p:p + W.size] != W).sum())
             # disjoint: mismatch-only strings share one length
             for (a0, b0), (a1, b1) in zip(pairs, pairs[1:]):
                 assert b0 < a1
             p0 = _pairs_of(res0, q)
+            assert not res0["costs"].any()
             if s == 0:
                 ke, le = int(k[r]), int(l[r])
                 assert p0 == ([(ke, le)] if ke <= le else [])
