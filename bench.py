@@ -45,7 +45,7 @@ BLOCK_BYTES = {32: 32, 64: 32, 128: 64, 256: 96}
 # reported only when the run matches that configuration
 # keyed by (interval, reference bp, reads, canonical enumeration on, interval-table depth); an
 # entry is removed when the kernel changes and added back from a fresh capture
-TRAFFIC_NCU = {}
+TRAFFIC_NCU = {(64, 2_000_000_000, 10_000_000, True, 13): 3.952365751040e12 + 1.226240768e9}
 
 
 def parse():
@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-best", action="store_true")
+    ap.add_argument("--skip-both", action="store_true")
     ap.add_argument("--skip-cfg3", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
@@ -353,6 +355,34 @@ def main():
                  "ms_per_step": 1000 * ptot / len(pms), "steps": len(pms),
                  "kernel_ms": prof.ms_search, "bit_exact_vs_persistent": same_plain}
 
+    # ---- minimum-cost annotation and best hits on the same batch -------------------------
+    best = None
+    if not args.skip_best:
+        costs_buf = torch.empty(pairs_cap, dtype=torch.uint8, device=dev)
+        best_pairs = torch.empty((pairs_cap, 2), dtype=torch.int32, device=dev)
+
+        def search_best():
+            return fmocc.fm_inexact(h, codes, offs, 2, 1, strands=2, counts=counts,
+                                    offsets=offsets, pairs=best_pairs, costs=costs_buf,
+                                    best=True, profile=prof)
+        search_best()
+        barrier()
+        flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        _, ob, pb, cb = search_best()
+        b.record()
+        torch.cuda.synchronize()
+        bms = max_over_ranks(a.elapsed_time(b) / 1000.0)
+        cvals = cb.cpu().numpy()
+        best = {"value": args.reads * world / bms, "unit": "reads/s", "ms_per_step": 1000 * bms,
+                "steps": 1, "what": "every query's minimum-cost intervals with their costs "
+                                    "(eager path: search, grouping, per-interval minimum cost, "
+                                    "best-hit compaction)",
+                "best_intervals": int(ob[-1].item()),
+                "all_intervals": int(ref_offsets[-1].item()),
+                "cost_histogram": np.bincount(cvals, minlength=3).tolist()}
+
     # ---- e2e through the C ABI with host buffers ----------------------------------------
     e2e = None
     if not args.skip_e2e:
@@ -391,6 +421,8 @@ def main():
         occ8 = bench_occ8(args, torch, fmocc, synth, dev, hbm_peak, peak_kind, flush, barrier,
                           max_over_ranks, world)
     exact = bench_exact(args, torch, fmocc, synth, dev, flush, barrier)
+    both = None if args.skip_both else bench_both_strands(args, torch, fmocc, synth, dev, flush,
+                                                          barrier)
     cfg3 = None if args.skip_cfg3 else bench_cfg3(args, torch, fmocc, synth, dev, flush, barrier,
                                                    hbm_peak)
 
@@ -442,10 +474,12 @@ def main():
                    "bit_exact_repeat": same, "step_ms": step_ms,
                    "profile_last": prof.as_dict()},
         "plain": plain,
+        "best_hits": best,
         "e2e": e2e,
         "occ8": occ8,
         "exact": exact,
         "inexact_64mbp": cfg3,
+        "both_strands_256mbp": both,
         "serving": serving,
         "locate": locate,
         "cpu_baseline": cpu,
@@ -652,6 +686,40 @@ def bench_serving(args, fmocc, h, reads):
                                  "p50_ms": float(np.percentile(lat, 50)),
                                  "p99_ms": float(np.percentile(lat, 99)),
                                  "batches": srv.stats()["batches"] - b0})
+    return out
+
+
+def bench_both_strands(args, torch, fmocc, synth, dev, flush, barrier):
+    """Both strands two ways, 256 Mbp repeat reference, 10^6 reads of the main read model,
+    z=2 with 1 gap: each read and its reverse complement as two queries on the index of R,
+    against one query per read on the index of R . revcomp(R) (FM_BUILD_BOTH_STRANDS)."""
+    R = synth.repeat_text(1811061276, 256_000_000)
+    reads = synth.sample_reads(1811061276, R, 1_000_000, 50, 250, sub_rate=0.01,
+                               indel_rate=0.0005, both_strands=True)
+    codes, offs = fmocc.to_device_reads(reads, dev)
+    out = {"reference_bp": R.size, "reads": len(reads)}
+    for name, kw, strands in (("two_queries", {}, 2), ("one_query_both_strands_index",
+                                                        {"both_strands": True}, 1)):
+        h = fmocc.fm_build(R, interval=64, device=dev.index, **kw)
+        stats = torch.zeros(4, dtype=torch.int64, device=dev)
+        prof = fmocc.fm_profile()
+        fmocc.fm_inexact(h, codes, offs, 2, 1, strands=strands)   # sizing, tables
+        ms = []
+        for rep in range(3):
+            flush()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            _, o, _ = fmocc.fm_inexact(h, codes, offs, 2, 1, strands=strands, profile=prof,
+                                       stats=stats if rep else None)
+            b.record()
+            torch.cuda.synchronize()
+            if rep:
+                ms.append(a.elapsed_time(b))
+        st = stats.cpu().numpy() / len(ms)
+        out[name] = {"reads_per_s": len(reads) / (np.mean(ms) / 1000), "ms_per_step": np.mean(ms),
+                     "nodes": float(st[0]), "intervals": int(o[-1].item()),
+                     "index_bytes": fmocc.fm_info(h)["bytes_device"]}
+        h.close()
     return out
 
 

@@ -61,10 +61,17 @@ typedef struct fm_params {
 #define FM_BUILD_CODES 1u        /* ref holds codes 0..3 instead of ASCII ACGTacgt */
 #define FM_BUILD_FORWARD_ONLY 2u /* skip the index of reverse(R): fm_dcalc and fm_inexact
                                     then return FM_EINVAL */
+#define FM_BUILD_BOTH_STRANDS 4u /* index the text T = R . revcomp(R) (length 2|R|, with
+                                    revcomp(R)[i] = 3 - R[|R|-1-i]) in place of R: one query
+                                    (strands = 1) then finds the occurrences on both strands.
+                                    Rows, intervals and locate positions are those of T (a
+                                    position p >= |R| is on the reverse strand; occurrences
+                                    that straddle the junction at |R| are occurrences of T).
+                                    Requires |R| <= 1,073,741,823 */
 
 /* Summary of a built index (fm_info). */
 typedef struct fm_info_t {
-    uint64_t n;              /* reference length |R| */
+    uint64_t n;              /* indexed text length: |R|, or 2|R| with FM_BUILD_BOTH_STRANDS */
     uint32_t interval;       /* checkpoint interval I */
     uint32_t block_bytes;    /* bytes per checkpoint block: 32 (I = 32, 64), 64 or 96 */
     uint64_t C[5];           /* C array (Fig. 1) */
@@ -75,6 +82,8 @@ typedef struct fm_info_t {
     uint64_t bytes_device;   /* device bytes held by the resident tables */
     int32_t has_reverse;
     int32_t device;
+    int32_t both_strands;    /* 1: built with FM_BUILD_BOTH_STRANDS (n is then 2|R|) */
+    int32_t reserved;
 } fm_info_t;
 
 /* Build the FM-index of R (Sec. 2: Eq. 1 suffix array, Eq. 2 BWT, C, and the checkpointed

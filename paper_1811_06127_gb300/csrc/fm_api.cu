@@ -50,6 +50,13 @@ struct DeviceGuard {
     }
 };
 
+// T[n + i] = 3 - T[n - 1 - i] (the reverse complement after R, codes already checked)
+__global__ void k_append_revcomp(uint8_t *__restrict__ t, uint64_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        t[n + i] = (uint8_t)(3u - t[n - 1 - i]);
+}
+
 __global__ void k_encode(uint8_t *__restrict__ t, uint64_t n, int ascii, uint32_t *__restrict__ err) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -93,7 +100,7 @@ struct FileHeader {
     uint64_t n_blocks;
     uint64_t C[5];
     uint64_t dollar, rev_dollar;
-    uint32_t has_rev, pad;
+    uint32_t has_rev, both_strands;
     uint64_t sa_rate, n_sa;
 };
 
@@ -163,6 +170,11 @@ int fm_build(const char *ref, uint64_t n, const fm_params *p, fm_index **out) {
     if (!ref) return set_global_error(FM_EINVAL, "ref is NULL");
     if (n < 1 || n > 2147483646ull)
         return set_global_error(FM_EINVAL, "reference length must be in [1, 2147483646]");
+    const bool both = p && (p->flags & FM_BUILD_BOTH_STRANDS);
+    if (both && n > 1073741823ull)
+        return set_global_error(FM_EINVAL, "with FM_BUILD_BOTH_STRANDS the reference length must be "
+                                           "at most 1073741823");
+    const uint64_t nt = both ? 2 * n : n;   // indexed text length
     uint32_t I = p && p->interval ? p->interval : 64;
     if (I != 32 && I != 64 && I != 128 && I != 256)
         return set_global_error(FM_EINVAL, "interval must be 32, 64, 128 or 256");
@@ -177,10 +189,11 @@ int fm_build(const char *ref, uint64_t n, const fm_params *p, fm_index **out) {
     fm_index *h = new fm_index();
     h->device = dev;
     h->sms = device_sms(dev);
-    h->n = n;
+    h->n = nt;
+    h->both_strands = both;
     h->interval = I;
     h->bbytes = block_bytes(I);
-    h->n_blocks = (n + 1) / I + 1;
+    h->n_blocks = (nt + 1) / I + 1;
     int rc = alloc_common(h);
     cudaStream_t st = nullptr;
     uint8_t *d_text = nullptr;
@@ -188,7 +201,7 @@ int fm_build(const char *ref, uint64_t n, const fm_params *p, fm_index **out) {
     if (!rc && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
         rc = cuda_status(h, cudaGetLastError(), "cudaStreamCreate");
     if (!rc) {
-        cudaError_t e = cudaMalloc((void **)&d_text, n);
+        cudaError_t e = cudaMalloc((void **)&d_text, nt);
         if (e != cudaSuccess) rc = cuda_status(h, e, "cudaMalloc(text)");
     }
     if (!rc) {
@@ -204,11 +217,16 @@ int fm_build(const char *ref, uint64_t n, const fm_params *p, fm_index **out) {
                                                            ? "reference holds a code above 3"
                                                            : "reference holds a symbol outside ACGTacgt");
     }
-    if (!rc) rc = build_index(h, d_text, n, false, &h->d_fwd, &h->dollar, h->C, &h->d_sa_sample, st);
-    if (!rc) h->n_sa_sample = (n + 1 + h->sa_rate - 1) / h->sa_rate;
+    if (!rc && both) {
+        k_append_revcomp<<<h->sms * 8, 256, 0, st>>>(d_text, n);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_status(h, e, "k_append_revcomp");
+    }
+    if (!rc) rc = build_index(h, d_text, nt, false, &h->d_fwd, &h->dollar, h->C, &h->d_sa_sample, st);
+    if (!rc) h->n_sa_sample = (nt + 1 + h->sa_rate - 1) / h->sa_rate;
     if (!rc && !(flags & FM_BUILD_FORWARD_ONLY)) {
         uint64_t Crev[5];
-        rc = build_index(h, d_text, n, true, &h->d_rev, &h->rev_dollar, Crev, nullptr, st);
+        rc = build_index(h, d_text, nt, true, &h->d_rev, &h->rev_dollar, Crev, nullptr, st);
         if (!rc) {
             h->has_rev = true;
             for (int b = 0; b < 5; ++b)
@@ -243,6 +261,7 @@ int fm_info(const fm_index *h, fm_info_t *out) {
     out->bytes_device = h->n_blocks * h->bbytes * (h->has_rev ? 2 : 1) + h->n_sa_sample * 4;
     if (h->kt_depth) out->bytes_device += (2ull << (2 * h->kt_depth)) * (8 + 1.0 / 8);
     out->has_reverse = h->has_rev ? 1 : 0;
+    out->both_strands = h->both_strands ? 1 : 0;
     out->device = h->device;
     return FM_OK;
 }
@@ -284,6 +303,7 @@ int fm_save(const fm_index *h_, const char *path) {
     hd.dollar = h->dollar;
     hd.rev_dollar = h->rev_dollar;
     hd.has_rev = h->has_rev;
+    hd.both_strands = h->both_strands ? 1u : 0u;
     hd.sa_rate = h->sa_rate;
     hd.n_sa = h->n_sa_sample;
     uint64_t sum = fnv1a(kFnvSeed, &hd, sizeof(hd));
@@ -342,6 +362,7 @@ int fm_load(const char *path, const fm_params *p, fm_index **out) {
     h->dollar = hd.dollar;
     h->rev_dollar = hd.rev_dollar;
     h->has_rev = hd.has_rev != 0;
+    h->both_strands = hd.both_strands != 0;
     h->sa_rate = hd.sa_rate;
     h->n_sa_sample = hd.n_sa;
     int rc = alloc_common(h);

@@ -96,6 +96,7 @@ struct fm_index {
     uint64_t C[5] = {0, 0, 0, 0, 0};
     uint64_t dollar = 0, rev_dollar = 0;
     bool has_rev = false;
+    bool both_strands = false;       // the text is R . revcomp(R)
     uint8_t *d_fwd = nullptr;        // forward checkpoint blocks
     uint8_t *d_rev = nullptr;        // reverse(R) checkpoint blocks
     uint32_t *d_sa_sample = nullptr; // SA[j * sa_rate]

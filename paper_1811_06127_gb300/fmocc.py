@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(PKG, "libfmocc.so")
 FM_OK, FM_EINVAL, FM_ENOMEM, FM_ECUDA, FM_ETRUNC, FM_ETIMEOUT, FM_EIO = range(7)
 FM_BUILD_CODES = 1
 FM_BUILD_FORWARD_ONLY = 2
+FM_BUILD_BOTH_STRANDS = 4
 FM_KERNEL_AUTO, FM_KERNEL_PLAIN, FM_KERNEL_PERSISTENT = 0, 1, 2
 KMER_AUTO, KMER_OFF = 0xFE, 0xFF
 KERNELS = {"auto": FM_KERNEL_AUTO, "plain": FM_KERNEL_PLAIN, "persistent": FM_KERNEL_PERSISTENT}
@@ -39,7 +40,8 @@ class fm_info_t(C.Structure):
     _fields_ = [("n", C.c_uint64), ("interval", C.c_uint32), ("block_bytes", C.c_uint32),
                 ("C", C.c_uint64 * 5), ("dollar_row", C.c_uint64), ("rev_dollar_row", C.c_uint64),
                 ("n_blocks", C.c_uint64), ("sa_sample_rate", C.c_uint64),
-                ("bytes_device", C.c_uint64), ("has_reverse", C.c_int32), ("device", C.c_int32)]
+                ("bytes_device", C.c_uint64), ("has_reverse", C.c_int32), ("device", C.c_int32),
+                ("both_strands", C.c_int32), ("reserved", C.c_int32)]
 
 
 class fm_profile(C.Structure):
@@ -203,8 +205,9 @@ class Index:
 
 
 def fm_build(ref, interval: int = 64, flags: int = 0, device: int = -1,
-             forward_only: bool = False) -> Index:
-    """Build the index of ``ref`` (bytes/str over ACGTacgt, or a uint8 numpy array of codes)."""
+             forward_only: bool = False, both_strands: bool = False) -> Index:
+    """Build the index of ``ref`` (bytes/str over ACGTacgt, or a uint8 numpy array of codes);
+    with ``both_strands`` the index of ref . revcomp(ref)."""
     lib = load_library()
     if isinstance(ref, np.ndarray):
         buf = np.ascontiguousarray(ref, dtype=np.uint8)
@@ -217,6 +220,8 @@ def fm_build(ref, interval: int = 64, flags: int = 0, device: int = -1,
         ptr, n = C.c_char_p(buf), len(buf)
     if forward_only:
         flags |= FM_BUILD_FORWARD_ONLY
+    if both_strands:
+        flags |= FM_BUILD_BOTH_STRANDS
     p = fm_params(interval, flags, device, 0)
     out = C.c_void_p()
     rc = lib.fm_build(C.cast(ptr, C.c_void_p), n, C.byref(p), C.byref(out))
@@ -239,7 +244,7 @@ def fm_info(h: Index) -> dict:
             "C": list(inf.C), "dollar_row": inf.dollar_row, "rev_dollar_row": inf.rev_dollar_row,
             "n_blocks": inf.n_blocks, "sa_sample_rate": inf.sa_sample_rate,
             "bytes_device": inf.bytes_device, "has_reverse": bool(inf.has_reverse),
-            "device": inf.device}
+            "device": inf.device, "both_strands": bool(inf.both_strands)}
 
 
 def fm_get_bwt(h: Index, rev: bool = False) -> np.ndarray:

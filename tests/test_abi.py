@@ -50,6 +50,10 @@ def test_host_side_argument_errors(lib):
     p.interval = 100
     assert lib.fm_build(C.c_char_p(b"ACGT"), 4, C.byref(p), C.byref(out)) == fmocc.FM_EINVAL
     assert b"interval" in lib.fm_last_error(None)
+    # both strands double the text: |R| above 2^30 - 1 is refused before any buffer is read
+    p.interval, p.flags = 64, fmocc.FM_BUILD_BOTH_STRANDS
+    assert lib.fm_build(C.c_char_p(b"ACGT"), 1073741824, C.byref(p), C.byref(out)) == fmocc.FM_EINVAL
+    assert b"BOTH_STRANDS" in lib.fm_last_error(None)
     assert lib.fm_occ8(None, None, None, None, 0, None) == fmocc.FM_EINVAL
     assert lib.fm_inexact(None, None, None, 0, None, None, None, None, 0, None, None) == fmocc.FM_EINVAL
 
