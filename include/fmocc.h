@@ -354,6 +354,14 @@ typedef struct fm_tuning {
                                    1.07 GB);
                                    FM_KMER_OFF none.  fm_get_tuning reports the depth in effect
                                    (FM_KMER_OFF for none) */
+    uint32_t pair_steps;        /* 1 (default): searches advance exact continuations two symbols
+                                   per step over a pair table (for each row, the two symbols
+                                   before its suffix; one 64-byte block per 64 rows, built from
+                                   the index on the first call that needs it: 2 x the
+                                   checkpoint table of I = 64).  Intervals, insertion points
+                                   and results are unchanged; an inexact search's stats[0] then
+                                   omits the middle node of a two-symbol step that ends the
+                                   branch.  2: one symbol per step (stats exactly as described) */
 } fm_tuning;
 
 #define FM_KMER_AUTO 0xfeu

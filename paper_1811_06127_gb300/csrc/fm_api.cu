@@ -121,6 +121,8 @@ void release(fm_index *h) {
     cudaFree(h->d_err);
     cudaFree(h->d_kt);
     cudaFree(h->d_kbits);
+    cudaFree(h->d_pblk);
+    cudaFree(h->d_psb);
     fm::Scratch *ss[] = {&h->s_qmeta, &h->s_raw, &h->s_spill, &h->s_group, &h->s_scan, &h->s_plain,
                          &h->s_misc};
     for (auto *s : ss) cudaFree(s->ptr);
@@ -260,6 +262,7 @@ int fm_info(const fm_index *h, fm_info_t *out) {
     out->sa_sample_rate = h->sa_rate;
     out->bytes_device = h->n_blocks * h->bbytes * (h->has_rev ? 2 : 1) + h->n_sa_sample * 4;
     if (h->kt_depth) out->bytes_device += (2ull << (2 * h->kt_depth)) * (8 + 1.0 / 8);
+    if (h->pairs_built) out->bytes_device += ((h->n + 1) / fm::kPairRows + 1) * 64 + ((h->n + 1) / fm::kPairSuper + 2) * 64;
     out->has_reverse = h->has_rev ? 1 : 0;
     out->both_strands = h->both_strands ? 1 : 0;
     out->device = h->device;
@@ -509,6 +512,7 @@ int fm_set_tuning(fm_index *h, const fm_tuning *t) {
     if (t->l2_fetch_bytes && t->l2_fetch_bytes != 32 && t->l2_fetch_bytes != 64 && t->l2_fetch_bytes != 128)
         return set_error(h, FM_EINVAL, "l2_fetch_bytes must be 32, 64 or 128");
     if (t->canonical > 2) return set_error(h, FM_EINVAL, "canonical must be 0, 1 or 2");
+    if (t->pair_steps > 2) return set_error(h, FM_EINVAL, "pair_steps must be 0, 1 or 2");
     if (t->kmer_depth > fm::kMaxKmerDepth && t->kmer_depth != FM_KMER_AUTO && t->kmer_depth != FM_KMER_OFF)
         return set_error(h, FM_EINVAL, "kmer_depth must be 0, 1..14, FM_KMER_AUTO or FM_KMER_OFF");
     if (t->warps_per_block) h->tune.warps_per_block = t->warps_per_block;
@@ -519,6 +523,7 @@ int fm_set_tuning(fm_index *h, const fm_tuning *t) {
     if (t->l2_fetch_bytes) h->tune.l2_fetch = t->l2_fetch_bytes;
     if (t->canonical) h->tune.canon = t->canonical == 1 ? 1u : 0u;
     if (t->kmer_depth) h->tune.kmer = t->kmer_depth;
+    if (t->pair_steps) h->tune.pairs = t->pair_steps == 1 ? 1u : 0u;
     if (t->graphs) h->use_graphs = t->graphs == 1;
     return FM_OK;
 }
@@ -536,6 +541,7 @@ int fm_get_tuning(const fm_index *h, fm_tuning *t) {
     t->canonical = h->tune.canon ? 1u : 2u;
     const uint32_t kd = fm::kmer_depth_for(h);
     t->kmer_depth = kd ? kd : FM_KMER_OFF;
+    t->pair_steps = h->tune.pairs ? 1u : 2u;
     return FM_OK;
 }
 

@@ -268,6 +268,47 @@ __device__ __forceinline__ void exact_step(const SearchCfg &c, const uint4 &nd, 
     out = make_uint4(nd.x, (i - 1u) | ybits, k2, l2);
 }
 
+// One exact continuation over two symbols: the interval of W[i-1] W[i] X from that of X through
+// the pair table, for interval (not shallow) nodes with i >= 1.  When non-empty it is the
+// interval of two single steps, both of whose nodes are counted (nn = 2); when empty the
+// branch ends either way and only this node is counted (the middle one may or may not have
+// been non-empty).  Sectors read go to the table-sector field of nblocks.
+template <int I>
+__device__ __forceinline__ void pair_step(const SearchCfg &c, const uint4 &nd, const uint4 &mt,
+                                          uint4 &out, bool &survive, bool &is_leaf,
+                                          uint32_t &nblocks, uint32_t &nn) {
+    const uint32_t i = nd.y & 255u;
+    const uint32_t b2 = w_at(c.reads, mt, i), b1 = w_at(c.reads, mt, i - 1u);
+    const uint32_t pc = 4u * b1 + b2, pk = nd.z, pl = nd.w + 1u;
+    const uint32_t jk = pk / kPairRows, jl = pl / kPairRows;
+    PairBlk Pk, Pl;
+    load_pair_block(c.ix, jk, pc, Pk);
+    if (jl == jk) Pl = Pk;
+    else load_pair_block(c.ix, jl, pc, Pl);
+    const uint32_t c2 = __ldg(c.ix.pc2 + pc);
+    const uint32_t k2 = c2 + pair_rank(c.ix, Pk, pc, pk);
+    const uint32_t l2 = c2 + pair_rank(c.ix, Pl, pc, pl) - 1u;
+    const bool alive = k2 <= l2;
+    nblocks = (jl == jk ? 2u : 4u) * kTabRead;
+    nn = alive ? 2u : 1u;
+    is_leaf = alive && i == 1u;
+    survive = alive && i >= 2u;
+    out = make_uint4(nd.x, (i - 2u) | (nd.y & 0xf000u), k2, l2);
+}
+
+// an exact continuation: two symbols from the pair table where it applies, else one
+template <int I>
+__device__ __forceinline__ void chain_step(const SearchCfg &c, const uint4 &nd, const uint4 &mt,
+                                           uint4 &out, bool &survive, bool &is_leaf,
+                                           uint32_t &nblocks, uint32_t &nn) {
+    if (c.ix.pairs && !(nd.y & kShallow) && (nd.y & 255u) >= 1u) {
+        pair_step<I>(c, nd, mt, out, survive, is_leaf, nblocks, nn);
+    } else {
+        exact_step<I>(c, nd, mt, out, survive, is_leaf, nblocks);
+        nn = 1u;
+    }
+}
+
 __device__ __forceinline__ uint32_t pick4(const uint32_t v[4], uint32_t b) {
     return b == 0 ? v[0] : (b == 1 ? v[1] : (b == 2 ? v[2] : v[3]));
 }
@@ -450,15 +491,15 @@ __global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk
                 }
                 uint4 c0 = make_uint4(0, 0, 0, 0), c1 = make_uint4(0, 0, 0, 0);
                 bool s0 = false, s1 = false, e0 = false, e1 = false;
-                uint32_t b0 = 0, b1 = 0;
+                uint32_t b0 = 0, b1 = 0, x0 = 0, x1 = 0;
                 if (a0) {
-                    exact_step<I>(c, n0, make_uint4(0, 0, r0.x, r0.y), c0, s0, e0, b0);
-                    my_nodes += 1;
+                    chain_step<I>(c, n0, make_uint4(0, 0, r0.x, r0.y), c0, s0, e0, b0, x0);
+                    my_nodes += x0;
                     my_blocks += step_cost(b0);
                 }
                 if (a1) {
-                    exact_step<I>(c, n1, make_uint4(0, 0, r1.x, r1.y), c1, s1, e1, b1);
-                    my_nodes += 1;
+                    chain_step<I>(c, n1, make_uint4(0, 0, r1.x, r1.y), c1, s1, e1, b1, x1);
+                    my_nodes += x1;
                     my_blocks += step_cost(b1);
                 }
                 const uint32_t lb0 = __ballot_sync(FULL, e0), lb1 = __ballot_sync(FULL, e1);
@@ -620,7 +661,7 @@ __global__ void __launch_bounds__(256) k_inexact_plain(SearchCfg c, uint4 *stack
             const uint4 mt = c.qmeta[nd.x];
             if (((nd.y >> 8) & 15u) == 0u) {
                 bool survive = false;
-                exact_step<I>(c, nd, mt, ex_out, survive, ex_leaf, nb);
+                chain_step<I>(c, nd, mt, ex_out, survive, ex_leaf, nb, counted);
                 if (survive) {
                     curnd = ex_out;
                     cur = true;
@@ -1203,7 +1244,7 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
     key.strands = sp->strands; key.z = sp->z; key.max_gaps = sp->max_gaps; key.interval = I;
     key.grid = (uint32_t)grid; key.block = (uint32_t)block; key.chunk = tu.chunk;
     key.spill_cap = spill_cap; key.profile = prof ? 1u : 0u; key.canon = tu.canon;
-    key.kt = h->d_kt; key.kdepth = h->kt_depth;
+    key.kt = h->d_kt; key.kdepth = h->kt_depth | (view_fwd(h).pairs << 16);
 
     char *misc = (char *)h->s_misc.ptr;
     unsigned long long *d_raw_count = (unsigned long long *)misc;
@@ -1347,6 +1388,7 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
                 const fm_search_params *sp, uint32_t *counts, uint64_t *offsets, uint32_t *pairs,
                 uint64_t pair_capacity, uint64_t *pairs_needed, cudaStream_t st) {
     if (int krc = ensure_kmer(h, st)) return krc;
+    if (int prc = ensure_pairs(h, st)) return prc;
     const bool want_cost = sp->costs != nullptr || sp->best;   // eager path only
     if (h->use_graphs && sp->kernel != FM_KERNEL_PLAIN && n_reads > 0 && !want_cost) {
         bool fallback = true;

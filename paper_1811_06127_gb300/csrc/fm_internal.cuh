@@ -46,6 +46,19 @@ struct IndexView {
     const uint2 *kt;
     const uint32_t *kbits;
     uint32_t kdepth;
+    // Pair table (0 when absent): for every row i, the two symbols before suffix SA[i],
+    // BWT[LF(i)] and BWT[i], as one 4-bit code 4 b1 + b2, so that one rank over pairs moves an
+    // interval back two symbols.  64-row blocks of 64 bytes: uint16 cnt[16] (pairs in the
+    // rows of its superblock of 32768 rows before the block, special rows excluded), then 64
+    // nibbles (row r of the block at bits 4(r%8) of 32-bit word r/8).  psb[s][c]: pairs c in
+    // the rows before superblock s; pc2[c]: rows whose suffix sorts before every string
+    // starting with pair c.  The $ row and the row whose LF is the $ row have no pair: stored
+    // as pair 0 and excluded from the counts (prow_a, prow_b).
+    const uint8_t *pblk;
+    const uint32_t *psb;
+    const uint32_t *pc2;
+    uint32_t prow_a, prow_b;
+    uint32_t pairs;
 };
 
 // Per-search device pointers (scratch owned by the handle).
@@ -81,6 +94,7 @@ struct Tuning {
     uint32_t occ_q = 2;
     uint32_t canon = 1;      // inexact search enumerates canonical alignments only
     uint32_t kmer = FM_KMER_AUTO;   // interval-table depth setting (FM_KMER_AUTO, FM_KMER_OFF, 1..14)
+    uint32_t pairs = 1;             // exact continuations two symbols per step from the pair table
     uint32_t l2_fetch = 0;   // 0: leave the context's limit alone
 };
 
@@ -106,6 +120,10 @@ struct fm_index {
     uint2 *d_kt = nullptr;           // interval tables of short strings (forward index)
     uint32_t *d_kbits = nullptr;     // their occurrence bits
     uint32_t kt_depth = 0;           // levels built (0: none)
+    uint8_t *d_pblk = nullptr;       // pair table (see IndexView)
+    uint32_t *d_psb = nullptr;       // its superblock counts, then pc2[16]
+    uint32_t prow_a = 0, prow_b = 0;
+    bool pairs_built = false;
     // grow-on-demand scratch of the search calls
     fm::Scratch s_qmeta, s_raw, s_spill, s_group, s_scan, s_plain, s_misc;
     fm::Tuning tune;
@@ -157,6 +175,9 @@ int launch_exact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32
 // interval tables: the depth the tuning asks for on this index, and (re)building them to it
 uint32_t kmer_depth_for(const fm_index *h);
 int ensure_kmer(fm_index *h, cudaStream_t st);
+// pair table: built on first use when the tuning asks for pair steps
+int ensure_pairs(fm_index *h, cudaStream_t st);
+constexpr uint32_t kPairRows = 64, kPairSuper = 32768;
 constexpr uint32_t kMaxKmerDepth = 14;
 // D lower bound per query; qmeta (uint4 per query) and/or D_out (uint8 per position)
 int launch_dcalc(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
@@ -271,6 +292,51 @@ __device__ __forceinline__ uint32_t low_mask(uint32_t width) {
     uint32_t m;
     asm("bmsk.clamp.b32 %0, %1, %2;" : "=r"(m) : "r"(0u), "r"(width));
     return m;
+}
+
+// The part of a pair block one rank of pair c needs: the word holding cnt[c] (two uint16 per
+// word, low half first) and the 64 nibbles.
+struct PairBlk {
+    uint32_t cw;
+    uint4 s0, s1;
+};
+
+__device__ __forceinline__ void load_pair_block(const IndexView &ix, uint32_t j, uint32_t c, PairBlk &B) {
+    const uint8_t *p = ix.pblk + (size_t)j * 64;
+    B.cw = __ldg((const uint32_t *)p + (c >> 1));
+    ldg256(p + 32, B.s0, B.s1);
+}
+
+// Pairs c among the first o rows (o in [0, 64]) of a pair block: XOR with c in every nibble
+// leaves a zero nibble where the pair is c; OR-folding a nibble onto its low bit then leaves
+// that bit clear exactly there.
+__device__ __forceinline__ uint32_t pair_count_in(const PairBlk &B, uint32_t c, uint32_t o) {
+    const uint32_t s[8] = {B.s0.x, B.s0.y, B.s0.z, B.s0.w, B.s1.x, B.s1.y, B.s1.z, B.s1.w};
+    const uint32_t pat = c * 0x11111111u;
+    uint32_t n = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const int32_t left = (int32_t)o - 8 * w;
+        const uint32_t t = left <= 0 ? 0u : (left >= 8 ? 8u : (uint32_t)left);
+        uint32_t x = s[w] ^ pat;
+        x |= x >> 1;
+        x |= x >> 2;
+        n += __popc(~x & 0x11111111u & low_mask(4u * t));
+    }
+    return n;
+}
+
+// Pairs c in rows [0, p) (rows without a pair excluded), B the pair block of p loaded for c.
+__device__ __forceinline__ uint32_t pair_rank(const IndexView &ix, const PairBlk &B, uint32_t c,
+                                              uint32_t p) {
+    const uint32_t j = p / kPairRows, o = p - j * kPairRows;
+    const uint32_t cnt = (c & 1u) ? (B.cw >> 16) : (B.cw & 0xffffu);
+    uint32_t n = __ldg(ix.psb + (size_t)(p / kPairSuper) * 16u + c) + cnt + pair_count_in(B, c, o);
+    if (c == 0u) {
+        const uint32_t b0 = j * kPairRows;   // rows without a pair are stored as pair 0
+        n -= (ix.prow_a >= b0 && ix.prow_a < p ? 1u : 0u) + (ix.prow_b >= b0 && ix.prow_b < p ? 1u : 0u);
+    }
+    return n;
 }
 
 // C, G and T among the first t symbols (t in [0, 32]) of one 64-bit word, in 32-bit steps:

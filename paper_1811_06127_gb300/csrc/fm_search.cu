@@ -9,6 +9,8 @@
 // C = popc(lo) - T, G = popc(hi) - T, and A is the remainder minus the $ correction.
 #include "fm_internal.cuh"
 
+#include <vector>
+
 namespace fm {
 
 IndexView view_fwd(const fm_index *h) {
@@ -20,6 +22,12 @@ IndexView view_fwd(const fm_index *h) {
     v.kt = h->d_kt;
     v.kbits = h->d_kbits;
     v.kdepth = h->kt_depth;
+    v.pblk = h->d_pblk;
+    v.psb = h->d_psb;
+    v.pc2 = h->d_psb ? h->d_psb + (h->n + 1) / kPairSuper * 16 + 16 : nullptr;
+    v.prow_a = h->prow_a;
+    v.prow_b = h->prow_b;
+    v.pairs = h->pairs_built && h->tune.pairs ? 1u : 0u;
     return v;
 }
 
@@ -29,6 +37,10 @@ IndexView view_rev(const fm_index *h) {
     v.kt = nullptr;
     v.kbits = nullptr;
     v.kdepth = 0;
+    v.pblk = nullptr;
+    v.psb = nullptr;
+    v.pc2 = nullptr;
+    v.pairs = 0;
     v.dollar = (uint32_t)h->rev_dollar;
     return v;
 }
@@ -130,6 +142,27 @@ __global__ void __launch_bounds__(128) k_exact(IndexView ix, const uint8_t *__re
             l = kl.y;
         }
         for (uint32_t i = e - j0; i > s; --i) {
+            if (ix.pairs && i - s >= 2u) {
+                // two symbols at once from the pair table (the same interval, insertion points
+                // included, as two single steps)
+                const uint32_t b2 = reads[i - 1], b1 = reads[i - 2];
+                if ((b1 | b2) > 3u) {
+                    atomicOr(err, kErrDomain);
+                    k = 0;
+                    l = ix.n;
+                    break;
+                }
+                const uint32_t pc = 4u * b1 + b2, pk = k, pl = l + 1u;
+                PairBlk Pk, Pl;
+                load_pair_block(ix, pk / kPairRows, pc, Pk);
+                if (pl / kPairRows == pk / kPairRows) Pl = Pk;
+                else load_pair_block(ix, pl / kPairRows, pc, Pl);
+                const uint32_t c2 = __ldg(ix.pc2 + pc);
+                k = c2 + pair_rank(ix, Pk, pc, pk);
+                l = c2 + pair_rank(ix, Pl, pc, pl) - 1u;
+                --i;
+                continue;
+            }
             const uint32_t b = reads[i - 1];
             if (b > 3u) {
                 atomicOr(err, kErrDomain);
@@ -317,6 +350,81 @@ __global__ void __launch_bounds__(256) k_kmer_bits(const uint2 *__restrict__ kt,
     }
 }
 
+// -------------------------------------------------------------------------------------------
+// Pair table.  Row i's pair is (BWT[LF(i)], BWT[i]) with LF(i) = C[b] + rank(b, i) + 1 for
+// b = BWT[i] (Eq. 4-5): the two symbols before suffix SA[i].  Thread per 8 rows (one nibble
+// word); the $ row and the row whose LF is the $ row have none (stored as 0, row b recorded).
+// -------------------------------------------------------------------------------------------
+template <int I>
+__global__ void __launch_bounds__(256) k_pair_sym(IndexView ix, uint8_t *__restrict__ pblk, uint64_t N,
+                                                  uint32_t *__restrict__ row_b) {
+    const uint64_t words = (N + 7) / 8;
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < words;
+         w += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t word = 0;
+        for (uint32_t t = 0; t < 8u; ++t) {
+            const uint64_t i64 = 8 * w + t;
+            if (i64 >= N) break;
+            const uint32_t i = (uint32_t)i64;
+            if (i == ix.dollar) continue;
+            const uint32_t jb = i / I;
+            Blk<I> B;
+            load_block<I>(ix.blocks, jb, i - jb * I + 1u, B);
+            const uint32_t b = sym_in<I>(B, jb, i);
+            const uint32_t cb = b == 0 ? ix.C[0] : (b == 1 ? ix.C[1] : (b == 2 ? ix.C[2] : ix.C[3]));
+            const uint32_t lf = cb + rank1_in<I>(B, jb, i, ix.dollar, b) + 1u;
+            if (lf == ix.dollar) {
+                *row_b = i;
+                continue;
+            }
+            const uint32_t jl = lf / I;
+            Blk<I> L;
+            load_block<I>(ix.blocks, jl, lf - jl * I + 1u, L);
+            const uint32_t b1 = sym_in<I>(L, jl, lf);
+            word |= (4u * b1 + b) << (4u * t);
+        }
+        const uint64_t r0 = 8 * w;
+        *(uint32_t *)(pblk + (r0 / kPairRows) * 64 + 32 + ((r0 % kPairRows) / 8) * 4) = word;
+    }
+}
+
+// Thread per (superblock, pair): the block counts relative to the superblock (uint16, written
+// into each block), and the superblock's total; rows >= N and rows without a pair not counted.
+__global__ void __launch_bounds__(256) k_pair_counts(uint8_t *__restrict__ pblk, uint64_t N,
+                                                     uint64_t nblk, uint32_t prow_a, uint32_t prow_b,
+                                                     uint32_t *__restrict__ sbtot, uint64_t nsb) {
+    const uint32_t per = kPairSuper / kPairRows;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nsb * 16;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t sbi = t / 16;
+        const uint32_t c = (uint32_t)(t % 16);
+        const uint32_t pat = c * 0x11111111u;
+        uint32_t acc = 0;
+        const uint64_t j1 = (sbi + 1) * per < nblk ? (sbi + 1) * per : nblk;
+        for (uint64_t j = sbi * per; j < j1; ++j) {
+            uint8_t *blk = pblk + j * 64;
+            *(uint16_t *)(blk + 2 * c) = (uint16_t)acc;
+            const uint32_t *sw = (const uint32_t *)(blk + 32);
+            const uint64_t r0 = j * kPairRows;
+            const uint32_t rows = N > r0 ? (uint32_t)(N - r0 < kPairRows ? N - r0 : kPairRows) : 0u;
+            uint32_t n = 0;
+            for (uint32_t q = 0; q < 8u; ++q) {
+                const int32_t left = (int32_t)rows - 8 * (int32_t)q;
+                const uint32_t m = left <= 0 ? 0u : (left >= 8 ? 8u : (uint32_t)left);
+                uint32_t x = sw[q] ^ pat;
+                x |= x >> 1;
+                x |= x >> 2;
+                n += __popc(~x & 0x11111111u & low_mask(4u * m));
+            }
+            if (c == 0u)
+                n -= (prow_a >= r0 && prow_a < r0 + rows ? 1u : 0u) +
+                     (prow_b >= r0 && prow_b < r0 + rows ? 1u : 0u);
+            acc += n;
+        }
+        sbtot[t] = acc;
+    }
+}
+
 int grid_occ(fm_index *h, uint64_t work, int block) {
     uint64_t g = (work + block - 1) / block;
     uint64_t cap = (uint64_t)h->sms * (2048 / block) * 4;
@@ -422,10 +530,91 @@ int ensure_kmer(fm_index *h, cudaStream_t st) {
     return FM_OK;
 }
 
+int ensure_pairs(fm_index *h, cudaStream_t st) {
+    if (!h->tune.pairs || h->pairs_built) return FM_OK;
+    const uint64_t N = h->n + 1;                    // rows
+    const uint64_t nblk = N / kPairRows + 1;        // rank positions 0..N
+    const uint64_t nsb = N / kPairSuper + 1;
+    const uint32_t sentinel = 0xffffffffu;
+    uint32_t *d_rowb = nullptr, *d_sbtot = nullptr;
+    int rc = FM_OK;
+    FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+    if (cudaMalloc(&h->d_pblk, nblk * 64) != cudaSuccess ||
+        cudaMalloc(&h->d_psb, (nsb * 16 + 16) * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&d_sbtot, nsb * 16 * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&d_rowb, sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        rc = set_error(h, FM_ENOMEM, "pair table: out of device memory");
+    }
+    std::vector<uint32_t> tot, psb;
+    if (!rc) {
+        FM_CUDA_TRY(h, cudaMemsetAsync(h->d_pblk, 0, nblk * 64, st));
+        FM_CUDA_TRY(h, cudaMemcpyAsync(d_rowb, &sentinel, 4, cudaMemcpyHostToDevice, st));
+        IndexView ix = view_fwd(h);
+        const int grid = grid_occ(h, (N + 7) / 8, 256);
+        switch (h->interval) {
+            case 32: k_pair_sym<32><<<grid, 256, 0, st>>>(ix, h->d_pblk, N, d_rowb); break;
+            case 64: k_pair_sym<64><<<grid, 256, 0, st>>>(ix, h->d_pblk, N, d_rowb); break;
+            case 128: k_pair_sym<128><<<grid, 256, 0, st>>>(ix, h->d_pblk, N, d_rowb); break;
+            default: k_pair_sym<256><<<grid, 256, 0, st>>>(ix, h->d_pblk, N, d_rowb); break;
+        }
+        FM_CUDA_TRY(h, cudaGetLastError());
+        uint32_t rowb = sentinel;
+        FM_CUDA_TRY(h, cudaMemcpyAsync(&rowb, d_rowb, 4, cudaMemcpyDeviceToHost, st));
+        FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+        if (rowb == sentinel) rc = set_error(h, FM_ECUDA, "pair table: no row precedes the $ row");
+        h->prow_a = (uint32_t)h->dollar;
+        h->prow_b = rowb;
+    }
+    if (!rc) {
+        k_pair_counts<<<grid_occ(h, nsb * 16, 256), 256, 0, st>>>(h->d_pblk, N, nblk, h->prow_a,
+                                                                  h->prow_b, d_sbtot, nsb);
+        FM_CUDA_TRY(h, cudaGetLastError());
+        tot.resize(nsb * 16);
+        FM_CUDA_TRY(h, cudaMemcpyAsync(tot.data(), d_sbtot, nsb * 16 * 4, cudaMemcpyDeviceToHost, st));
+        // the symbol of row 0 (the $ suffix) is T[n-1]: read it from the first checkpoint block
+        uint8_t b0[32];
+        FM_CUDA_TRY(h, cudaMemcpyAsync(b0, h->d_fwd, 32, cudaMemcpyDeviceToHost, st));
+        FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+        const uint32_t last = b0[16] & 3u;
+        // superblock bases (exclusive scan per pair), then pc2
+        psb.assign(nsb * 16 + 16, 0u);
+        uint64_t run[16] = {0};
+        for (uint64_t sbi = 0; sbi < nsb; ++sbi)
+            for (int c = 0; c < 16; ++c) {
+                psb[sbi * 16 + c] = (uint32_t)run[c];
+                run[c] += tot[sbi * 16 + c];
+            }
+        // rows before every string that starts with pair (b1, b2): the $ row, suffixes starting
+        // with a symbol below b1, the suffix "b1 $" when R ends with b1, and suffixes starting
+        // with b1 then a symbol below b2
+        for (uint32_t b1 = 0; b1 < 4; ++b1)
+            for (uint32_t b2 = 0; b2 < 4; ++b2) {
+                uint64_t v = 1 + h->C[b1] + (last == b1 ? 1 : 0);
+                for (uint32_t y = 0; y < b2; ++y) v += run[4 * b1 + y];
+                psb[nsb * 16 + 4 * b1 + b2] = (uint32_t)v;
+            }
+        FM_CUDA_TRY(h, cudaMemcpyAsync(h->d_psb, psb.data(), psb.size() * 4, cudaMemcpyHostToDevice, st));
+        FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+    }
+    cudaFree(d_sbtot);
+    cudaFree(d_rowb);
+    if (rc) {
+        cudaFree(h->d_pblk);
+        cudaFree(h->d_psb);
+        h->d_pblk = nullptr;
+        h->d_psb = nullptr;
+        return rc;
+    }
+    h->pairs_built = true;
+    return FM_OK;
+}
+
 int launch_exact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
                  uint32_t *k_out, uint32_t *l_out, cudaStream_t st) {
     if (n_reads == 0) return FM_OK;
     if (int rc = ensure_kmer(h, st)) return rc;
+    if (int rc = ensure_pairs(h, st)) return rc;
     IndexView ix = view_fwd(h);
     uint32_t *err = h->d_err + kErrExact;
     const int block = 128;

@@ -137,6 +137,7 @@ def test_inexact_64mbp_sample_matches_oracle(fm):
     reads = synth.sample_reads(1811061273, R, 20_000, 100, 100, sub_rate=0.005,
                                both_strands=True, random_frac=0.05)
     h = fm.fm_build(R, interval=64)
+    fm.fm_set_tuning(h, pair_steps=2)   # node totals as the oracle counts them
     codes, offs = fm.to_device_reads(reads)
     stats = torch.zeros(4, dtype=torch.int64, device="cuda")
     counts, offsets, pairs = fm.fm_inexact(h, codes, offs, 2, 0, strands=2, stats=stats)

@@ -52,7 +52,8 @@ def test_graph_replay_matches_oracle(fm, case):
     nq = 2 * len(reads)
     counts, offsets, pairs = _bufs(nq, 4 * nq + 1024)
     stats = torch.zeros(4, dtype=torch.int64, device="cuda")
-    fm.fm_set_tuning(h, kmer_depth=fm.KMER_OFF)   # block totals as the oracle counts them
+    # node and block totals as the oracle counts them: no tables, one symbol per exact step
+    fm.fm_set_tuning(h, kmer_depth=fm.KMER_OFF, pair_steps=2)
     kinds = []
     for _ in range(4):
         prof = fm.fm_profile()
@@ -73,6 +74,12 @@ def test_graph_replay_matches_oracle(fm, case):
                                 offsets=offsets, pairs=pairs)
         _check(want, c, o, p)
     assert stats.cpu().numpy()[0] == 2 * want["nodes"].sum()
+    # two-symbol exact steps: a new graph, the same results
+    fm.fm_set_tuning(h, pair_steps=1)
+    for _ in range(2):
+        c, o, p = fm.fm_inexact(h, codes, offs, 2, 1, strands=2, counts=counts,
+                                offsets=offsets, pairs=pairs)
+        _check(want, c, o, p)
     # new output buffers: a new graph is captured, results unchanged
     counts2, offsets2, pairs2 = _bufs(nq, 4 * nq + 1024)
     prof = fm.fm_profile()

@@ -153,6 +153,38 @@ def test_exact_matches_oracle(fm, interval):
     h.close()
 
 
+@pytest.mark.parametrize("n", [1, 2, 3, 62, 63, 64, 65, 127, 128, 4095, 32767, 32768, 70000])
+def test_exact_pair_steps_edge_sizes(fm, n):
+    """Listing 1 two symbols per step over the pair table on texts whose row count falls on
+    and around pair-block (64) and superblock (32768) boundaries: every string of length <= 5
+    and random reads, occurring or not (insertion points included), with and without pair
+    steps and tables, equal the oracle's."""
+    R = synth.uniform_text(900 + n, n) if n > 3 else np.array([0, 0, 1][:n], np.uint8)
+    ix = oracle.Index(R, "sais" if n > 64 else "naive")
+    words = [np.array([(c >> (2 * t)) & 3 for t in range(j)], np.uint8)
+             for j in range(0, 6) for c in range(4 ** j)]
+    rng = np.random.default_rng(n)
+    for _ in range(300):
+        m = int(rng.integers(1, 40))
+        if n > m and rng.random() < 0.7:
+            p = int(rng.integers(0, n - m + 1))
+            words.append(R[p:p + m].copy())
+        else:
+            words.append(rng.integers(0, 4, m).astype(np.uint8))
+    codes = np.concatenate(words).astype(np.uint8)
+    offs = np.concatenate([[0], np.cumsum([w.size for w in words])]).astype(np.uint32)
+    rd = synth.Reads(codes, offs)
+    kw, lw = ix.exact(codes, offs)
+    h = fm.fm_build(R)
+    c, o = fm.to_device_reads(rd)
+    for pairs, kmer in ((1, fm.KMER_AUTO), (1, fm.KMER_OFF), (2, fm.KMER_OFF)):
+        fm.fm_set_tuning(h, pair_steps=pairs, kmer_depth=kmer)
+        k, l = fm.fm_exact(h, c, o)
+        assert np.array_equal(_u32(k), kw), (pairs, kmer)
+        assert np.array_equal(_u32(l), lw), (pairs, kmer)
+    h.close()
+
+
 @pytest.mark.parametrize("depth", [1, 2, 6, 9, 11])
 def test_exact_interval_tables(fm, depth):
     """Listing 1 started from the interval tables: every string of length <= 6 (so every table
@@ -208,9 +240,11 @@ def test_dcalc_matches_oracle(fm, interval):
 def _inexact_case(fm, R, reads, z, gaps, interval, kernels=("plain", "persistent"),
                   modes=("canonical", "listing"), kmers=(0xFE, 0xFF)):   # tables auto, off
     """Both kernels, with the canonical enumeration (default) and with every call of Listing 2,
-    with and without interval tables: result sets equal the oracle's Listing 2 sets, node
-    counts equal the oracle's for the same enumeration, and so do block counts without tables
-    (with tables, nodes shorter than the table depth read no checkpoint block)."""
+    with and without interval tables, one symbol per exact step: result sets equal the
+    oracle's Listing 2 sets, node counts equal the oracle's for the same enumeration, and so do
+    block counts without tables (with tables, nodes shorter than the table depth read no
+    checkpoint block).  Then with two-symbol exact steps (the default): same sets, no more
+    nodes than the oracle's."""
     h = fm.fm_build(R, interval=interval)
     ix = oracle.Index(R, "sais")
     want_c = ix.inexact(reads.codes, reads.offs, z, gaps, strands=2, interval=interval,
@@ -222,7 +256,8 @@ def _inexact_case(fm, R, reads, z, gaps, interval, kernels=("plain", "persistent
     codes, offs = fm.to_device_reads(reads)
     for mode in modes:
         for kmer in kmers:
-            fm.fm_set_tuning(h, canonical=1 if mode == "canonical" else 2, kmer_depth=kmer)
+            fm.fm_set_tuning(h, canonical=1 if mode == "canonical" else 2, kmer_depth=kmer,
+                             pair_steps=2)
             ref = want_c if mode == "canonical" else want
             for kern in kernels:
                 stats = torch.zeros(4, dtype=torch.int64, device="cuda")
@@ -241,6 +276,15 @@ def _inexact_case(fm, R, reads, z, gaps, interval, kernels=("plain", "persistent
                 else:
                     assert st[1] <= ref["blocks"].sum(), tag
                     assert st[3] <= st[0], tag   # at most one table sector per node
+    fm.fm_set_tuning(h, canonical=1, kmer_depth=fm.KMER_AUTO, pair_steps=1)
+    for kern in kernels:
+        stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+        counts, offsets, pairs = fm.fm_inexact(h, codes, offs, z, gaps, strands=2, kernel=kern,
+                                               stats=stats)
+        assert np.array_equal(_u32(counts), want["counts"]), (kern, "pairs")
+        assert np.array_equal(offsets.cpu().numpy().astype(np.uint64), want["offsets"])
+        assert np.array_equal(_u32(pairs), want["pairs"]), (kern, "pairs")
+        assert stats.cpu().numpy()[0] <= want_c["nodes"].sum()
     h.close()
 
 
