@@ -43,9 +43,9 @@ BLOCK_BYTES = {32: 32, 64: 32, 128: 64, 256: 96}
 # DRAM bytes (read + write) per launch of the search kernel from one ncu capture
 # (profiles/k_inexact_persistent_2gbp_10m_reads_dram.md), by (interval, reference bp, reads):
 # reported only when the run matches that configuration
-# keyed by (interval, reference bp, reads, canonical enumeration on, interval-table depth); an
-# entry is removed when the kernel changes and added back from a fresh capture
-TRAFFIC_NCU = {(64, 2_000_000_000, 10_000_000, True, 13): 3.952365751040e12 + 1.226240768e9}
+# keyed by (interval, reference bp, reads, canonical enumeration on, interval-table depth, pair
+# steps on); an entry is removed when the kernel changes and added back from a fresh capture
+TRAFFIC_NCU = {}
 
 
 def parse():
@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--canonical", type=int, default=1, choices=[1, 2],
                     help="1: enumerate canonical alignments (same interval sets, fewer nodes); "
                          "2: every call of Listing 2")
+    ap.add_argument("--pair-steps", type=int, default=1, choices=[1, 2],
+                    help="1: exact continuations two symbols per step (pair table); 2: one")
     ap.add_argument("--kmer-depth", type=int, default=0xFE,
                     help="interval tables of short strings: 1..14 levels, 254 automatic "
                          "(floor(log4(n+1)) - 2), 255 none")
@@ -277,7 +279,8 @@ def main():
     notes["build_s"] = time.time() - t0
     if tuned:
         autotune.apply(h, tuned)
-    fmocc.fm_set_tuning(h, canonical=args.canonical, kmer_depth=args.kmer_depth)
+    fmocc.fm_set_tuning(h, canonical=args.canonical, kmer_depth=args.kmer_depth,
+                        pair_steps=args.pair_steps)
     kdepth = fmocc.fm_get_tuning(h)["kmer_depth"]
     kdepth = 0 if kdepth == fmocc.KMER_OFF else kdepth
     del R
@@ -442,6 +445,7 @@ def main():
                                 "kernel"),
                    "enumeration": ("canonical alignments (the interval sets of Listing 2)"
                                    if args.canonical == 1 else "every call of Listing 2"),
+                   "pair_steps": args.pair_steps == 1,
                    "interval_tables": (f"strings of length <= {kdepth} expanded from tables "
                                        f"({(2 << (2 * kdepth)) * 8 / 1e6:.0f} MB)"
                                        if kdepth else "none"),
@@ -455,14 +459,15 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
                      "traffic": TRAFFIC_NCU.get((args.interval, args.ref_n, args.reads,
-                                                 args.canonical == 1, kdepth)),
+                                                 args.canonical == 1, kdepth,
+                                                 args.pair_steps == 1)),
                      "kernel": "k_inexact_persistent", "kernel_ms": k_ms,
                      "gather_ceiling": ceil_main,
                      "blocks_per_s_over_gather_ceiling": (blocks_per_step / (k_ms / 1000) / 1e9
                                                           / ceil_main["g_gathers_s"]),
                      "algorithmic_bytes": alg_bytes, "peak_kind": peak_kind,
                      "per_unit": f"{bbytes} B per checkpoint block read and 32 B per "
-                                 f"interval-table sector read; "
+                                 f"interval-table or pair-table sector read; "
                                  f"{blocks_per_step / max(nodes_per_step, 1):.3f} blocks and "
                                  f"{tables_per_step / max(nodes_per_step, 1):.3f} table sectors "
                                  f"per node, {nodes_per_step / nq:.1f} nodes per query"},

@@ -162,6 +162,7 @@ __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, cons
         const uint32_t pk = k, pl = l + 1u;
         const uint32_t jk = pk / I, jl = pl / I;
         const uint32_t ok = pk - jk * I, ol = pl - jl * I;
+        // every lane runs the same counting code on (Bk, Bl), Bl a copy when they share a block
         Blk<I> Bk, Bl;
         if (jk == jl) {
             load_block<I>(c.ix.blocks, jk, ok > ol ? ok : ol, Bk);
@@ -247,6 +248,8 @@ __device__ __forceinline__ void exact_step(const SearchCfg &c, const uint4 &nd, 
         const uint32_t pk = k, pl = l + 1u;
         const uint32_t jk = pk / I, jl = pl / I;
         const uint32_t ok = pk - jk * I, ol = pl - jl * I;
+        // C[b] by select: a runtime index into the parameter struct would copy it to local memory
+        const uint32_t cb = b == 0 ? c.ix.C[0] : (b == 1 ? c.ix.C[1] : (b == 2 ? c.ix.C[2] : c.ix.C[3]));
         Blk<I> Bk, Bl;
         if (jk == jl) {
             load_block<I>(c.ix.blocks, jk, ok > ol ? ok : ol, Bk);
@@ -257,8 +260,6 @@ __device__ __forceinline__ void exact_step(const SearchCfg &c, const uint4 &nd, 
             load_block<I>(c.ix.blocks, jl, ol, Bl);
             nblocks = 2;
         }
-        // C[b] by select: a runtime index into the parameter struct would copy it to local memory
-        const uint32_t cb = b == 0 ? c.ix.C[0] : (b == 1 ? c.ix.C[1] : (b == 2 ? c.ix.C[2] : c.ix.C[3]));
         k2 = cb + rank1_in<I>(Bk, jk, pk, c.ix.dollar, b) + 1u;
         l2 = cb + rank1_in<I>(Bl, jl, pl, c.ix.dollar, b);
         alive = k2 <= l2;
@@ -281,11 +282,11 @@ __device__ __forceinline__ void pair_step(const SearchCfg &c, const uint4 &nd, c
     const uint32_t b2 = w_at(c.reads, mt, i), b1 = w_at(c.reads, mt, i - 1u);
     const uint32_t pc = 4u * b1 + b2, pk = nd.z, pl = nd.w + 1u;
     const uint32_t jk = pk / kPairRows, jl = pl / kPairRows;
-    PairBlk Pk, Pl;
+    const uint32_t c2 = __ldg(c.ix.pc2 + pc);
+    PairBlk Pk, Pl;   // the same counting code on every lane (Pl a copy when shared)
     load_pair_block(c.ix, jk, pc, Pk);
     if (jl == jk) Pl = Pk;
     else load_pair_block(c.ix, jl, pc, Pl);
-    const uint32_t c2 = __ldg(c.ix.pc2 + pc);
     const uint32_t k2 = c2 + pair_rank(c.ix, Pk, pc, pk);
     const uint32_t l2 = c2 + pair_rank(c.ix, Pl, pc, pl) - 1u;
     const bool alive = k2 <= l2;

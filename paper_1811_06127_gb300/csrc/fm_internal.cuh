@@ -307,33 +307,40 @@ __device__ __forceinline__ void load_pair_block(const IndexView &ix, uint32_t j,
     ldg256(p + 32, B.s0, B.s1);
 }
 
-// Pairs c among the first o rows (o in [0, 64]) of a pair block: XOR with c in every nibble
-// leaves a zero nibble where the pair is c; OR-folding a nibble onto its low bit then leaves
-// that bit clear exactly there.
+// Bit 3 of each nibble of the result is set exactly where that nibble of w equals pair c:
+// with x = w ^ (c in every nibble), (x & 7) + 7 reaches bit 3 of its nibble only when the low
+// three bits are not all zero (and never carries into the next nibble), and OR-ing x adds bit 3
+// itself.
+__device__ __forceinline__ uint32_t pair_flags(uint32_t w, uint32_t pat) {
+    const uint32_t x = w ^ pat;
+    return ~(((x & 0x77777777u) + 0x77777777u) | x) & 0x88888888u;
+}
+
+// rows of a word (8 nibbles) below prefix length o, as a mask of nibble bit 3s
+__device__ __forceinline__ uint32_t pair_prefix(uint32_t o, int w) {
+    const int32_t left = (int32_t)o - 8 * w;
+    const uint32_t t = left <= 0 ? 0u : (left >= 8 ? 8u : (uint32_t)left);
+    return low_mask(4u * t) & 0x88888888u;
+}
+
+// Pairs c among the first o rows (o in [0, 64]) of a pair block.
 __device__ __forceinline__ uint32_t pair_count_in(const PairBlk &B, uint32_t c, uint32_t o) {
     const uint32_t s[8] = {B.s0.x, B.s0.y, B.s0.z, B.s0.w, B.s1.x, B.s1.y, B.s1.z, B.s1.w};
     const uint32_t pat = c * 0x11111111u;
     uint32_t n = 0;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
-        const int32_t left = (int32_t)o - 8 * w;
-        const uint32_t t = left <= 0 ? 0u : (left >= 8 ? 8u : (uint32_t)left);
-        uint32_t x = s[w] ^ pat;
-        x |= x >> 1;
-        x |= x >> 2;
-        n += __popc(~x & 0x11111111u & low_mask(4u * t));
-    }
+    for (int w = 0; w < 8; ++w) n += __popc(pair_flags(s[w], pat) & pair_prefix(o, w));
     return n;
 }
 
 // Pairs c in rows [0, p) (rows without a pair excluded), B the pair block of p loaded for c.
 __device__ __forceinline__ uint32_t pair_rank(const IndexView &ix, const PairBlk &B, uint32_t c,
                                               uint32_t p) {
-    const uint32_t j = p / kPairRows, o = p - j * kPairRows;
     const uint32_t cnt = (c & 1u) ? (B.cw >> 16) : (B.cw & 0xffffu);
-    uint32_t n = __ldg(ix.psb + (size_t)(p / kPairSuper) * 16u + c) + cnt + pair_count_in(B, c, o);
+    uint32_t n = __ldg(ix.psb + (size_t)(p / kPairSuper) * 16u + c) + cnt +
+                 pair_count_in(B, c, p % kPairRows);
     if (c == 0u) {
-        const uint32_t b0 = j * kPairRows;   // rows without a pair are stored as pair 0
+        const uint32_t b0 = p / kPairRows * kPairRows;   // rows without a pair are stored as 0
         n -= (ix.prow_a >= b0 && ix.prow_a < p ? 1u : 0u) + (ix.prow_b >= b0 && ix.prow_b < p ? 1u : 0u);
     }
     return n;
