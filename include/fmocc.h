@@ -285,7 +285,8 @@ typedef struct fm_server_result {
     uint32_t reserved;
 } fm_server_result;
 
-/* Start the server thread on h.  Errors: FM_EINVAL, FM_ENOMEM, FM_ECUDA. */
+/* Start the server thread on h, after building the interval and pair tables the tuning asks
+ * for (so no request waits for them).  Errors: FM_EINVAL, FM_ENOMEM, FM_ECUDA. */
 int fm_server_start(fm_index *h, const fm_server_params *p, fm_server **out);
 
 /* Queue a request: reads are host memory (codes 0..3, concatenated, offs[n_reads+1]); they are

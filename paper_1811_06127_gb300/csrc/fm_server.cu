@@ -178,6 +178,16 @@ int fm_server_start(fm_index *h, const fm_server_params *p, fm_server **out) {
         delete s;
         return cuda_status(h, e, "cudaStreamCreate(server)");
     }
+    // the interval and pair tables are built here, not inside the first batch's latency
+    cudaSetDevice(h->device);
+    int rc = ensure_kmer(h, s->stream);
+    if (!rc) rc = ensure_pairs(h, s->stream);
+    if (prev >= 0) cudaSetDevice(prev);
+    if (rc) {
+        cudaStreamDestroy(s->stream);
+        delete s;
+        return rc;
+    }
     s->thr = std::thread(server_loop, s);
     *out = s;
     return FM_OK;
