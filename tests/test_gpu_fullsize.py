@@ -105,6 +105,28 @@ def test_exact_and_mismatch_counts_2gbp_repeats(fm):
     counts, offsets, pairs = a
     pr = _u32(pairs).astype(np.int64)
     assert ((pr[:, 0] >= 1) & (pr[:, 0] <= pr[:, 1]) & (pr[:, 1] <= R.size)).all()
+    # the optimisations change nothing at this size: canonical enumeration, interval tables and
+    # two-symbol steps (the defaults) against every call of Listing 2, one symbol per step, no
+    # tables, with costs, on a 20k-read slice
+    sl = reads.subset(np.arange(20_000))
+    lc, lo = fm.to_device_reads(sl)
+    fast = fm.fm_inexact(h, lc, lo, 2, 1, strands=2, costs=True)
+    fm.fm_set_tuning(h, canonical=2, kmer_depth=fm.KMER_OFF, pair_steps=2)
+    literal = fm.fm_inexact(h, lc, lo, 2, 1, strands=2, costs=True)
+    ke, le = fm.fm_exact(h, codes, offs)
+    fm.fm_set_tuning(h, canonical=1, kmer_depth=fm.KMER_AUTO, pair_steps=1)
+    for x, y in zip(fast, literal):
+        assert torch.equal(x, y)
+    k1, l1 = fm.fm_exact(h, codes, offs)
+    assert torch.equal(ke, k1) and torch.equal(le, l1)
+    # the cost-0 intervals of a read's search are exactly its exact-match interval
+    fc, fo, fp, fcost = (t.cpu().numpy() for t in fast)
+    ks, ls = _u32(k1)[:len(sl)], _u32(l1)[:len(sl)]
+    for r in range(len(sl)):
+        q = 2 * r
+        zero = fp[fo[q]:fo[q + 1]][fcost[fo[q]:fo[q + 1]] == 0].view(np.uint32)
+        want0 = [[ks[r], ls[r]]] if ks[r] <= ls[r] else []
+        assert zero.tolist() == want0, r
     # exact intervals of sampled reads against the closed form
     sample = reads.subset(np.arange(8))
     kn, ln, _ = oracle.interval_naive(R, sample.codes, sample.offs)
