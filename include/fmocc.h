@@ -168,7 +168,8 @@ typedef struct fm_search_params {
     uint32_t strands;  /* 1: reads as given; 2: each read and its reverse complement, as
                           queries q = 2r (read) and q = 2r+1 (reverse complement) */
     uint32_t kernel;   /* FM_KERNEL_* */
-    uint64_t *stats;   /* optional device uint64[4], accumulated by each successful call:
+    uint64_t *stats;   /* optional device uint64[4], accumulated by each call that completes
+                          its search (FM_OK, or FM_ETRUNC with counts and offsets filled):
                           [0] nodes expanded (calls of InexRecur reaching the Occ step; with
                               fm_tuning.canonical on, those of the canonical enumeration),
                           [1] checkpoint blocks read by those expansions (1 when k and l+1

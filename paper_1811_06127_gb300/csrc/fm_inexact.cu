@@ -767,8 +767,30 @@ __global__ void k_sort_small(uint32_t nq, const uint32_t *__restrict__ cnt,
     }
 }
 
-// CTA per large segment: bitonic sort in shared memory up to 8192 keys; above that, each key's
-// final position is its rank (keys smaller, plus equal keys before it), written to tmp
+// bitonic sort of P keys (a power of two, P <= 8192) in shared memory, by the whole CTA
+__device__ __forceinline__ void cta_bitonic(uint64_t *sk, uint32_t P) {
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t t = threadIdx.x; t < P; t += blockDim.x) {
+                const uint32_t o = t ^ j;
+                if (o > t) {
+                    const bool up = (t & k) == 0;
+                    const uint64_t a = sk[t], b = sk[o];
+                    if ((a > b) == up) {
+                        sk[t] = b;
+                        sk[o] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// CTA per large segment: bitonic sort in shared memory up to 8192 keys; above that, tiles of
+// 8192 sorted in shared memory, then pairwise merges of sorted runs between the segment and
+// tmp (each key's place: its index in its run plus its rank in the other run, by binary
+// search; keys of the left run go before equal keys of the right run).
 __global__ void k_sort_large(const uint32_t *__restrict__ large, const uint32_t *__restrict__ nlarge,
                              const uint32_t *__restrict__ cnt, const uint64_t *__restrict__ start,
                              uint64_t *__restrict__ grouped, uint64_t *__restrict__ tmp,
@@ -785,37 +807,45 @@ __global__ void k_sort_large(const uint32_t *__restrict__ large, const uint32_t 
             while (P < n) P <<= 1;
             for (uint32_t t = threadIdx.x; t < P; t += blockDim.x) sk[t] = t < n ? seg[t] : ~0ull;
             __syncthreads();
-            for (uint32_t k = 2; k <= P; k <<= 1) {
-                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                    for (uint32_t t = threadIdx.x; t < P; t += blockDim.x) {
-                        const uint32_t o = t ^ j;
-                        if (o > t) {
-                            const bool up = (t & k) == 0;
-                            const uint64_t a = sk[t], b = sk[o];
-                            if ((a > b) == up) {
-                                sk[t] = b;
-                                sk[o] = a;
-                            }
-                        }
-                    }
-                    __syncthreads();
-                }
-            }
+            cta_bitonic(sk, P);
             for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) seg[t] = sk[t];
             __syncthreads();
         } else {
-            uint64_t *tq = tmp + start[q];
-            for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
-                const uint64_t x = seg[t];
-                uint32_t r = 0;
-                for (uint32_t u = 0; u < n; ++u) {
-                    const uint64_t y = seg[u];
-                    r += (y < x) || (y == x && u < t);
-                }
-                tq[r] = x;
+            for (uint32_t base = 0; base < n; base += 8192) {
+                const uint32_t m = n - base < 8192 ? n - base : 8192;
+                for (uint32_t t = threadIdx.x; t < 8192; t += blockDim.x)
+                    sk[t] = t < m ? seg[base + t] : ~0ull;
+                __syncthreads();
+                cta_bitonic(sk, 8192);
+                for (uint32_t t = threadIdx.x; t < m; t += blockDim.x) seg[base + t] = sk[t];
+                __syncthreads();
             }
-            __syncthreads();
-            for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) seg[t] = tq[t];
+            uint64_t *src = seg, *dst = tmp + start[q];
+            for (uint32_t w = 8192; w < n; w <<= 1) {
+                for (uint32_t a0 = 0; a0 < n; a0 += 2 * w) {
+                    const uint32_t a1 = n - a0 > w ? a0 + w : n;
+                    const uint32_t b1 = n - a1 > w ? a1 + w : n;
+                    for (uint32_t x = a0 + threadIdx.x; x < b1; x += blockDim.x) {
+                        const uint64_t v = src[x];
+                        // rank of v in the other run: lower bound in the right run for a left
+                        // key, upper bound in the left run for a right key
+                        const bool left = x < a1;
+                        uint32_t lo = left ? a1 : a0, hi = left ? b1 : a1;
+                        while (lo < hi) {
+                            const uint32_t mid = (lo + hi) >> 1;
+                            const uint64_t u = src[mid];
+                            if (left ? (u < v) : (u <= v)) lo = mid + 1; else hi = mid;
+                        }
+                        dst[left ? x + (lo - a1) : a0 + (x - a1) + (lo - a0)] = v;
+                    }
+                }
+                __syncthreads();
+                uint64_t *t = src;
+                src = dst;
+                dst = t;
+            }
+            if (src != seg)
+                for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) seg[t] = src[t];
             __syncthreads();
         }
         // deduplicate the sorted segment in place, in tiles of blockDim keys

@@ -350,9 +350,10 @@ def fm_inexact(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int, max_ga
     if want_costs and costs.numel() < cap:
         raise ValueError("costs must hold pair capacity entries")
 
-    def call():
+    def call(with_stats=True):
         sp = fm_search_params(z, max_gaps, strands, kern,
-                              _dptr(stats, _U64, "stats") if stats is not None else None,
+                              _dptr(stats, _U64, "stats") if stats is not None and with_stats
+                              else None,
                               C.pointer(profile) if profile is not None else None,
                               _dptr(costs, _U8, "costs") if want_costs else None,
                               1 if best else 0, 0)
@@ -365,14 +366,12 @@ def fm_inexact(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int, max_ga
 
     rc, need = call()
     if rc == FM_ETRUNC and (want_costs or best):
-        # counts and offsets are complete; repeat with buffers of the needed size
+        # counts and offsets are complete and the truncated call already added its stats:
+        # repeat with buffers of the needed size, without stats
         pairs = torch.empty((max(need, 1), 2), dtype=torch.int32, device=dev)
         if want_costs:
             costs = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
-        if stats is not None:
-            raise FmError(FM_ETRUNC, "pair capacity below the intervals found (stats would "
-                                     "count the search twice)")
-        rc, need = call()
+        rc, need = call(with_stats=False)
     elif rc == FM_ETRUNC:
         pairs = torch.empty((max(need, 1), 2), dtype=torch.int32, device=dev)
         rc = lib.fm_inexact_fetch(h.ptr, _dptr(pairs, _U32, "pairs"), pairs.shape[0],

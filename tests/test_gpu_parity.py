@@ -385,6 +385,38 @@ def test_inexact_interval_table_depths(fm, depth):
     _inexact_case(fm, R, reads, 2, 1, 64, modes=("canonical",), kmers=(depth,))
 
 
+@pytest.mark.parametrize("z,gaps,n_reads,min_len,max_len", [(4, 2, 40, 6, 16), (5, 1, 40, 6, 16),
+                                                             (6, 2, 40, 6, 16), (7, 7, 6, 4, 8)])
+def test_inexact_high_differences(fm, z, gaps, n_reads, min_len, max_len):
+    """z up to 7 with up to 7 indel columns (the limits of the node's 4-bit fields): both
+    kernels against the oracle's canonical enumeration (the literal recursion explodes here),
+    results and node counts with one symbol per exact step, results with the defaults.  The
+    batches are small (millions of nodes per query at z = 7), and the pair buffer holds the
+    whole result, so no call is repeated."""
+    R = synth.repeat_text(81, 50_000, families=5, min_len=300, max_len=1500)
+    ix = oracle.Index(R, "sais")
+    reads = synth.sample_reads(82, R, n_reads, min_len, max_len, sub_rate=0.1, indel_rate=0.05,
+                               both_strands=True, random_frac=0.1)
+    want = ix.inexact(reads.codes, reads.offs, z, gaps, strands=2, canonical=True)
+    cap = int(want["offsets"][-1]) + 64
+    h = fm.fm_build(R)
+    codes, offs = fm.to_device_reads(reads)
+    for pairs in (2, 1):
+        fm.fm_set_tuning(h, pair_steps=pairs)
+        for kern in ("plain", "persistent"):
+            stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+            c, o, p, cs = fm.fm_inexact(h, codes, offs, z, gaps, strands=2, kernel=kern,
+                                        stats=stats, costs=True, pair_capacity=cap)
+            tag = (kern, pairs)
+            assert np.array_equal(_u32(c), want["counts"]), tag
+            assert np.array_equal(o.cpu().numpy().astype(np.uint64), want["offsets"]), tag
+            assert np.array_equal(_u32(p), want["pairs"]), tag
+            assert np.array_equal(cs.cpu().numpy(), want["costs"]), tag
+            if pairs == 2:
+                assert stats.cpu().numpy()[0] == want["nodes"].sum(), tag
+    h.close()
+
+
 @pytest.mark.parametrize("interval", [32, 128, 256])
 def test_inexact_intervals(fm, interval):
     R = synth.repeat_text(11, 200_000, families=20, min_len=300, max_len=3000)
