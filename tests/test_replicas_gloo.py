@@ -72,3 +72,4 @@ def test_single_process_defaults():
     assert replicas.max_over_ranks(3.0) == 3.0
     assert replicas.job_throughput(10, 2.0) == 5.0
     assert replicas.gather_counts(torch.tensor([1, 2]))[0].tolist() == [1, 2]
+
