@@ -336,11 +336,12 @@ typedef struct fm_tuning {
                                    (cudaLimitMaxL2FetchGranularity of its CUDA context, set at
                                    each compute call; it ends with the process) */
     uint32_t canonical;         /* 1 (default): the inexact search enumerates only canonical
-                                   alignments (an indel next to a mismatch, or inside a run of
-                                   one base, in one fixed order), so no reference string is
-                                   spelled twice by alignments of the same cost; the reported
-                                   intervals are those of Listing 2, the nodes fewer.  2: every
-                                   call of Listing 2 (stats then count its nodes exactly) */
+                                   alignments: an indel next to a mismatch, or inside a run of
+                                   one base, is taken in one fixed order or place, so the
+                                   alignments that differ only there are searched once; the
+                                   reported intervals are those of Listing 2, the nodes fewer.
+                                   2: every call of Listing 2 (with pair_steps = 2 as well,
+                                   stats count its nodes exactly) */
     uint32_t kmer_depth;        /* interval tables of short strings (Sec. 4.2 leaves the
                                    memory-bound search to better cache locality of the
                                    FM-index; this is one such method): for every string X of
