@@ -167,7 +167,8 @@ def repeat_text(seed: int, n: int, gc: float = 0.41, repeat_frac: float = 0.2,
 
     Each family has a consensus of uniform length in [min_len, max_len] and receives an equal
     expected share repeat_frac*n/families of repeat bases, i.e. round(share/len) copies (at
-    least one).  Every copy is substituted independently at ``divergence`` and reversed and
+    least one, so when the share is below the longer consensus lengths the copies cover more
+    than repeat_frac: 41% at n = 4e6 with 500 families, 20.0% at 6.4e7 and 2e9).  Every copy is substituted independently at ``divergence`` and reversed and
     complemented with probability ``rc_prob``.  The copies are shuffled and laid at
     non-overlapping uniform positions: sorted uniform offsets in [0, n - total] are shifted
     by the lengths of the copies before them.
