@@ -74,7 +74,7 @@ def _declare(lib):
     lib.or_interval_naive_batch.argtypes = [P, i64, P, P, i64, P, P, P, C.c_int]
     lib.or_dcalc.argtypes = [P, P, i64, P]
     lib.or_inexact_batch.argtypes = [P, P, P, i64, C.c_int, C.c_int, C.c_int, C.c_int,
-                                     C.c_int, C.c_int]
+                                     C.c_int, C.c_int, C.c_int]
     lib.or_inexact_batch.restype = C.POINTER(_Results)
     lib.or_results_free.argtypes = [C.POINTER(_Results)]
     lib.or_hamming_count.argtypes = [P, i64, P, i64, C.c_int]
@@ -257,17 +257,18 @@ class Index:
 
     def inexact(self, codes, offs, z: int, max_gaps: int = 0, strands: int = 1,
                 prune: bool = True, interval: int = 64, threads: int = 0,
-                canonical: bool = False):
+                canonical: bool = False, end_skip: int = 0):
         """Listing 2 result sets: dict with counts, offsets, pairs (total x 2), costs (per
         interval the fewest differences of the alignments reaching it), nodes, blocks.
         canonical: enumerate canonical alignments only (same results; nodes and blocks are
-        those of that enumeration)."""
+        those of that enumeration).  end_skip: indel columns only with at least that many
+        read symbols on each side (not with canonical)."""
         codes = _u8(codes)
         offs = np.ascontiguousarray(offs, dtype=np.uint32)
         nr = offs.size - 1
         res = self.lib.or_inexact_batch(self.h, _p(codes), _p(offs), nr, strands, z, max_gaps,
                                         (1 if prune else 0) | (2 if canonical else 0),
-                                        interval, threads)
+                                        interval, threads, end_skip)
         if not res:
             raise ValueError("or_inexact_batch")
         try:

@@ -574,7 +574,22 @@ typedef struct {
     pairvec *out;
     uint64_t nodes, blocks;
     int z0; /* the differences allowed at the top call; a result's cost is z0 - z */
+    int64_t m;        /* length of W */
+    int64_t end_skip; /* an indel column needs at least this many symbols of W on each side */
 } inex_ctx;
+
+/* End restriction on indel columns (an option in the manner of BWA, Li and Durbin 2009, which
+ * Listing 2 cites; not in the paper).  Reading: an indel column may be placed only where at
+ * least end_skip symbols of W lie on each side of it.  Inserting W[i] leaves W[0..i-1] (i
+ * symbols) on its left and W[i+1..m-1] (m-1-i) on its right; a deletion taken at position i
+ * sits between W[i] and W[i+1], with i+1 symbols on its left and m-1-i on its right. */
+static int ins_allowed(const inex_ctx *X, int64_t i) {
+    return i >= X->end_skip && X->m - 1 - i >= X->end_skip;
+}
+
+static int del_allowed(const inex_ctx *X, int64_t i) {
+    return i + 1 >= X->end_skip && X->m - 1 - i >= X->end_skip;
+}
 
 static void inex_recur(inex_ctx *X, int64_t i, int z, int gaps, int64_t k, int64_t l) {
     if (z < 0) return;
@@ -587,7 +602,7 @@ static void inex_recur(inex_ctx *X, int64_t i, int z, int gaps, int64_t k, int64
     X->blocks += (k / X->interval == (l + 1) / X->interval) ? 1 : 2;
     const or_index *ix = X->ix;
     /* insertion: W[i] aligned to no reference symbol */
-    if (gaps < X->max_gaps) inex_recur(X, i - 1, z - 1, gaps + 1, k, l);
+    if (gaps < X->max_gaps && ins_allowed(X, i)) inex_recur(X, i - 1, z - 1, gaps + 1, k, l);
     int64_t ok[4], ol[4];
     or_occ4(ix, k - 1, ok);
     or_occ4(ix, l, ol);
@@ -596,7 +611,7 @@ static void inex_recur(inex_ctx *X, int64_t i, int z, int gaps, int64_t k, int64
         int64_t l2 = ix->C[b] + ol[b];
         if (k2 <= l2) {
             /* deletion: reference symbol b aligned to no read symbol */
-            if (gaps < X->max_gaps) inex_recur(X, i, z - 1, gaps + 1, k2, l2);
+            if (gaps < X->max_gaps && del_allowed(X, i)) inex_recur(X, i, z - 1, gaps + 1, k2, l2);
             if (b == X->W[i])
                 inex_recur(X, i - 1, z, gaps, k2, l2);
             else
@@ -615,7 +630,8 @@ static void inex_recur(inex_ctx *X, int64_t i, int z, int gaps, int64_t k, int64
  * Each skipped pair spells the same reference string as a canonical pair of no higher cost,
  * so the reported intervals are unchanged.  A call counts as a node only when one of its
  * Occ children (deletion, mismatch, match) is allowed by these rules and by z; a call with
- * none passes through to its insertion child alone. */
+ * none passes through to its insertion child alone.  The rewrites move indel columns, so
+ * they do not hold under an end restriction: the two are not combined. */
 static void inex_canon(inex_ctx *X, int64_t i, int z, int gaps, int64_t k, int64_t l, int last,
                        int lb) {
     if (z < 0 || (X->prune && i >= 0 && z < X->D[i])) return;
@@ -676,7 +692,7 @@ typedef struct {
     const or_index *ix;
     const uint8_t *codes;
     const uint32_t *offs;
-    int strands, z, max_gaps, prune, interval;
+    int strands, z, max_gaps, prune, interval, end_skip;
     pairvec *per_query;
     uint64_t *nodes, *blocks;
 } inex_job;
@@ -694,7 +710,8 @@ static void inex_one(void *a, int64_t q, int tid) {
         W[i] = strand ? (uint8_t)(3 - J->codes[s + m - 1 - i]) : J->codes[s + i];
     or_dcalc(J->ix, W, m, D);
     pairvec v = {NULL, 0, 0};
-    inex_ctx X = {J->ix, W, D, J->max_gaps, J->prune & 1, J->interval, &v, 0, 0, J->z};
+    inex_ctx X = {J->ix, W, D, J->max_gaps, J->prune & 1, J->interval, &v, 0, 0, J->z, m,
+                  J->end_skip};
     if (J->prune & 2)
         inex_canon(&X, m - 1, J->z, 0, 0, J->ix->n, 0, 0);
     else
@@ -722,8 +739,9 @@ static void inex_one(void *a, int64_t q, int tid) {
 
 or_results *or_inexact_batch(const or_index *ix, const uint8_t *codes, const uint32_t *offs,
                              int64_t nreads, int strands, int z, int max_gaps, int prune,
-                             int interval, int threads) {
+                             int interval, int threads, int end_skip) {
     if (strands != 1 && strands != 2) return NULL;
+    if (end_skip < 0 || (end_skip > 0 && (prune & 2))) return NULL;
     if (interval <= 0) interval = 64;
     int64_t nq = nreads * strands;
     or_results *res = (or_results *)calloc(1, sizeof(or_results));
@@ -733,8 +751,8 @@ or_results *or_inexact_batch(const or_index *ix, const uint8_t *codes, const uin
     res->nodes = (uint64_t *)calloc((size_t)(nq > 0 ? nq : 1), sizeof(uint64_t));
     res->blocks = (uint64_t *)calloc((size_t)(nq > 0 ? nq : 1), sizeof(uint64_t));
     pairvec *pq = (pairvec *)calloc((size_t)(nq > 0 ? nq : 1), sizeof(pairvec));
-    inex_job J = {ix, codes, offs, strands, z, max_gaps, prune, interval, pq, res->nodes,
-                  res->blocks};
+    inex_job J = {ix, codes, offs, strands, z, max_gaps, prune, interval, end_skip, pq,
+                  res->nodes, res->blocks};
     run_parallel(inex_one, &J, nq, 16, threads);
     uint64_t total = 0;
     for (int64_t q = 0; q < nq; ++q) {

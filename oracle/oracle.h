@@ -104,7 +104,11 @@ void or_dcalc(const or_index *ix, const uint8_t *W, int64_t m, uint8_t *D);
  *   - with prune & 2 the search enumerates canonical alignments only (test instrumentation,
  *     not in the paper; oracle.c states the rules): same results, fewer nodes;
  *   - a call with i < 0 and z >= 0 reports {k, l} unless k = 0 (no reference symbol used);
- *   - the top call is InexRecur(W, m-1, z, 0, n).
+ *   - the top call is InexRecur(W, m-1, z, 0, n);
+ *   - end_skip > 0 (an option after BWA, not in the paper): an indel column only where at
+ *     least end_skip symbols of W lie on each side of it, i.e. inserting W[i] needs
+ *     end_skip <= i <= m-1-end_skip, and a deletion between W[i] and W[i+1] needs
+ *     end_skip - 1 <= i <= m-1-end_skip.  Not combined with prune & 2 (NULL).
  * Query q = r*strands + s searches read r (s = 0) or its reverse complement (s = 1).
  * Results per query are distinct intervals sorted by (k, l).  nodes counts calls that reach
  * the Occ loop (i >= 0 after the tests); blocks counts, per such call, the checkpoint blocks
@@ -123,7 +127,7 @@ typedef struct or_results {
 
 or_results *or_inexact_batch(const or_index *ix, const uint8_t *codes, const uint32_t *offs,
                              int64_t nreads, int strands, int z, int max_gaps, int prune,
-                             int interval, int threads);
+                             int interval, int threads, int end_skip);
 void or_results_free(or_results *res);
 
 /* Textbook sliding window: #{p in [0, n-m] : Hamming(W, R[p..p+m-1]) <= z}. */

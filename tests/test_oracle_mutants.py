@@ -42,13 +42,13 @@ MUTANTS = [
      "            else\n                inex_recur(X, i - 1, z - 1, gaps, k2, l2);",
      "            else\n                inex_recur(X, i - 1, z, gaps, k2, l2);"),
     ("deletion consumes a read symbol",
-     "if (gaps < X->max_gaps) inex_recur(X, i, z - 1, gaps + 1, k2, l2);",
-     "if (gaps < X->max_gaps) inex_recur(X, i - 1, z - 1, gaps + 1, k2, l2);"),
+     "del_allowed(X, i)) inex_recur(X, i, z - 1, gaps + 1, k2, l2);",
+     "del_allowed(X, i)) inex_recur(X, i - 1, z - 1, gaps + 1, k2, l2);"),
     ("insertion moves the interval",
-     "if (gaps < X->max_gaps) inex_recur(X, i - 1, z - 1, gaps + 1, k, l);",
-     "if (gaps < X->max_gaps) inex_recur(X, i - 1, z - 1, gaps + 1, k + 1, l);"),
-    ("gap cap off by one", "if (gaps < X->max_gaps) inex_recur(X, i, z - 1,",
-     "if (gaps <= X->max_gaps) inex_recur(X, i, z - 1,"),
+     "ins_allowed(X, i)) inex_recur(X, i - 1, z - 1, gaps + 1, k, l);",
+     "ins_allowed(X, i)) inex_recur(X, i - 1, z - 1, gaps + 1, k + 1, l);"),
+    ("gap cap off by one", "if (gaps < X->max_gaps && del_allowed(X, i)) inex_recur(X, i, z - 1,",
+     "if (gaps <= X->max_gaps && del_allowed(X, i)) inex_recur(X, i, z - 1,"),
     ("empty-interval children kept", "        if (k2 <= l2) {\n            /* deletion",
      "        if (k2 <= l2 + 1) {\n            /* deletion"),
     ("prune too eagerly", "if (X->prune && i >= 0 && z < X->D[i]) return;",
@@ -86,6 +86,15 @@ MUTANTS = [
      "        if (W[i] == lb) may_ins = 0;", "        may_ins = 0;"),
     ("canonical: pass-through call counted as a node",
      "    if (!may_del && !may_mis && !may_match) return;\n", ""),
+    ("end restriction: insertion bound shifted",
+     "    return i >= X->end_skip && X->m - 1 - i >= X->end_skip;",
+     "    return i > X->end_skip && X->m - 1 - i >= X->end_skip;"),
+    ("end restriction: deletion treated like an insertion",
+     "    return i + 1 >= X->end_skip && X->m - 1 - i >= X->end_skip;",
+     "    return i >= X->end_skip && X->m - 1 - i >= X->end_skip;"),
+    ("end restriction: deletion counted from the wrong side",
+     "    return i + 1 >= X->end_skip && X->m - 1 - i >= X->end_skip;",
+     "    return i + 1 >= X->end_skip && X->m - i >= X->end_skip;"),
 ]
 
 

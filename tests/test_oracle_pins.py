@@ -343,7 +343,7 @@ def canonical_pair_ok(prev, col, i, w):
     return True
 
 
-def brute_inexact(text, w, z, gaps, prune=False, interval=4, canonical=False):
+def brute_inexact(text, w, z, gaps, prune=False, interval=4, canonical=False, end_skip=0):
     """Enumerate every alignment column script of Listing 2's grammar (processing w from its
     right end): insertion (consume w[i]), deletion (emit a reference symbol, i unchanged),
     match/mismatch (emit b, consume w[i]); cost <= z, indel columns <= gaps; stop at i < 0.
@@ -353,10 +353,19 @@ def brute_inexact(text, w, z, gaps, prune=False, interval=4, canonical=False):
     width at rank positions k and l+1.  canonical: only scripts whose adjacent columns pass
     canonical_pair_ok; a state counts only when a deletion (needs a gap and a difference
     left), a mismatch (needs a difference left) or the match may follow it.  The fourth value
-    maps each interval to the fewest differences of the scripts that reach it."""
+    maps each interval to the fewest differences of the scripts that reach it.  end_skip: an
+    insertion of w[i] needs end_skip <= i <= m-1-end_skip, a deletion taken at i (between
+    w[i] and w[i+1]) needs end_skip <= i+1 and i <= m-1-end_skip."""
     strings = {}
     D = brute_D(text, w)
     stats = [0, 0]
+    m = len(w)
+
+    def ins_ok(i):
+        return end_skip <= i <= m - 1 - end_skip
+
+    def del_ok(i):
+        return end_skip <= i + 1 and i <= m - 1 - end_skip
 
     def ok(prev, col, i):
         return not canonical or canonical_pair_ok(prev, col, i, w)
@@ -372,9 +381,9 @@ def brute_inexact(text, w, z, gaps, prune=False, interval=4, canonical=False):
             if x:
                 strings[x] = min(strings.get(x, 99), z - zl)
             return
-        if g < gaps and ok(prev, ("I",), i):
+        if g < gaps and ins_ok(i) and ok(prev, ("I",), i):
             rec(i - 1, zl - 1, g + 1, x, ("I",))
-        occ_child = any((col[0] == "D" and g < gaps and zl >= 1) or
+        occ_child = any((col[0] == "D" and g < gaps and zl >= 1 and del_ok(i)) or
                         (col[0] == "M" and (col[1] == w[i] or zl >= 1))
                         for col in [("D", b) for b in SYM] + [("M", b) for b in SYM]
                         if ok(prev, col, i))
@@ -384,7 +393,7 @@ def brute_inexact(text, w, z, gaps, prune=False, interval=4, canonical=False):
         stats[0] += 1
         stats[1] += 1 if k // interval == (l + 1) // interval else 2
         for b in SYM:
-            if g < gaps and ok(prev, ("D", b), i):
+            if g < gaps and del_ok(i) and ok(prev, ("D", b), i):
                 rec(i, zl - 1, g + 1, b + x, ("D", b))
             if ok(prev, ("M", b), i):
                 rec(i - 1, zl - (b != w[i]), g, b + x, ("M", b))
@@ -454,6 +463,131 @@ def test_inexact_bruteforce_tiny():
                     cases += 1
                 assert np.array_equal(res_c["costs"], res["costs"])
     assert cases > 500
+
+
+def min_script_cost(w, x, gaps, end_skip):
+    """The fewest differences of a column script that aligns all of w to all of x, read left to
+    right: a match or mismatch column takes one symbol of each, an insertion one symbol of w,
+    a deletion one symbol of x; at most `gaps` indel columns; a deletion has at least one
+    symbol of w on its left (Listing 2 places nothing before w[0]); every indel column has at
+    least end_skip symbols of w on each side.  None when no script exists.  A dynamic program
+    over (symbols of w used, symbols of x used, indel columns used): an independent statement
+    of the set Listing 2 reaches, since a string's suffixes occur wherever it occurs."""
+    m, n = len(w), len(x)
+    INF = 1 << 20
+    f = [[[INF] * (gaps + 1) for _ in range(n + 1)] for _ in range(m + 1)]
+    f[0][0][0] = 0
+    for i in range(m + 1):
+        for j in range(n + 1):
+            for g in range(gaps + 1):
+                v = f[i][j][g]
+                if v >= INF:
+                    continue
+                if i < m and j < n:
+                    c = v + (w[i] != x[j])
+                    f[i + 1][j + 1][g] = min(f[i + 1][j + 1][g], c)
+                if g < gaps and i < m and end_skip <= i <= m - 1 - end_skip:
+                    f[i + 1][j][g + 1] = min(f[i + 1][j][g + 1], v + 1)
+                if g < gaps and j < n and i >= max(1, end_skip) and m - i >= end_skip:
+                    f[i][j + 1][g + 1] = min(f[i][j + 1][g + 1], v + 1)
+    best = min(f[m][n][g] for g in range(gaps + 1))
+    return None if best >= INF else best
+
+
+def defined_inexact(text, w, z, gaps, end_skip):
+    """Interval -> fewest differences over the non-empty strings x of text that some script of
+    at most z differences aligns w to (min_script_cost), by enumerating the substrings."""
+    out = {}
+    subs = {text[p:p + t] for t in range(1, len(w) + gaps + 1) for p in range(len(text) - t + 1)}
+    for x in subs:
+        c = min_script_cost(w, x, gaps, end_skip)
+        if c is not None and c <= z:
+            k, l = brute_interval(text, x)
+            out[(k, l)] = min(out.get((k, l), 99), c)
+    return out
+
+
+def test_end_restriction_bruteforce_and_definition():
+    """Indel columns only with at least end_skip read symbols on each side: the oracle's sets,
+    costs, node and block counts equal the brute-force scripts', and its sets and costs equal
+    the alignment definition (which also pins end_skip = 0, plain Listing 2, a second way)."""
+    rng = np.random.default_rng(33)
+    cases = 0
+    for _ in range(14):
+        n = int(rng.integers(8, 40))
+        R = synth.uniform_text(int(rng.integers(1 << 30)), n)
+        text = "".join(SYM[c] for c in R)
+        ix = oracle.Index(R, "naive")
+        ws = []
+        for _ in range(4):
+            m = int(rng.integers(1, 9))
+            if rng.random() < 0.7 and n > m + 1:
+                p = int(rng.integers(0, n - m - 1))
+                W = R[p:p + m].copy()
+                u = rng.random()
+                if u < 0.3:
+                    W[rng.integers(0, m)] = rng.integers(0, 4)
+                elif u < 0.6 and m > 1:     # one symbol dropped: an insertion in R's terms
+                    W = np.delete(R[p:p + m + 1], rng.integers(1, m))
+                elif u < 0.9 and m > 1:
+                    W = np.delete(W, rng.integers(0, m))
+            else:
+                W = rng.integers(0, 4, m).astype(np.uint8)
+            ws.append(W.astype(np.uint8))
+        codes = np.concatenate(ws).astype(np.uint8)
+        offs = np.concatenate([[0], np.cumsum([w.size for w in ws])]).astype(np.uint32)
+        for z in (1, 2):
+            for gaps in (1, 2):
+                for e in (0, 1, 2, 3):
+                    res = ix.inexact(codes, offs, z, gaps, strands=1, interval=4, end_skip=e)
+                    res_np = ix.inexact(codes, offs, z, gaps, strands=1, interval=4,
+                                        end_skip=e, prune=False)
+                    o = res["offsets"]
+                    for q, W in enumerate(ws):
+                        w = "".join(SYM[c] for c in W)
+                        got = _pairs_of(res, q)
+                        costs = [int(c) for c in res["costs"][o[q]:o[q + 1]]]
+                        assert got == _pairs_of(res_np, q)
+                        want, nodes, blocks, cost = brute_inexact(text, w, z, gaps, prune=True,
+                                                                  end_skip=e)
+                        assert got == want and costs == [cost[p] for p in want], (text, w, z, e)
+                        assert (int(res["nodes"][q]), int(res["blocks"][q])) == (nodes, blocks)
+                        d = defined_inexact(text, w, z, gaps, e)
+                        assert got == sorted(d) and costs == [d[p] for p in got], (text, w, z, e)
+                        cases += 1
+    assert cases > 400
+
+
+def test_end_restriction_invariants():
+    """end_skip = 0 is the unrestricted search; a larger end_skip reports a subset with no
+    lower costs; above half the read length no indel fits, which is the mismatch-only search
+    (same sets, costs and nodes); the canonical rewrites are not combined with it."""
+    R = synth.repeat_text(5, 30_000, families=8, min_len=100, max_len=600)
+    reads = synth.sample_reads(6, R, 120, 10, 40, sub_rate=0.02, indel_rate=0.02,
+                               both_strands=True)
+    ix = oracle.Index(R, "sais")
+    base = ix.inexact(reads.codes, reads.offs, 2, 1, strands=2)
+    e0 = ix.inexact(reads.codes, reads.offs, 2, 1, strands=2, end_skip=0)
+    for key in ("counts", "offsets", "pairs", "costs", "nodes", "blocks"):
+        assert np.array_equal(base[key], e0[key])
+    prev = base
+    for e in (1, 3, 8):
+        cur = ix.inexact(reads.codes, reads.offs, 2, 1, strands=2, end_skip=e)
+        for q in range(cur["counts"].size):
+            a, b = prev["offsets"][q:q + 2], cur["offsets"][q:q + 2]
+            old = {tuple(map(int, p)): int(c) for p, c in
+                   zip(prev["pairs"][a[0]:a[1]], prev["costs"][a[0]:a[1]])}
+            for p, c in zip(cur["pairs"][b[0]:b[1]], cur["costs"][b[0]:b[1]]):
+                assert tuple(map(int, p)) in old and int(c) >= old[tuple(map(int, p))]
+        assert cur["nodes"].sum() <= prev["nodes"].sum()
+        prev = cur
+    assert prev["counts"].sum() < base["counts"].sum()
+    none = ix.inexact(reads.codes, reads.offs, 2, 1, strands=2, end_skip=21)
+    mis = ix.inexact(reads.codes, reads.offs, 2, 0, strands=2)
+    for key in ("counts", "offsets", "pairs", "costs", "nodes", "blocks"):
+        assert np.array_equal(none[key], mis[key]), key
+    with pytest.raises(ValueError):
+        ix.inexact(reads.codes, reads.offs, 2, 1, strands=2, end_skip=2, canonical=True)
 
 
 def _runs_text(rng, n):
