@@ -7,12 +7,18 @@ indels, drawn from both strands) against a 2,000,000,000-base repeat-structured 
 z = 2 differences with at most 1 gap, each read searched on both strands.  Metric: reads/s.
 Beside it, in the same line:
   * the plain per-read kernel on the same batch (bit-exact comparison of the two);
+  * best_hits: the same batch with per-interval minimum costs, keeping each query's best;
+  * end_restricted: the same batch with indel columns kept 5 read symbols from either end;
   * e2e: the same step through the C ABI with the reads in pinned host memory, the
     host->device copy of the reads and the device->host copy of the interval sets timed;
+  * serving: mixed-mode requests on the resident index, offline and under Poisson arrivals;
+  * locate: SA positions of 2^24 random rows (Eq. 4-5);
   * occ8: the Occ micro-benchmark, 2^28 eight-Occ queries on a 2 Gbp i.i.d. 41% GC index
     (half in one checkpoint block, half at a geometric gap of mean 1000), against the
     random-gather roofline;
   * exact: plain exact search of 10,000 32 bp reads on a 1 Mbp uniform reference;
+  * both_strands_256mbp: two queries per read on R against one on R . revcomp(R);
+  * inexact_64mbp: 10^6 100 bp reads, z = 2 mismatches, on a 64 Mbp repeat reference;
   * cpu_baseline: the CPU oracle on a bounded sample of the main workload.
 With --impl reference the CPU oracle itself is timed on a bounded sample per step.
 Launch: python bench.py [--gpus N --steps K --warmup W]; under torchrun one replica per GPU,
@@ -66,6 +72,10 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-best", action="store_true")
     ap.add_argument("--skip-both", action="store_true")
+    ap.add_argument("--skip-end", action="store_true")
+    ap.add_argument("--end-skip", type=int, default=5,
+                    help="end restriction of the end_restricted line: indel columns only with at "
+                         "least this many read symbols on each side")
     ap.add_argument("--skip-cfg3", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
@@ -386,6 +396,34 @@ def main():
                 "all_intervals": int(ref_offsets[-1].item()),
                 "cost_histogram": np.bincount(cvals, minlength=3).tolist()}
 
+    # ---- end restriction on indel columns, same batch --------------------------------------
+    endr = None
+    if not args.skip_end:
+        end_pairs = torch.empty((pairs_cap, 2), dtype=torch.int32, device=dev)
+        est = torch.zeros(4, dtype=torch.int64, device=dev)
+
+        def search_end(st=None):
+            return fmocc.fm_inexact(h, codes, offs, 2, 1, strands=2, counts=counts,
+                                    offsets=offsets, pairs=end_pairs, end_skip=args.end_skip,
+                                    stats=st, profile=prof)
+        search_end()
+        barrier()
+        flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        _, oe, _ = search_end(est)
+        b.record()
+        torch.cuda.synchronize()
+        ems = max_over_ranks(a.elapsed_time(b) / 1000.0)
+        endr = {"value": args.reads * world / ems, "unit": "reads/s", "ms_per_step": 1000 * ems,
+                "steps": 1, "end_skip": args.end_skip, "kernel_ms": prof.ms_search,
+                "what": "indel columns only where at least end_skip read symbols lie on each "
+                        "side; every alignment of Listing 2 is enumerated (the canonical "
+                        "rewrites move indels across that boundary)",
+                "intervals": int(oe[-1].item()), "all_intervals": int(ref_offsets[-1].item()),
+                "nodes": int(est[0].item()), "nodes_unrestricted": int(nodes_per_step)}
+        del end_pairs
+
     # ---- e2e through the C ABI with host buffers ----------------------------------------
     e2e = None
     if not args.skip_e2e:
@@ -480,6 +518,7 @@ def main():
                    "profile_last": prof.as_dict()},
         "plain": plain,
         "best_hits": best,
+        "end_restricted": endr,
         "e2e": e2e,
         "occ8": occ8,
         "exact": exact,

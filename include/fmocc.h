@@ -182,7 +182,13 @@ typedef struct fm_search_params {
                           the alignments of Listing 2 that reach it; written beside pairs */
     uint32_t best;     /* 1: report, per query, only the intervals of its minimum cost (the
                           best hits); counts and offsets then describe those.  0: all */
-    uint32_t reserved; /* must be 0 */
+    uint32_t indel_end_skip; /* 0: indel columns anywhere Listing 2 allows them.  e > 0 (an option
+                          in the manner of BWA, Li and Durbin 2009; not in the paper): an indel
+                          column only where at least e symbols of the query lie on each side of
+                          it, i.e. inserting W[i] needs e <= i <= m-1-e and a deletion between
+                          W[i] and W[i+1] needs e-1 <= i <= m-1-e.  Costs and best hits follow
+                          the restricted set.  The search then enumerates every alignment of
+                          Listing 2 (fm_tuning.canonical does not apply).  At most 255. */
     /* With costs or best set, FM_ETRUNC leaves counts and offsets complete and the call must
      * be repeated with a larger pairs (and costs) buffer: fm_inexact_fetch does not apply.
      * fm_inexact_noalloc and the serving calls accept neither (FM_EINVAL). */

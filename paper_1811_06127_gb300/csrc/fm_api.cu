@@ -483,7 +483,8 @@ int fm_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t
     if (sp->max_gaps > (uint32_t)kMaxGaps) return set_error(h, FM_EINVAL, "max_gaps must be at most 7");
     if (sp->strands != 1 && sp->strands != 2) return set_error(h, FM_EINVAL, "strands must be 1 or 2");
     if (sp->kernel > FM_KERNEL_PERSISTENT) return set_error(h, FM_EINVAL, "unknown kernel");
-    if (sp->best > 1 || sp->reserved) return set_error(h, FM_EINVAL, "best must be 0 or 1, reserved 0");
+    if (sp->best > 1) return set_error(h, FM_EINVAL, "best must be 0 or 1");
+    if (sp->indel_end_skip > 255) return set_error(h, FM_EINVAL, "indel_end_skip must be at most 255");
     if (!offsets || (n_reads && (!reads || !offs || !counts))) return set_error(h, FM_EINVAL, "null buffer");
     if (pair_capacity && !pairs) return set_error(h, FM_EINVAL, "pairs is NULL");
     DeviceGuard g(h->device);

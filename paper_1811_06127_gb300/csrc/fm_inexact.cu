@@ -8,6 +8,9 @@
 //   deletion   (i,   z-1, g+1, k'_b, l'_b)      for each b with k'_b <= l'_b, z >= 1, g < max_gaps
 //   match      (i-1, z,   g,   k'_b, l'_b)      for b = W[i], k'_b <= l'_b
 //   mismatch   (i-1, z-1, g,   k'_b, l'_b)      for b != W[i], k'_b <= l'_b, z >= 1
+// and, with an end restriction e > 0 (an option after BWA, not in the paper), an indel column
+// only where at least e read symbols lie on each side of it: an insertion of W[i] when
+// e <= i <= m-1-e, a deletion at i (between W[i] and W[i+1]) when e-1 <= i <= m-1-e.
 // with k'_b = C[b] + rank(b, k) + 1 and l'_b = C[b] + rank(b, l+1) computed from the node's
 // own interval.  A child at position i' >= 0 survives only when its z' >= D(i'); a child at
 // i' = -1 is a leaf: its interval is a result unless k = 0 (no reference symbol read).
@@ -47,7 +50,14 @@ struct SearchCfg {
     unsigned long long *stats;   // nodes, blocks, raw
     uint32_t *err;
     uint32_t canon;              // enumerate canonical alignments only (see expand)
+    uint32_t end_skip;           // indel columns need this many read symbols on each side
 };
+
+// The canonical rewrites move indel columns across read positions, so under an end
+// restriction the search enumerates every alignment of Listing 2 instead.
+inline uint32_t search_canon(const Tuning &tu, const fm_search_params *sp) {
+    return sp->indel_end_skip ? 0u : tu.canon;
+}
 
 __device__ __forceinline__ uint32_t d_at(const uint4 &mt, int i) {
     if (i < 0) return 0u;
@@ -100,7 +110,8 @@ __device__ __forceinline__ unsigned long long step_cost(uint32_t nb) {
 //   mismatch b at W[i+1], then insertion of W[i] = b   (insertion, then match: one less)
 //   mismatch at W[i+1], then deletion of b = W[i+1]    (deletion, then match: one less)
 // A node none of whose Occ children is allowed takes no Occ step and is not counted; a child
-// that could take no step at all is not created.
+// that could take no step at all is not created.  The rewrites move indel columns, so they
+// are not applied together with an end restriction (the host clears canon).
 template <int I>
 __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, const uint4 &mt,
                                        uint32_t k2[4], uint32_t l2[4], uint32_t &push,
@@ -135,6 +146,11 @@ __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, cons
             }
         }
         if (i >= 1) wp = w_at(c.reads, mt, (uint32_t)i - 1u);
+    }
+    if (c.end_skip) {
+        const uint32_t m = mt.w & 255u, e = c.end_skip;
+        if ((uint32_t)i < e || (uint32_t)i + e >= m) ins_r = false;
+        if ((uint32_t)i + 1u < e || (uint32_t)i + e >= m) del_r = false;
     }
     const bool gap_ok = z >= 1u && g < c.max_gaps;
     const bool need = (gap_ok && del_r) || (z >= 1u && mis_r) || match_r;
@@ -1274,7 +1290,8 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
     key.pair_capacity = pair_capacity; key.raw_cap = raw_cap; key.n_reads = n_reads;
     key.strands = sp->strands; key.z = sp->z; key.max_gaps = sp->max_gaps; key.interval = I;
     key.grid = (uint32_t)grid; key.block = (uint32_t)block; key.chunk = tu.chunk;
-    key.spill_cap = spill_cap; key.profile = prof ? 1u : 0u; key.canon = tu.canon;
+    key.spill_cap = spill_cap; key.profile = prof ? 1u : 0u; key.canon = search_canon(tu, sp);
+    key.end_skip = sp->indel_end_skip;
     key.kt = h->d_kt; key.kdepth = h->kt_depth | (view_fwd(h).pairs << 16);
 
     char *misc = (char *)h->s_misc.ptr;
@@ -1325,7 +1342,8 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
             c.raw_cap = raw_cap;
             c.stats = d_stats;
             c.err = h->d_err + kErrSearch;
-            c.canon = tu.canon;
+            c.canon = search_canon(tu, sp);
+            c.end_skip = sp->indel_end_skip;
             switch (I) {
                 case 32: crc = launch_search<32>(h, c, FM_KERNEL_PERSISTENT, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, nullptr, 0, 0, cs); break;
                 case 64: crc = launch_search<64>(h, c, FM_KERNEL_PERSISTENT, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, nullptr, 0, 0, cs); break;
@@ -1527,7 +1545,8 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
         c.raw_cap = raw_cap;
         c.stats = d_stats;
         c.err = h->d_err + kErrSearch;
-        c.canon = tu.canon;
+        c.canon = search_canon(tu, sp);
+        c.end_skip = sp->indel_end_skip;
         if (prof) FM_CUDA_TRY(h, cudaEventRecord(ev[1], st));
         switch (I) {
             case 32: rc = launch_search<32>(h, c, sp->kernel, (uint4 *)h->s_spill.ptr, spill_cap, grid, block, stk, (uint4 *)h->s_plain.ptr, cap, T, st); break;
@@ -1805,7 +1824,8 @@ int run_inexact_noalloc(fm_index *h, const uint8_t *reads, const uint32_t *offs,
     c.raw_cap = kNoAllocMaxRaw;
     c.stats = d_stats;
     c.err = h->d_err + kErrSearch;
-    c.canon = h->tune.canon;
+    c.canon = search_canon(h->tune, sp);
+    c.end_skip = sp->indel_end_skip;
     switch (h->interval) {
         case 32: rc = noalloc_launch<32>(h, c, stacks, st); break;
         case 64: rc = noalloc_launch<64>(h, c, stacks, st); break;
@@ -1889,6 +1909,7 @@ extern "C" int fm_inexact_noalloc(fm_index *h, const uint8_t *reads, const uint3
     if (sp->z > (uint32_t)kMaxZ) return set_error(h, FM_EINVAL, "z must be at most 7");
     if (sp->max_gaps > (uint32_t)kMaxGaps) return set_error(h, FM_EINVAL, "max_gaps must be at most 7");
     if (sp->strands != 1 && sp->strands != 2) return set_error(h, FM_EINVAL, "strands must be 1 or 2");
+    if (sp->indel_end_skip > 255) return set_error(h, FM_EINVAL, "indel_end_skip must be at most 255");
     if (!offsets || (n_reads && (!reads || !offs || !counts))) return set_error(h, FM_EINVAL, "null buffer");
     if (pair_capacity && !pairs) return set_error(h, FM_EINVAL, "pairs is NULL");
     int prev = -1;

@@ -73,7 +73,7 @@ struct GraphKey {
     const void *qmeta, *raw, *spill, *group, *misc, *kt;
     uint64_t pair_capacity, raw_cap;
     uint32_t n_reads, strands, z, max_gaps, interval, grid, block, chunk, spill_cap, profile, canon,
-        kdepth;
+        kdepth, end_skip;
     bool operator==(const GraphKey &o) const {
         return reads == o.reads && offs == o.offs && counts == o.counts && offsets == o.offsets &&
                pairs == o.pairs && stats == o.stats && qmeta == o.qmeta && raw == o.raw &&
@@ -82,7 +82,7 @@ struct GraphKey {
                strands == o.strands && z == o.z && max_gaps == o.max_gaps &&
                interval == o.interval && grid == o.grid && block == o.block && chunk == o.chunk &&
                spill_cap == o.spill_cap && profile == o.profile && canon == o.canon && kt == o.kt &&
-               kdepth == o.kdepth;
+               kdepth == o.kdepth && end_skip == o.end_skip;
     }
 };
 

@@ -57,7 +57,7 @@ class fm_search_params(C.Structure):
     _fields_ = [("z", C.c_uint32), ("max_gaps", C.c_uint32), ("strands", C.c_uint32),
                 ("kernel", C.c_uint32), ("stats", C.c_void_p),
                 ("profile", C.POINTER(fm_profile)), ("costs", C.c_void_p),
-                ("best", C.c_uint32), ("reserved", C.c_uint32)]
+                ("best", C.c_uint32), ("indel_end_skip", C.c_uint32)]
 
 
 class fm_tuning(C.Structure):
@@ -325,11 +325,13 @@ def fm_dcalc(h: Index, reads: torch.Tensor, offs: torch.Tensor, strands: int = 1
 def fm_inexact(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int, max_gaps: int = 0,
                strands: int = 1, kernel="auto", stats: torch.Tensor | None = None,
                pair_capacity: int | None = None, counts=None, offsets=None, pairs=None,
-               profile: fm_profile | None = None, stream=None, costs=False, best=False):
+               profile: fm_profile | None = None, stream=None, costs=False, best=False,
+               end_skip: int = 0):
     """Listing 2 interval sets.  Returns (counts int32[nq], offsets int64[nq+1],
     pairs int32[total, 2]), plus costs uint8[total] (per interval the fewest differences) when
     ``costs`` is True or a uint8 tensor; ``best`` keeps only each query's minimum-cost
-    intervals.  On FM_ETRUNC the pairs buffer is regrown and fetched again (or, with costs or
+    intervals; ``end_skip`` > 0 places indel columns only where at least that many query
+    symbols lie on each side of them.  On FM_ETRUNC the pairs buffer is regrown and fetched again (or, with costs or
     best, the call is repeated with larger buffers)."""
     lib = load_library()
     nr = offs.numel() - 1
@@ -356,7 +358,7 @@ def fm_inexact(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int, max_ga
                               else None,
                               C.pointer(profile) if profile is not None else None,
                               _dptr(costs, _U8, "costs") if want_costs else None,
-                              1 if best else 0, 0)
+                              1 if best else 0, end_skip)
         need = C.c_uint64(0)
         rc = lib.fm_inexact(h.ptr, _dptr(reads, _U8, "reads"), _dptr(offs, _U32, "offs"), nr,
                             C.byref(sp), _dptr(counts, _U32, "counts"),
@@ -384,7 +386,7 @@ def fm_inexact(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int, max_ga
 
 def fm_inexact_noalloc(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int,
                        max_gaps: int = 0, strands: int = 1, counts=None, offsets=None,
-                       pairs=None, stream=None):
+                       pairs=None, stream=None, end_skip: int = 0):
     """fm_inexact without device allocation inside the library (fixed static scratch; at most
     32,768 queries per call).  The caller provides (or this wrapper allocates through torch,
     before the call) the output buffers.  Returns (counts, offsets, pairs, status); status is
@@ -399,7 +401,8 @@ def fm_inexact_noalloc(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int
         offsets = torch.empty(nq + 1, dtype=torch.int64, device=dev)
     if pairs is None:
         pairs = torch.empty((4 * nq + 1024, 2), dtype=torch.int32, device=dev)
-    sp = fm_search_params(z, max_gaps, strands, FM_KERNEL_PERSISTENT, None, None, None, 0, 0)
+    sp = fm_search_params(z, max_gaps, strands, FM_KERNEL_PERSISTENT, None, None, None, 0,
+                          end_skip)
     need = C.c_uint64(0)
     rc = lib.fm_inexact_noalloc(h.ptr, _dptr(reads, _U8, "reads"), _dptr(offs, _U32, "offs"), nr,
                                 C.byref(sp), _dptr(counts, _U32, "counts"),

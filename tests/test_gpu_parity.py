@@ -366,12 +366,81 @@ def test_costs_rejected_where_unsupported(fm):
                                 fm._dptr(offsets, fm._U64, "f"), fm._dptr(pairs, fm._U32, "p"), 100,
                                 fm.C.byref(need), None)
     assert rc == fm.FM_EINVAL
-    sp.best, sp.reserved = 2, 0
+    sp.best, sp.indel_end_skip = 2, 0
     rc = lib.fm_inexact(h.ptr, fm._dptr(codes, fm._U8, "r"), fm._dptr(offs, fm._U32, "o"), 10,
                         fm.C.byref(sp), fm._dptr(counts, fm._U32, "c"),
                         fm._dptr(offsets, fm._U64, "f"), fm._dptr(pairs, fm._U32, "p"), 100,
                         fm.C.byref(need), None)
     assert rc == fm.FM_EINVAL
+    # an end restriction above 255 (longer than any read can use) is rejected by both calls
+    sp = fm.fm_search_params(1, 1, 1, fm.FM_KERNEL_PERSISTENT, None, None, None, 0, 256)
+    for call in (lib.fm_inexact, lib.fm_inexact_noalloc):
+        rc = call(h.ptr, fm._dptr(codes, fm._U8, "r"), fm._dptr(offs, fm._U32, "o"), 10,
+                  fm.C.byref(sp), fm._dptr(counts, fm._U32, "c"), fm._dptr(offsets, fm._U64, "f"),
+                  fm._dptr(pairs, fm._U32, "p"), 100, fm.C.byref(need), None)
+        assert rc == fm.FM_EINVAL
+    h.close()
+
+
+@pytest.mark.parametrize("z,gaps,e", [(1, 1, 1), (2, 1, 5), (2, 2, 3), (3, 2, 12)])
+def test_inexact_end_restriction(fm, z, gaps, e):
+    """Indel columns only where at least e read symbols lie on each side (reads of 1..150
+    symbols, so some fit no indel at all): sets, costs and best hits equal the oracle's, for
+    both kernels, with interval tables and two-symbol steps (the defaults) and without; node
+    counts equal those of the oracle's Listing 2 enumeration with one symbol per step (the
+    canonical rewrites do not apply under the restriction).  A captured graph is not reused
+    across restrictions, and the allocation-free call agrees."""
+    R = synth.repeat_text(1811061273, 300_000, families=30, min_len=300, max_len=3000)
+    reads = synth.sample_reads(71 + e, R, 300 if z < 3 else 60, 1, 150, sub_rate=0.01,
+                               indel_rate=0.01, both_strands=True, random_frac=0.05)
+    ix = oracle.Index(R, "sais")
+    want = ix.inexact(reads.codes, reads.offs, z, gaps, strands=2, end_skip=e)
+    full = ix.inexact(reads.codes, reads.offs, z, gaps, strands=2)
+    assert want["counts"].sum() < full["counts"].sum()
+    bc, bo, bp, bcost = _best_of(want)
+    h = fm.fm_build(R)
+    codes, offs = fm.to_device_reads(reads)
+
+    def same(got, ref, tag):
+        c, o, p = got[:3]
+        assert np.array_equal(_u32(c), ref["counts"]), tag
+        assert np.array_equal(o.cpu().numpy().astype(np.uint64), ref["offsets"]), tag
+        assert np.array_equal(_u32(p), ref["pairs"]), tag
+
+    for tuning in ({"pair_steps": 2}, {"pair_steps": 2, "kmer_depth": fm.KMER_OFF},
+                   {"pair_steps": 1, "kmer_depth": fm.KMER_AUTO}):
+        fm.fm_set_tuning(h, **tuning)
+        for kern in ("plain", "persistent"):
+            tag = (kern, tuning)
+            stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+            got = fm.fm_inexact(h, codes, offs, z, gaps, strands=2, kernel=kern, costs=True,
+                                end_skip=e, stats=stats)
+            same(got, want, tag)
+            assert np.array_equal(got[3].cpu().numpy(), want["costs"]), tag
+            st = stats.cpu().numpy()
+            if tuning["pair_steps"] == 2:
+                assert st[0] == want["nodes"].sum(), tag
+                if tuning.get("kmer_depth") == fm.KMER_OFF:
+                    assert st[1] == want["blocks"].sum(), tag
+            else:
+                assert st[0] <= want["nodes"].sum(), tag
+            c, o, p, cs = fm.fm_inexact(h, codes, offs, z, gaps, strands=2, kernel=kern,
+                                        costs=True, best=True, end_skip=e)
+            assert np.array_equal(_u32(c), bc) and np.array_equal(_u32(p), bp), tag
+            assert np.array_equal(cs.cpu().numpy(), bcost), tag
+    # the default search (graph replay): restricted, unrestricted, restricted again
+    for ref, skip in ((want, e), (full, 0), (want, e)):
+        same(fm.fm_inexact(h, codes, offs, z, gaps, strands=2, end_skip=skip), ref, ("graph", skip))
+    # the allocation-free call on the first 100 reads (well inside its fixed scratch)
+    sub_offs = reads.offs[:101].copy()
+    sub_codes = reads.codes[:int(sub_offs[-1])].copy()
+    want_sub = ix.inexact(sub_codes, sub_offs, z, gaps, strands=2, end_skip=e)
+    room = torch.empty((int(want_sub["offsets"][-1]) + 16, 2), dtype=torch.int32, device="cuda")
+    c, o, p, rc = fm.fm_inexact_noalloc(h, torch.from_numpy(sub_codes).cuda(),
+                                        torch.from_numpy(sub_offs.view(np.int32)).cuda(), z,
+                                        gaps, strands=2, end_skip=e, pairs=room)
+    assert rc == fm.FM_OK
+    same((c, o, p), want_sub, "noalloc")
     h.close()
 
 
