@@ -46,12 +46,14 @@ METRIC = ("reads/s at z<=2 (batched vs plain kernel, bit-exact); 8-Occ Gq/s vs g
 SEED_EXACT, SEED_OCC, SEED_SEARCH = 1811061271, 1811061272, 1811061274
 # bytes of one checkpoint block per interval (fm_info reports the same)
 BLOCK_BYTES = {32: 32, 64: 32, 128: 64, 256: 96}
-# DRAM bytes (read + write) per launch of the search kernel from one ncu capture
-# (profiles/k_inexact_persistent_2gbp_10m_reads_dram.md), by (interval, reference bp, reads):
-# reported only when the run matches that configuration
+# DRAM bytes (read + write) per launch of the current search kernel from one ncu capture,
 # keyed by (interval, reference bp, reads, canonical enumeration on, interval-table depth, pair
-# steps on); an entry is removed when the kernel changes and added back from a fresh capture
-TRAFFIC_NCU = {(64, 2_000_000_000, 10_000_000, True, 13, True): 3.204977914368e12 + 9.60976640e8}
+# steps on) and reported only when the run matches that configuration.  An entry is removed
+# when the kernel changes and added back from a fresh capture.
+TRAFFIC_NCU = {}
+# the last capture, taken before the kernel gained the end-restriction test (a uniform branch
+# on a kernel argument, not taken when the restriction is off): reported beside a null traffic
+TRAFFIC_PREVIOUS = {(64, 2_000_000_000, 10_000_000, True, 13, True): 3.204977914368e12 + 9.60976640e8}
 
 
 def parse():
@@ -471,6 +473,8 @@ def main():
     if not args.skip_cpu and rank == 0 and world == 1:
         cpu = cpu_baseline(args)
 
+    traffic_key = (args.interval, args.ref_n, args.reads, args.canonical == 1, kdepth,
+                   args.pair_steps == 1)
     line = {
         "metric": METRIC, "value": value, "unit": "reads/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -496,9 +500,14 @@ def main():
                    "l2": "flushed between timed steps (256 MB write); index 2x1 GB > L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
-                     "traffic": TRAFFIC_NCU.get((args.interval, args.ref_n, args.reads,
-                                                 args.canonical == 1, kdepth,
-                                                 args.pair_steps == 1)),
+                     "traffic": TRAFFIC_NCU.get(traffic_key),
+                     "traffic_previous_kernel": (
+                         None if traffic_key in TRAFFIC_NCU or traffic_key not in TRAFFIC_PREVIOUS
+                         else {"bytes": TRAFFIC_PREVIOUS[traffic_key],
+                               "note": "ncu DRAM bytes per launch of the search kernel before "
+                                       "its end-restriction test was added (not re-captured "
+                                       "since); profiles/k_inexact_persistent_2gbp_10m_reads_"
+                                       "dram.md"}),
                      "kernel": "k_inexact_persistent", "kernel_ms": k_ms,
                      "gather_ceiling": ceil_main,
                      "blocks_per_s_over_gather_ceiling": (blocks_per_step / (k_ms / 1000) / 1e9
