@@ -515,6 +515,33 @@ def test_inexact_edge_reads(fm):
     _inexact_case(fm, R, batch(short + long_), 3, 3, 64, modes=("canonical",))
 
 
+def test_empty_batches(fm):
+    """Zero reads, zero queries and zero rows: every call returns with empty outputs (offsets
+    = [0], no intervals) and launches no search; a normal batch on the same handle afterwards
+    still equals the oracle."""
+    R = synth.uniform_text(17, 5000)
+    h = fm.fm_build(R)
+    codes = torch.empty(0, dtype=torch.uint8, device="cuda")
+    offs = torch.zeros(1, dtype=torch.int32, device="cuda")
+    k, l = fm.fm_exact(h, codes, offs)
+    assert k.numel() == 0 and l.numel() == 0
+    assert fm.fm_dcalc(h, codes, offs, strands=2).numel() == 0
+    assert fm.fm_locate(h, torch.empty(0, dtype=torch.int32, device="cuda")).numel() == 0
+    for kern in ("plain", "persistent"):
+        c, o, p = fm.fm_inexact(h, codes, offs, 2, 1, strands=2, kernel=kern)
+        assert c.numel() == 0 and o.tolist() == [0] and p.shape[0] == 0, kern
+        c, o, p, cs = fm.fm_inexact(h, codes, offs, 2, 1, strands=2, kernel=kern, costs=True,
+                                    best=True)
+        assert c.numel() == 0 and o.tolist() == [0] and p.shape[0] == 0 and cs.numel() == 0
+    c, o, p, rc = fm.fm_inexact_noalloc(h, codes, offs, 2, 1, strands=2)
+    assert rc == fm.FM_OK and c.numel() == 0 and o.tolist() == [0] and p.shape[0] == 0
+    reads = synth.sample_reads(18, R, 50, 10, 40, sub_rate=0.02, both_strands=True)
+    want = oracle.Index(R, "sais").inexact(reads.codes, reads.offs, 2, 1, strands=2)
+    c, o, p = fm.fm_inexact(h, *fm.to_device_reads(reads), 2, 1, strands=2)
+    assert np.array_equal(_u32(c), want["counts"]) and np.array_equal(_u32(p), want["pairs"])
+    h.close()
+
+
 def test_canonical_knob(fm):
     h = fm.fm_build(_text("uniform", 5000))
     assert fm.fm_get_tuning(h)["canonical"] == 1
