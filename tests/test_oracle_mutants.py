@@ -86,6 +86,26 @@ MUTANTS = [
      "        if (W[i] == lb) may_ins = 0;", "        may_ins = 0;"),
     ("canonical: pass-through call counted as a node",
      "    if (!may_del && !may_mis && !may_match) return;\n", ""),
+    ("deletion not charged",
+     "del_allowed(X, i)) inex_recur(X, i, z - 1, gaps + 1, k2, l2);",
+     "del_allowed(X, i)) inex_recur(X, i, z, gaps + 1, k2, l2);"),
+    ("insertion not charged",
+     "ins_allowed(X, i)) inex_recur(X, i - 1, z - 1, gaps + 1, k, l);",
+     "ins_allowed(X, i)) inex_recur(X, i - 1, z, gaps + 1, k, l);"),
+    ("block count takes l instead of l+1",
+     "    X->blocks += (k / X->interval == (l + 1) / X->interval) ? 1 : 2;\n    const or_index *ix",
+     "    X->blocks += (k / X->interval == l / X->interval) ? 1 : 2;\n    const or_index *ix"),
+    ("closed form: l misses the -1", "    J->l_out[q] = less + pre - 1;",
+     "    J->l_out[q] = less + pre;"),
+    ("closed form: Occ at l drops the matching rows",
+     "J->out8[8 * q + 4 + b] = oc_less[b] + oc_pre[b];", "J->out8[8 * q + 4 + b] = oc_less[b];"),
+    ("occ sweep swaps the k and l halves", "        int half = (int)(s & 1);",
+     "        int half = (int)(~s & 1);"),
+    ("hamming window misses the last position", "    for (int64_t p = 0; p + m <= n; ++p) {",
+     "    for (int64_t p = 0; p + m < n; ++p) {"),
+    ("SA narrowing takes the lower bound inclusive",
+     "        if (row_sym(ix, mid, d) < c) a = mid + 1; else b = mid;",
+     "        if (row_sym(ix, mid, d) <= c) a = mid + 1; else b = mid;"),
     ("end restriction: insertion bound shifted",
      "    return i >= X->end_skip && X->m - 1 - i >= X->end_skip;",
      "    return i > X->end_skip && X->m - 1 - i >= X->end_skip;"),
