@@ -29,6 +29,9 @@ MUTANTS = [
     ("SA-IS typing ignores runs",
      "t[i] = (s[i] < s[i + 1] || (s[i] == s[i + 1] && t[i + 1])) ? 1 : 0;",
      "t[i] = (s[i] < s[i + 1]) ? 1 : 0;"),
+    ("SA-IS names every LMS substring apart",
+     "        if (prev < 0 || !lms_equal(s, t, len, prev, p)) names++;",
+     "        names++;"),
     ("naive SA orders the symbols backwards", "return p < n ? (int)R[p] + 1 : 0; /* $ = 0",
      "return p < n ? 4 - (int)R[p] : 0; /* $ = 0"),
     ("BWT takes the suffix's own first symbol",
