@@ -265,7 +265,10 @@ def main():
 
     max_over_ranks = replicas.max_over_ranks
 
-    l2_flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB L2
+    # the flush writes at least twice the L2 size read from the device (129 MB on GB300)
+    l2_bytes = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0) or 0)
+    flush_bytes = max(256 << 20, 2 * l2_bytes)
+    l2_flush = torch.empty(flush_bytes, dtype=torch.uint8, device=dev)
 
     def flush():
         l2_flush.add_(1)
@@ -497,7 +500,8 @@ def main():
                                                       "blocks_per_sm", "chunk", "trials",
                                                       "tune_seconds")} if tuned else None),
                    "parallelism": f"replicas x{world} (read sharding)",
-                   "l2": "flushed between timed steps (256 MB write); index 2x1 GB > L2"},
+                   "l2": (f"flushed between timed steps ({flush_bytes >> 20} MB write; L2 "
+                          f"{l2_bytes >> 20} MB read from the device); index 2x1 GB > L2")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
                      "traffic": TRAFFIC_NCU.get(traffic_key),
