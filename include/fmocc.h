@@ -98,22 +98,26 @@ typedef struct fm_info_t {
  * NULL and fm_last_error(NULL) holds the message. */
 int fm_build(const char *ref, uint64_t n, const fm_params *p, fm_index **out);
 
-/* Release the index and all device memory it holds.  NULL is ignored. */
+/* Release the index and all device memory it holds (handle lifetime: no counterpart in the
+ * paper).  NULL is ignored. */
 void fm_free(fm_index *h);
 
 /* Message for the last failure on h, or of the last failed fm_build/fm_load on this thread
- * when h is NULL.  The string lives until the next call on the same handle/thread. */
+ * when h is NULL (error reporting: no counterpart in the paper).  The string lives until the
+ * next call on the same handle/thread. */
 const char *fm_last_error(const fm_index *h);
 
-/* Fill *out with the summary of h.  Errors: FM_EINVAL. */
+/* Fill *out with the summary of h: n, the checkpoint interval and layout of Sec. 2, C (Eq. 3),
+ * the $ rows and the device bytes.  Errors: FM_EINVAL. */
 int fm_info(const fm_index *h, fm_info_t *out);
 
-/* Copy the forward C array and BWT symbols back (test access).  bwt: host, n+1 bytes, codes
+/* Copy the BWT (Eq. 2, Fig. 1) back to the host (test access).  bwt: host, n+1 bytes, codes
  * 0..3 with 4 at the $ row.  rev != 0 selects the reverse index.  Errors: FM_EINVAL. */
 int fm_get_bwt(const fm_index *h, int rev, uint8_t *bwt);
 
-/* Save the resident tables to a file (header with n, I, C, $ rows, sizes, then the tables,
- * then a 64-bit FNV-1a checksum) and load them back on a device.
+/* Save the resident tables of Sec. 2 to a file (header with n, I, C, $ rows, sizes, then the
+ * tables, then a 64-bit FNV-1a checksum) and load them back on a device (persistence: no
+ * counterpart in the paper).  fm_load reads a file fm_save wrote; p selects the device.
  * Errors: FM_EIO (open/write/read, bad magic or checksum), FM_ENOMEM, FM_ECUDA. */
 int fm_save(const fm_index *h, const char *path);
 int fm_load(const char *path, const fm_params *p, fm_index **out);
@@ -227,7 +231,7 @@ int fm_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t
                const fm_search_params *sp, uint32_t *counts, uint64_t *offsets, uint32_t *pairs,
                uint64_t pair_capacity, uint64_t *pairs_needed, void *stream);
 
-/* Copy the canonical intervals of the most recent fm_inexact call on h into pairs (device
+/* Copy the Listing 2 interval sets of the most recent fm_inexact call on h into pairs (device
  * uint32[2*pair_capacity], laid out as in fm_inexact), e.g. after that call returned
  * FM_ETRUNC.  Valid until the next fm_inexact call on h.
  * Errors: FM_EINVAL (no earlier search), FM_ETRUNC (capacity below the count found). */
@@ -292,28 +296,32 @@ typedef struct fm_server_result {
     uint32_t reserved;
 } fm_server_result;
 
-/* Start the server thread on h, after building the interval and pair tables the tuning asks
- * for (so no request waits for them).  Errors: FM_EINVAL, FM_ENOMEM, FM_ECUDA. */
+/* Start the server thread on h (serving: no counterpart in the paper; every request runs the
+ * search of Listing 2 exactly as fm_inexact does), after building the interval and pair tables
+ * the tuning asks for (so no request waits for them).  Errors: FM_EINVAL, FM_ENOMEM,
+ * FM_ECUDA. */
 int fm_server_start(fm_index *h, const fm_server_params *p, fm_server **out);
 
-/* Queue a request: reads are host memory (codes 0..3, concatenated, offs[n_reads+1]); they are
- * copied before the call returns.  z <= 7, max_gaps <= 7, read lengths 1..255 (else FM_EINVAL).
- * *ticket identifies the request. */
+/* Queue a request for the search of Listing 2: reads are host memory (codes 0..3,
+ * concatenated, offs[n_reads+1]); they are copied before the call returns.  z <= 7,
+ * max_gaps <= 7, read lengths 1..255 (else FM_EINVAL).  *ticket identifies the request. */
 int fm_server_submit(fm_server *s, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
                      uint32_t z, uint32_t max_gaps, uint64_t *ticket);
 
-/* Wait up to wait_ms milliseconds (0: do not wait) for a request.  FM_OK fills *res;
- * FM_ETIMEOUT when it is not done yet; FM_EINVAL for an unknown ticket. */
+/* Wait up to wait_ms milliseconds (0: do not wait) for a request (serving: no counterpart in
+ * the paper).  FM_OK fills *res with its Listing 2 interval sets; FM_ETIMEOUT when it is not
+ * done yet; FM_EINVAL for an unknown ticket. */
 int fm_server_poll(fm_server *s, uint64_t ticket, uint32_t wait_ms, fm_server_result *res);
 
-/* Drop a finished request's result memory. */
+/* Drop a finished request's result memory (serving: no counterpart in the paper). */
 int fm_server_release(fm_server *s, uint64_t ticket);
 
-/* Counters: batches run, reads searched, requests finished, GPU busy milliseconds. */
+/* Serving counters (no counterpart in the paper): batches run, reads searched, requests
+ * finished, GPU busy milliseconds. */
 int fm_server_stats(fm_server *s, uint64_t out[4]);
 
 /* Finish the queued requests, stop the thread and free the server (results not released are
- * freed too).  NULL is ignored. */
+ * freed too; serving: no counterpart in the paper).  NULL is ignored. */
 int fm_server_stop(fm_server *s);
 
 /* Measurement probe (no counterpart in the paper): `threads` threads (a multiple of 256) each
@@ -376,6 +384,10 @@ typedef struct fm_tuning {
 #define FM_KMER_AUTO 0xfeu
 #define FM_KMER_OFF 0xffu
 
+/* Set or read the knobs above.  They change speed and memory only, never results; the
+ * interval tables and pair steps answer the cache-locality question Sec. 4.2 leaves open, the
+ * rest have no counterpart in the paper.  fm_set_tuning checks every value before applying
+ * any: a rejected call changes nothing. */
 int fm_set_tuning(fm_index *h, const fm_tuning *t);
 int fm_get_tuning(const fm_index *h, fm_tuning *t);
 
