@@ -207,8 +207,10 @@ class Index:
 
 def fm_build(ref, interval: int = 64, flags: int = 0, device: int = -1,
              forward_only: bool = False, both_strands: bool = False) -> Index:
-    """Build the index of ``ref`` (bytes/str over ACGTacgt, or a uint8 numpy array of codes);
-    with ``both_strands`` the index of ref . revcomp(ref)."""
+    """Build the index of ``ref`` (bytes/str over ACGTacgt, or a uint8 numpy array of codes):
+    suffix array (Eq. 1), BWT (Eq. 2), C and the interleaved checkpoint table of Sec. 2, and
+    the same for reverse(ref), which the D bound needs; with ``both_strands`` the index of
+    ref . revcomp(ref)."""
     lib = load_library()
     if isinstance(ref, np.ndarray):
         buf = np.ascontiguousarray(ref, dtype=np.uint8)
@@ -231,14 +233,17 @@ def fm_build(ref, interval: int = 64, flags: int = 0, device: int = -1,
 
 
 def fm_free(h: Index):
+    """Release the index (handle lifetime: no counterpart in the paper)."""
     h.close()
 
 
 def fm_last_error(h: Index | None = None) -> str:
+    """Message of the last failure (error reporting: no counterpart in the paper)."""
     return (load_library().fm_last_error(h.ptr if h is not None else None) or b"").decode()
 
 
 def fm_info(h: Index) -> dict:
+    """Summary of the index: n, the checkpoint layout of Sec. 2, C (Eq. 3), the $ rows."""
     inf = fm_info_t()
     _check(load_library().fm_info(h.ptr, C.byref(inf)), h)
     return {"n": inf.n, "interval": inf.interval, "block_bytes": inf.block_bytes,
@@ -249,6 +254,7 @@ def fm_info(h: Index) -> dict:
 
 
 def fm_get_bwt(h: Index, rev: bool = False) -> np.ndarray:
+    """The BWT (Eq. 2, Fig. 1) as host codes 0..3, 4 at the $ row (test access)."""
     n = fm_info(h)["n"]
     out = np.empty(n + 1, dtype=np.uint8)
     _check(load_library().fm_get_bwt(h.ptr, 1 if rev else 0, out.ctypes.data_as(C.c_void_p)), h)
@@ -256,10 +262,13 @@ def fm_get_bwt(h: Index, rev: bool = False) -> np.ndarray:
 
 
 def fm_save(h: Index, path: str):
+    """Write the resident tables of Sec. 2 to a file (persistence: no counterpart in the
+    paper)."""
     _check(load_library().fm_save(h.ptr, path.encode()), h)
 
 
 def fm_load(path: str, device: int = -1) -> Index:
+    """Load a file fm_save wrote onto a device (persistence: no counterpart in the paper)."""
     p = fm_params(0, 0, device, 0)
     out = C.c_void_p()
     _check(load_library().fm_load(path.encode(), C.byref(p), C.byref(out)))
@@ -268,7 +277,8 @@ def fm_load(path: str, device: int = -1) -> Index:
 
 def fm_occ8(h: Index, k: torch.Tensor, l: torch.Tensor, out: torch.Tensor | None = None,
             stream=None) -> torch.Tensor:
-    """out[q] = [Occ(A..T, k[q]-1), Occ(A..T, l[q])] as an int32 [N, 8] CUDA tensor."""
+    """out[q] = [Occ(A..T, k[q]-1), Occ(A..T, l[q])] as an int32 [N, 8] CUDA tensor: the eight
+    Occ values of one backward-search step in one pass (Sec. 2 closing remarks, Sec. 3.3)."""
     N = k.numel()
     if l.numel() != N:
         raise ValueError("k and l differ in length")
@@ -298,7 +308,8 @@ def fm_exact(h: Index, reads: torch.Tensor, offs: torch.Tensor, k_out=None, l_ou
 
 def fm_locate(h: Index, rows: torch.Tensor, pos_out: torch.Tensor | None = None,
               steps: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """SA[row] for each row (int32 CUDA tensor of the same length)."""
+    """SA[row] for each row (int32 CUDA tensor of the same length), by Psi^-1 walks to a sampled
+    row (Sec. 2, Eq. 4-5)."""
     N = rows.numel()
     if pos_out is None:
         pos_out = torch.empty(N, dtype=torch.int32, device=rows.device)
@@ -312,6 +323,8 @@ def fm_locate(h: Index, rows: torch.Tensor, pos_out: torch.Tensor | None = None,
 
 def fm_dcalc(h: Index, reads: torch.Tensor, offs: torch.Tensor, strands: int = 1, D_out=None,
              stream=None) -> torch.Tensor:
+    """The D lower bound of the inexact search (Li and Durbin 2009, cited with Listing 2), one
+    uint8 per query symbol, by forward extension on the index of reverse(R)."""
     nr = offs.numel() - 1
     total = int(reads.numel()) * strands
     if D_out is None:
@@ -331,8 +344,8 @@ def fm_inexact(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int, max_ga
     pairs int32[total, 2]), plus costs uint8[total] (per interval the fewest differences) when
     ``costs`` is True or a uint8 tensor; ``best`` keeps only each query's minimum-cost
     intervals; ``end_skip`` > 0 places indel columns only where at least that many query
-    symbols lie on each side of them.  On FM_ETRUNC the pairs buffer is regrown and fetched again (or, with costs or
-    best, the call is repeated with larger buffers)."""
+    symbols lie on each side of them.  On FM_ETRUNC the pairs buffer is regrown and fetched
+    again (or, with costs or best, the call is repeated with larger buffers)."""
     lib = load_library()
     nr = offs.numel() - 1
     nq = nr * strands
@@ -387,8 +400,8 @@ def fm_inexact(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int, max_ga
 def fm_inexact_noalloc(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int,
                        max_gaps: int = 0, strands: int = 1, counts=None, offsets=None,
                        pairs=None, stream=None, end_skip: int = 0):
-    """fm_inexact without device allocation inside the library (fixed static scratch; at most
-    32,768 queries per call).  The caller provides (or this wrapper allocates through torch,
+    """fm_inexact (Listing 2) without device allocation inside the library (fixed static
+    scratch; at most 32,768 queries per call).  The caller provides (or this wrapper allocates through torch,
     before the call) the output buffers.  Returns (counts, offsets, pairs, status); status is
     FM_ETRUNC when ``pairs`` is too small (counts and offsets are then complete)."""
     lib = load_library()
@@ -414,6 +427,7 @@ def fm_inexact_noalloc(h: Index, reads: torch.Tensor, offs: torch.Tensor, z: int
 
 
 def fm_inexact_fetch(h: Index, pairs: torch.Tensor, stream=None):
+    """Copy the Listing 2 interval sets of the last fm_inexact call into ``pairs``."""
     _check(load_library().fm_inexact_fetch(h.ptr, _dptr(pairs, _U32, "pairs"), pairs.shape[0],
                                            _stream(stream)), h)
     return pairs
@@ -423,13 +437,16 @@ def fm_set_tuning(h: Index, warps_per_block=0, blocks_per_sm=0, chunk=0, plain_b
                   graphs=0, occ_per_thread=0, l2_fetch_bytes=0, canonical=0, kmer_depth=0,
                   pair_steps=0):
     """Zero keeps a knob; graphs, canonical and pair_steps: 1 on, 2 off; kmer_depth: 1..14,
-    KMER_AUTO or KMER_OFF."""
+    KMER_AUTO or KMER_OFF.  Speed and memory only, never results (the tables and pair steps
+    answer the cache-locality question of Sec. 4.2; the rest have no counterpart in the
+    paper)."""
     t = fm_tuning(warps_per_block, blocks_per_sm, chunk, plain_block, graphs, occ_per_thread,
                   l2_fetch_bytes, canonical, kmer_depth, pair_steps)
     _check(load_library().fm_set_tuning(h.ptr, C.byref(t)), h)
 
 
 def fm_get_tuning(h: Index) -> dict:
+    """The knobs in effect (see fm_set_tuning)."""
     t = fm_tuning()
     _check(load_library().fm_get_tuning(h.ptr, C.byref(t)), h)
     return {"warps_per_block": t.warps_per_block, "blocks_per_sm": t.blocks_per_sm,
@@ -441,7 +458,7 @@ def fm_get_tuning(h: Index) -> dict:
 def fm_probe_gather(buf: torch.Tensor, granule: int, threads: int, per_thread: int,
                     seed: int = 1, sink: torch.Tensor | None = None, stream=None,
                     inflight: int = 4):
-    """Random-gather probe over a CUDA buffer (measurement only)."""
+    """Random-gather probe over a CUDA buffer (measurement only: no counterpart in the paper)."""
     if sink is None:
         sink = torch.empty(threads, dtype=torch.int32, device=buf.device)
     rc = load_library().fm_probe_gather(C.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size(),
@@ -452,8 +469,9 @@ def fm_probe_gather(buf: torch.Tensor, granule: int, threads: int, per_thread: i
 
 
 class Server:
-    """Request loop over a resident index (fm_server_*): submit host read batches, poll for
-    their interval sets.  While it runs, the index handle belongs to the server."""
+    """Request loop over a resident index (fm_server_*; serving has no counterpart in the paper,
+    each request runs the search of Listing 2): submit host read batches, poll for their
+    interval sets.  While it runs, the index handle belongs to the server."""
 
     def __init__(self, h: Index, max_batch_reads: int = 0, strands: int = 2,
                  frontier_budget: int = 0, kernel="persistent"):
