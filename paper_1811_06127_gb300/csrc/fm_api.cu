@@ -57,6 +57,7 @@ __global__ void k_append_revcomp(uint8_t *__restrict__ t, uint64_t n) {
         t[n + i] = (uint8_t)(3u - t[n - 1 - i]);
 }
 
+// ACGTacgt (or codes 0..3) to codes 0..3 in place; any other symbol sets *err
 __global__ void k_encode(uint8_t *__restrict__ t, uint64_t n, int ascii, uint32_t *__restrict__ err) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {

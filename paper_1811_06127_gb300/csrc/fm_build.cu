@@ -17,12 +17,14 @@
 namespace fm {
 namespace {
 
+// reverse(R), the text of the second index (the D bound extends forward on it)
 __global__ void k_reverse(const uint8_t *__restrict__ in, uint64_t n, uint8_t *__restrict__ out) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x)
         out[i] = in[n - 1 - i];
 }
 
+// pass-0 key of suffix i: its first 27 symbols in base 5 ($ = 0 past the end); val = i
 __global__ void k_keys27(const uint8_t *__restrict__ codes, uint64_t n, uint64_t *__restrict__ key,
                          uint32_t *__restrict__ val) {
     const uint64_t N = n + 1;
@@ -54,6 +56,7 @@ __global__ void k_heads(const uint64_t *__restrict__ key, uint64_t N, uint32_t *
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(nheads, local);
 }
 
+// rank[suffix] = the start of its group, from the sorted order (val) and the group heads
 __global__ void k_scatter_rank(const uint32_t *__restrict__ val, const uint32_t *__restrict__ grp,
                                uint64_t N, uint32_t *__restrict__ rank) {
     for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < N;
@@ -61,6 +64,7 @@ __global__ void k_scatter_rank(const uint32_t *__restrict__ val, const uint32_t 
         rank[val[j]] = grp[j];
 }
 
+// doubling key of suffix i: (rank_h(i), rank_h(i+h) + 1), 0 when i+h passes the end
 __global__ void k_keys_double(const uint32_t *__restrict__ rank, uint64_t N, uint64_t h, int shift,
                               uint64_t *__restrict__ key, uint32_t *__restrict__ val) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N;

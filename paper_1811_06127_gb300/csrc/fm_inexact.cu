@@ -737,6 +737,7 @@ __global__ void k_hist(const uint4 *__restrict__ raw, const unsigned long long *
         atomicAdd(cnt + raw[e].x, 1u);
 }
 
+// raw results grouped by query: each goes to start[q] + its arrival order, as (k << 32) | l
 __global__ void k_scatter(const uint4 *__restrict__ raw, const unsigned long long *__restrict__ d_R,
                           uint64_t cap, const uint64_t *__restrict__ start,
                           uint32_t *__restrict__ cursor, uint64_t *__restrict__ grouped) {
@@ -1025,6 +1026,7 @@ __global__ void k_status(const unsigned long long *__restrict__ raw, const uint3
     }
 }
 
+// the per-query distinct counts into the caller's counts
 __global__ void k_copy_counts(uint32_t nq, const uint32_t *__restrict__ ucnt,
                               uint32_t *__restrict__ counts) {
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x)
@@ -1063,6 +1065,7 @@ __device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t *ws, ui
     return before + x - v;
 }
 
+// pass 1: the sum of each tile of kScanTile values
 __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const uint32_t *__restrict__ in, uint64_t n,
                                                              uint64_t *__restrict__ tile_sum) {
     __shared__ uint64_t ws[32];
@@ -1078,6 +1081,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const uint32_t *__r
     if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
 }
 
+// pass 2 (one CTA): exclusive scan of the tile sums in place; tile_sum[ntiles] = total
 __global__ void __launch_bounds__(kScanThreads) k_scan_sums(uint64_t *__restrict__ tile_sum, uint64_t ntiles) {
     __shared__ uint64_t ws[32];
     uint64_t carry = 0;
@@ -1092,6 +1096,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_sums(uint64_t *__restrict
     if (threadIdx.x == 0) tile_sum[ntiles] = carry;
 }
 
+// pass 3: each tile's exclusive scan from its offset; the last tile writes out[n] = total
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t *__restrict__ in, uint64_t n,
                                                              const uint64_t *__restrict__ tile_off,
                                                              uint64_t *__restrict__ out) {
