@@ -233,7 +233,8 @@ int fm_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t
 
 /* Copy the Listing 2 interval sets of the most recent fm_inexact call on h into pairs (device
  * uint32[2*pair_capacity], laid out as in fm_inexact), e.g. after that call returned
- * FM_ETRUNC.  Valid until the next fm_inexact call on h.
+ * FM_ETRUNC.  Valid until the next fm_inexact or fm_inexact_noalloc call on h; a call that
+ * failed with any other status leaves nothing to fetch.
  * Errors: FM_EINVAL (no earlier search), FM_ETRUNC (capacity below the count found). */
 int fm_inexact_fetch(fm_index *h, uint32_t *pairs, uint64_t pair_capacity, void *stream);
 
@@ -250,7 +251,12 @@ int fm_inexact_fetch(fm_index *h, uint32_t *pairs, uint64_t pair_capacity, void 
  *   - at most 32,768 queries (n_reads * strands) per call, else FM_EINVAL;
  *   - at most 262,144 intervals before deduplication, else FM_ENOMEM (nothing is grown: split
  *     the batch and call again).
- * The index handle itself must already exist (fm_build/fm_load allocate).  The first call on
+ * The index handle itself must already exist (fm_build/fm_load allocate).  This call builds
+ * no table: it expands short strings from the interval tables, and takes two-symbol steps
+ * over the pair table, only when an earlier fm_inexact, fm_exact or fm_server_start on h
+ * built them (results are the same either way; without them it reads more checkpoint blocks
+ * and runs slower).  Its results live in the static array, so fm_inexact_fetch does not serve
+ * them: after this call, fetch returns FM_EINVAL until the next fm_inexact.  The first call on
  * each device looks up the array's device address (cudaGetSymbolAddress, once per device, with
  * that device current); make that first call before any stream capture.  Every call shares the
  * one array and leaves its contents behind; calls that overlap on the GPU, from any thread,
@@ -324,7 +330,8 @@ int fm_server_stats(fm_server *s, uint64_t out[4]);
  * freed too; serving: no counterpart in the paper).  NULL is ignored. */
 int fm_server_stop(fm_server *s);
 
-/* Measurement probe (no counterpart in the paper): `threads` threads (a multiple of 256) each
+/* Measurement probe, exported for the benchmark only (no counterpart in the paper, and not a
+ * search call): `threads` threads (a multiple of 256) each
  * read `per_thread` (a multiple of `inflight`) granules of `granule` bytes (32, 64 or 128) at
  * uniformly random granule-aligned offsets of the device buffer buf[0, bytes), `inflight`
  * (1, 2, 4 or 8) at a time in flight, and write one folded word each to sink (device

@@ -1407,6 +1407,9 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
     const uint32_t errs = (uint32_t)status[1], errd = (uint32_t)status[2];
     if (rawn > raw_cap || (errs & (kErrSpill | kErrStack))) return FM_OK;   // regrow eagerly
     *fallback = false;
+    h->last_valid = false;
+    if (errd & kErrReadLen) return set_error(h, FM_EINVAL, "a read is longer than 255 symbols");
+    if (errd & kErrDomain) return set_error(h, FM_EINVAL, "a read holds a code above 3");
     h->last_nq = nq;
     h->last_total = need;
     h->last_off_ucnt = L.ucnt;
@@ -1430,8 +1433,6 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
         prof->passes = 1;
         prof->graph = 1;
     }
-    if (errd & kErrReadLen) return set_error(h, FM_EINVAL, "a read is longer than 255 symbols");
-    if (errd & kErrDomain) return set_error(h, FM_EINVAL, "a read holds a code above 3");
     if (need > pair_capacity)
         return set_error(h, FM_ETRUNC, "pair capacity " + std::to_string(pair_capacity) +
                                            " below the " + std::to_string(need) + " intervals found");
@@ -1451,6 +1452,7 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
         if (!fallback) return grc;
         if (grc) return grc;
     }
+    h->last_valid = false;   // only this call's results may be fetched after it
     const uint32_t strands = sp->strands;
     const uint64_t nq64 = (uint64_t)n_reads * strands;
     if (nq64 > 0xffffffffull) return set_error(h, FM_EINVAL, "too many queries");
@@ -1566,10 +1568,15 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
             prof->passes += 1;
         }
         unsigned long long rawn = 0;
-        uint32_t errw = 0;
+        uint32_t errw = 0, derr = 0;
         FM_CUDA_TRY(h, cudaMemcpyAsync(&rawn, d_raw_count, 8, cudaMemcpyDeviceToHost, st));
         FM_CUDA_TRY(h, cudaMemcpyAsync(&errw, h->d_err + kErrSearch, 4, cudaMemcpyDeviceToHost, st));
+        FM_CUDA_TRY(h, cudaMemcpyAsync(&derr, h->d_err + kErrDcalc, 4, cudaMemcpyDeviceToHost, st));
         FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+        // a bad read is reported before anything else (a truncation status would send the
+        // caller to fm_inexact_fetch for the results of a failed call)
+        if (derr & kErrReadLen) return set_error(h, FM_EINVAL, "a read is longer than 255 symbols");
+        if (derr & kErrDomain) return set_error(h, FM_EINVAL, "a read holds a code above 3");
         if (errw & kErrStack) return set_error(h, FM_ENOMEM, "plain search stack overflow");
         bool again = false;
         if (errw & kErrSpill) {
@@ -1687,11 +1694,6 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
                 launches += sp->costs && !sp->best ? 2u : 1u;
             }
             if ((rc = finish_profile(h, prof, ev, launches, st))) return rc;
-            uint32_t derr = 0;
-            FM_CUDA_TRY(h, cudaMemcpyAsync(&derr, h->d_err + kErrDcalc, 4, cudaMemcpyDeviceToHost, st));
-            FM_CUDA_TRY(h, cudaStreamSynchronize(st));
-            if (derr & kErrReadLen) return set_error(h, FM_EINVAL, "a read is longer than 255 symbols");
-            if (derr & kErrDomain) return set_error(h, FM_EINVAL, "a read holds a code above 3");
             return FM_OK;
         }
     }
@@ -1780,6 +1782,9 @@ int run_inexact_noalloc(fm_index *h, const uint8_t *reads, const uint32_t *offs,
                         uint32_t n_reads, const fm_search_params *sp, uint32_t *counts,
                         uint64_t *offsets, uint32_t *pairs, uint64_t pair_capacity,
                         uint64_t *pairs_needed, cudaStream_t st) {
+    // its results live in the static array, not in the handle's scratch: fm_inexact_fetch
+    // must not serve an earlier fm_inexact call's intervals in their place
+    h->last_valid = false;
     if (sp->costs || sp->best)
         return set_error(h, FM_EINVAL, "fm_inexact_noalloc reports interval sets only (no costs, no best)");
     const uint64_t nq64 = (uint64_t)n_reads * sp->strands;
@@ -1839,10 +1844,13 @@ int run_inexact_noalloc(fm_index *h, const uint8_t *reads, const uint32_t *offs,
     }
     if (rc) return rc;
     unsigned long long rawn = 0;
-    uint32_t errw = 0;
+    uint32_t errw = 0, derr = 0;
     FM_CUDA_TRY(h, cudaMemcpyAsync(&rawn, d_raw_count, 8, cudaMemcpyDeviceToHost, st));
     FM_CUDA_TRY(h, cudaMemcpyAsync(&errw, h->d_err + kErrSearch, 4, cudaMemcpyDeviceToHost, st));
+    FM_CUDA_TRY(h, cudaMemcpyAsync(&derr, h->d_err + kErrDcalc, 4, cudaMemcpyDeviceToHost, st));
     FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+    if (derr & kErrReadLen) return set_error(h, FM_EINVAL, "a read is longer than 255 symbols");
+    if (derr & kErrDomain) return set_error(h, FM_EINVAL, "a read holds a code above 3");
     if (errw & kErrStack)   // cannot happen: the stack capacity is the proven bound
         return set_error(h, FM_ENOMEM, "fm_inexact_noalloc: depth-first stack overflow");
     if (rawn > kNoAllocMaxRaw)
@@ -1892,11 +1900,7 @@ int run_inexact_noalloc(fm_index *h, const uint8_t *reads, const uint32_t *offs,
                                                                         grouped, pairs, pair_capacity);
         FM_CUDA_TRY(h, cudaGetLastError());
     }
-    uint32_t derr = 0;
-    FM_CUDA_TRY(h, cudaMemcpyAsync(&derr, h->d_err + kErrDcalc, 4, cudaMemcpyDeviceToHost, st));
     FM_CUDA_TRY(h, cudaStreamSynchronize(st));
-    if (derr & kErrReadLen) return set_error(h, FM_EINVAL, "a read is longer than 255 symbols");
-    if (derr & kErrDomain) return set_error(h, FM_EINVAL, "a read holds a code above 3");
     return FM_OK;
 }
 

@@ -578,6 +578,34 @@ def test_inexact_too_long_read(fm):
     h.close()
 
 
+@pytest.mark.parametrize("graphs", [1, 2])
+def test_bad_read_reported_before_truncation(fm, graphs):
+    """A batch holding a code above 3 fails with FM_EINVAL even when the pairs buffer is also
+    too small: the truncation status would send the caller to fm_inexact_fetch, which must not
+    hand out the intervals of a failed call.  Graph replay (1) and the eager path (2)."""
+    R = synth.repeat_text(31, 100_000, families=10, min_len=300, max_len=2000)
+    reads = synth.sample_reads(32, R, 300, 30, 80, sub_rate=0.02, both_strands=True)
+    h = fm.fm_build(R)
+    fm.fm_set_tuning(h, graphs=graphs)
+    codes, offs = fm.to_device_reads(reads)
+    c0, o0, p0 = fm.fm_inexact(h, codes, offs, 2, 1, strands=2)   # sizes the scratch
+    assert int(o0[-1]) > 10
+    pairs = torch.empty((2, 2), dtype=torch.int32, device="cuda")
+    good = codes.clone()
+    codes[int(offs[7]) + 3] = 5                                    # one bad symbol
+    for _ in range(2):   # the second call of the same key replays the captured graph
+        with pytest.raises(fm.FmError) as ei:
+            fm.fm_inexact(h, codes, offs, 2, 1, strands=2, pairs=pairs)
+        assert ei.value.code == fm.FM_EINVAL
+        with pytest.raises(fm.FmError) as ei:   # nothing of the failed call can be fetched
+            fm.fm_inexact_fetch(h, pairs)
+        assert ei.value.code == fm.FM_EINVAL
+    codes.copy_(good)
+    c1, o1, p1 = fm.fm_inexact(h, codes, offs, 2, 1, strands=2)
+    assert torch.equal(c0, c1) and torch.equal(o0, o1) and torch.equal(p0, p1)
+    h.close()
+
+
 def test_save_load_roundtrip(fm):
     R = synth.repeat_text(8, 50_000, families=5, min_len=300, max_len=1000)
     h = fm.fm_build(R, interval=128)

@@ -650,6 +650,26 @@ def test_canonical_same_results(kind):
         assert b["nodes"].sum() < a["nodes"].sum()
 
 
+@pytest.mark.parametrize("z,gaps", [(4, 1), (4, 2), (4, 4), (5, 2), (6, 3)])
+def test_canonical_same_results_high_z_run_poor(z, gaps):
+    """Beyond z = 3: canonical enumeration = Listing 2's result sets and costs on a text with
+    no run of one symbol (R[i] != R[i-1]), where the literal recursion stays affordable at
+    z = 4..6.  Reads carry substitutions and indels, so every canonical rule is exercised."""
+    rng = np.random.default_rng(1811061290)
+    R = (np.cumsum(rng.integers(1, 4, 20_000)) % 4).astype(np.uint8)
+    assert (R[1:] != R[:-1]).all()
+    ix = oracle.Index(R, "sais")
+    m = 40 if z == 4 else 24
+    reads = synth.sample_reads(91 + z, R, 120, m // 2, m, sub_rate=0.03, indel_rate=0.01,
+                               both_strands=True)
+    a = ix.inexact(reads.codes, reads.offs, z, gaps, strands=2)
+    b = ix.inexact(reads.codes, reads.offs, z, gaps, strands=2, canonical=True)
+    for key in ("counts", "offsets", "pairs", "costs"):
+        assert np.array_equal(a[key], b[key]), (z, gaps, key)
+    assert int(a["offsets"][-1]) > 100
+    assert (b["nodes"] <= a["nodes"]).all() and b["nodes"].sum() < a["nodes"].sum()
+
+
 def test_inexact_hamming_identity_and_z0():
     R = synth.repeat_text(13, 40000, families=6, min_len=300, max_len=900)
     ix = oracle.Index(R, "sais")
