@@ -548,7 +548,7 @@ void or_dcalc(const or_index *ix, const uint8_t *W, int64_t m, uint8_t *D) {
 }
 
 /* ------------------------------------------------------------------------------------------
- * Listing 2 (InexRecur) with D pruning, set semantics
+ * The inexact search of Sec. 2 (Listing 2) with D pruning, set semantics
  * ---------------------------------------------------------------------------------------- */
 typedef struct {
     uint32_t *pairs; /* k, l, cost (differences the alignment used) */
@@ -591,89 +591,121 @@ static int del_allowed(const inex_ctx *X, int64_t i) {
     return i + 1 >= X->end_skip && X->m - 1 - i >= X->end_skip;
 }
 
-static void inex_recur(inex_ctx *X, int64_t i, int z, int gaps, int64_t k, int64_t l) {
-    if (z < 0) return;
-    if (X->prune && i >= 0 && z < X->D[i]) return;
-    if (i < 0) {
-        if (k >= 1) pv_push(X->out, (uint32_t)k, (uint32_t)l, (uint32_t)(X->z0 - z));
-        return;
+/* The search of Sec. 2 (Listing 2) as a worklist of alignment states.  A state is a partial
+ * alignment built from the end of W: the columns placed so far spell a reference string X,
+ * whose suffix-array interval is [k, l]; W[0..i] is still to be aligned, z differences are
+ * left and gaps indel columns were used.  For the canonical enumeration a state also keeps
+ * the column that created it (last: 0 match or the start, 1 mismatch, 2 insertion,
+ * 3 deletion) and that column's reference symbol lb.  The next column to the left is one of:
+ *   - W[i] against no reference symbol (an insertion): X and [k, l] unchanged, i - 1;
+ *   - a reference symbol b against no symbol of W (a deletion): X becomes bX, i unchanged;
+ *   - W[i] against b: X becomes bX, i - 1, one difference unless b = W[i].
+ * An indel column costs a difference and a gap; prepending b needs bX to occur in R (its
+ * interval non-empty).  A state with i < 0 has aligned all of W: X's interval is a result
+ * (unless X is empty), with cost z0 - z.  A state is dropped when z < 0, or when z < D(i)
+ * (the bound of or_dcalc) with pruning on.  The order in which states are taken does not
+ * change the result set; this one is depth first. */
+typedef struct {
+    int64_t i, k, l;
+    int z, gaps, last, lb;
+} inex_state;
+
+typedef struct {
+    inex_state *a;
+    int64_t n, cap;
+} state_stack;
+
+static void st_push(state_stack *S, int64_t i, int z, int gaps, int64_t k, int64_t l, int last,
+                    int lb) {
+    if (S->n == S->cap) {
+        S->cap = S->cap ? 2 * S->cap : 256;
+        S->a = (inex_state *)realloc(S->a, sizeof(inex_state) * (size_t)S->cap);
     }
-    X->nodes++;
-    X->blocks += (k / X->interval == (l + 1) / X->interval) ? 1 : 2;
-    const or_index *ix = X->ix;
-    /* insertion: W[i] aligned to no reference symbol */
-    if (gaps < X->max_gaps && ins_allowed(X, i)) inex_recur(X, i - 1, z - 1, gaps + 1, k, l);
+    inex_state *t = &S->a[S->n++];
+    t->i = i;
+    t->z = z;
+    t->gaps = gaps;
+    t->k = k;
+    t->l = l;
+    t->last = last;
+    t->lb = lb;
+}
+
+/* the interval of bX for every b, from the interval [k, l] of X: one backward step
+ * (Eq. 3 and Listing 1) */
+static void extend4(const or_index *ix, int64_t k, int64_t l, int64_t nk[4], int64_t nl[4]) {
     int64_t ok[4], ol[4];
     or_occ4(ix, k - 1, ok);
     or_occ4(ix, l, ol);
     for (int b = 0; b < 4; ++b) {
-        int64_t k2 = ix->C[b] + ok[b] + 1;
-        int64_t l2 = ix->C[b] + ol[b];
-        if (k2 <= l2) {
-            /* deletion: reference symbol b aligned to no read symbol */
-            if (gaps < X->max_gaps && del_allowed(X, i)) inex_recur(X, i, z - 1, gaps + 1, k2, l2);
-            if (b == X->W[i])
-                inex_recur(X, i - 1, z, gaps, k2, l2);
-            else
-                inex_recur(X, i - 1, z - 1, gaps, k2, l2);
-        }
+        nk[b] = ix->C[b] + ok[b] + 1;
+        nl[b] = ix->C[b] + ol[b];
     }
 }
 
-/* Canonical enumeration (test instrumentation, not part of the paper's method): the same
- * search, except that a call also knows the column that created it (last: 0 match or top
- * call, 1 mismatch with reference symbol lb, 2 insertion, 3 deletion of lb) and skips the
- * children that begin a non-canonical pair of adjacent columns:
+/* canonical = 0: every alignment (the enumeration of Listing 2).  canonical = 1: the
+ * canonical alignments only (test instrumentation, not part of the paper's method): a state
+ * does not start a non-canonical pair of adjacent columns,
  *   after an insertion (of W[i+1]): no mismatch, no deletion, no match when W[i] = W[i+1];
  *   after a deletion of lb: no insertion; when i >= 1 also no mismatch and no match of lb;
  *   after a mismatch with lb at W[i+1]: no insertion when W[i] = lb, no deletion of W[i+1].
- * Each skipped pair spells the same reference string as a canonical pair of no higher cost,
- * so the reported intervals are unchanged.  A call counts as a node only when one of its
- * Occ children (deletion, mismatch, match) is allowed by these rules and by z; a call with
- * none passes through to its insertion child alone.  The rewrites move indel columns, so
- * they do not hold under an end restriction: the two are not combined. */
-static void inex_canon(inex_ctx *X, int64_t i, int z, int gaps, int64_t k, int64_t l, int last,
-                       int lb) {
-    if (z < 0 || (X->prune && i >= 0 && z < X->D[i])) return;
-    if (i < 0) { /* a result, unless no reference symbol was used */
-        if (k > 0) pv_push(X->out, (uint32_t)k, (uint32_t)l, (uint32_t)(X->z0 - z));
-        return;
-    }
+ * Each excluded pair spells the same reference string as a canonical pair of no higher cost,
+ * so the results are unchanged.  A state counts as a node (nodes, blocks) when it reaches
+ * the backward step: always with i >= 0 in the first enumeration; in the canonical one only
+ * when a deletion, mismatch or match may follow (a state with none only passes its insertion
+ * on).  The rules move indel columns, so they are not combined with an end restriction. */
+static void inex_search(inex_ctx *X, int canonical) {
     const uint8_t *W = X->W;
-    int may_ins = gaps < X->max_gaps, may_del = gaps < X->max_gaps && z >= 1;
-    int may_mis = z >= 1, may_match = 1, no_del_sym = -1;
-    if (last == 2) {
-        may_del = 0;
-        may_mis = 0;
-        if (W[i] == W[i + 1]) may_match = 0;
-    } else if (last == 3) {
-        may_ins = 0;
-        if (i >= 1) {
-            may_mis = 0;
-            if (W[i] == lb) may_match = 0;
+    state_stack S = {NULL, 0, 0};
+    st_push(&S, X->m - 1, X->z0, 0, 0, X->ix->n, 0, 0);
+    while (S.n > 0) {
+        const inex_state s = S.a[--S.n];
+        if (s.z < 0) continue;
+        if (X->prune && s.i >= 0 && s.z < X->D[s.i]) continue;
+        if (s.i < 0) {
+            if (s.k >= 1) pv_push(X->out, (uint32_t)s.k, (uint32_t)s.l, (uint32_t)(X->z0 - s.z));
+            continue;
         }
-    } else if (last == 1) {
-        if (W[i] == lb) may_ins = 0;
-        no_del_sym = W[i + 1];
-    }
-    if (may_ins) inex_canon(X, i - 1, z - 1, gaps + 1, k, l, 2, 0);
-    if (!may_del && !may_mis && !may_match) return;
-    X->nodes++;
-    X->blocks += (k / X->interval == (l + 1) / X->interval) ? 1 : 2;
-    int64_t ok[4], ol[4];
-    or_occ4(X->ix, k - 1, ok);
-    or_occ4(X->ix, l, ol);
-    for (int b = 0; b < 4; ++b) {
-        int64_t k2 = X->ix->C[b] + ok[b] + 1;
-        int64_t l2 = X->ix->C[b] + ol[b];
-        if (k2 > l2) continue;
-        if (may_del && b != no_del_sym) inex_canon(X, i, z - 1, gaps + 1, k2, l2, 3, b);
-        if (b == W[i]) {
-            if (may_match) inex_canon(X, i - 1, z, gaps, k2, l2, 0, b);
-        } else if (may_mis) {
-            inex_canon(X, i - 1, z - 1, gaps, k2, l2, 1, b);
+        const int64_t i = s.i;
+        /* the columns that may come next */
+        int ins_ok = s.gaps < X->max_gaps && ins_allowed(X, i);
+        int del_ok = s.gaps < X->max_gaps && del_allowed(X, i);
+        int mis_ok = 1, match_ok = 1, no_del_sym = -1;
+        if (canonical) {
+            del_ok = del_ok && s.z >= 1;
+            mis_ok = s.z >= 1;
+            if (s.last == 2) {
+                del_ok = 0;
+                mis_ok = 0;
+                if (W[i] == W[i + 1]) match_ok = 0;
+            } else if (s.last == 3) {
+                ins_ok = 0;
+                if (i >= 1) {
+                    mis_ok = 0;
+                    if (W[i] == s.lb) match_ok = 0;
+                }
+            } else if (s.last == 1) {
+                if (W[i] == s.lb) ins_ok = 0;
+                no_del_sym = W[i + 1];
+            }
+        }
+        if (ins_ok) st_push(&S, i - 1, s.z - 1, s.gaps + 1, s.k, s.l, 2, 0);
+        if (canonical && !del_ok && !mis_ok && !match_ok) continue;
+        X->nodes++;
+        X->blocks += (s.k / X->interval == (s.l + 1) / X->interval) ? 1 : 2;
+        int64_t nk[4], nl[4];
+        extend4(X->ix, s.k, s.l, nk, nl);
+        for (int b = 0; b < 4; ++b) {
+            if (nk[b] > nl[b]) continue; /* bX does not occur */
+            if (del_ok && b != no_del_sym) st_push(&S, i, s.z - 1, s.gaps + 1, nk[b], nl[b], 3, b);
+            if (b == W[i]) {
+                if (match_ok) st_push(&S, i - 1, s.z, s.gaps, nk[b], nl[b], 0, b);
+            } else if (mis_ok) {
+                st_push(&S, i - 1, s.z - 1, s.gaps, nk[b], nl[b], 1, b);
+            }
         }
     }
+    free(S.a);
 }
 
 /* order of (k, l, cost) triples; same_interval compares (k, l) only */
@@ -712,10 +744,7 @@ static void inex_one(void *a, int64_t q, int tid) {
     pairvec v = {NULL, 0, 0};
     inex_ctx X = {J->ix, W, D, J->max_gaps, J->prune & 1, J->interval, &v, 0, 0, J->z, m,
                   J->end_skip};
-    if (J->prune & 2)
-        inex_canon(&X, m - 1, J->z, 0, 0, J->ix->n, 0, 0);
-    else
-        inex_recur(&X, m - 1, J->z, 0, 0, J->ix->n);
+    inex_search(&X, (J->prune & 2) ? 1 : 0);
     if (v.size > 1) { /* sort and keep distinct intervals */
         /* each interval once, with the fewest differences any of its alignments used (the
          * first of its run after sorting by cost too) */

@@ -42,27 +42,27 @@ MUTANTS = [
      "    for (int64_t i = j * CK_STEP; i < p; ++i)\n        if (ix->L[i] < 4) out[ix->L[i]]++;",
      "    for (int64_t i = j * CK_STEP; i + 1 < p; ++i)\n        if (ix->L[i] < 4) out[ix->L[i]]++;"),
     ("mismatch not charged",
-     "            else\n                inex_recur(X, i - 1, z - 1, gaps, k2, l2);",
-     "            else\n                inex_recur(X, i - 1, z, gaps, k2, l2);"),
+     "st_push(&S, i - 1, s.z - 1, s.gaps, nk[b], nl[b], 1, b);",
+     "st_push(&S, i - 1, s.z, s.gaps, nk[b], nl[b], 1, b);"),
     ("deletion consumes a read symbol",
-     "del_allowed(X, i)) inex_recur(X, i, z - 1, gaps + 1, k2, l2);",
-     "del_allowed(X, i)) inex_recur(X, i - 1, z - 1, gaps + 1, k2, l2);"),
+     "st_push(&S, i, s.z - 1, s.gaps + 1, nk[b], nl[b], 3, b);",
+     "st_push(&S, i - 1, s.z - 1, s.gaps + 1, nk[b], nl[b], 3, b);"),
     ("insertion moves the interval",
-     "ins_allowed(X, i)) inex_recur(X, i - 1, z - 1, gaps + 1, k, l);",
-     "ins_allowed(X, i)) inex_recur(X, i - 1, z - 1, gaps + 1, k + 1, l);"),
-    ("gap cap off by one", "if (gaps < X->max_gaps && del_allowed(X, i)) inex_recur(X, i, z - 1,",
-     "if (gaps <= X->max_gaps && del_allowed(X, i)) inex_recur(X, i, z - 1,"),
-    ("empty-interval children kept", "        if (k2 <= l2) {\n            /* deletion",
-     "        if (k2 <= l2 + 1) {\n            /* deletion"),
-    ("prune too eagerly", "if (X->prune && i >= 0 && z < X->D[i]) return;",
-     "if (X->prune && i >= 0 && z <= X->D[i]) return;"),
-    ("prune with the wrong position", "if (X->prune && i >= 0 && z < X->D[i]) return;",
-     "if (X->prune && i >= 1 && z < X->D[i - 1]) return;"),
+     "st_push(&S, i - 1, s.z - 1, s.gaps + 1, s.k, s.l, 2, 0);",
+     "st_push(&S, i - 1, s.z - 1, s.gaps + 1, s.k + 1, s.l, 2, 0);"),
+    ("gap cap off by one", "int del_ok = s.gaps < X->max_gaps && del_allowed(X, i);",
+     "int del_ok = s.gaps <= X->max_gaps && del_allowed(X, i);"),
+    ("empty-interval children kept", "if (nk[b] > nl[b]) continue; /* bX does not occur */",
+     "if (nk[b] > nl[b] + 1) continue; /* bX does not occur */"),
+    ("prune too eagerly", "if (X->prune && s.i >= 0 && s.z < X->D[s.i]) continue;",
+     "if (X->prune && s.i >= 0 && s.z <= X->D[s.i]) continue;"),
+    ("prune with the wrong position", "if (X->prune && s.i >= 0 && s.z < X->D[s.i]) continue;",
+     "if (X->prune && s.i >= 1 && s.z < X->D[s.i - 1]) continue;"),
     ("no dedup of intervals", "    if (v.size > 1) { /* sort and keep distinct intervals */",
      "    if (0) { /* sort and keep distinct intervals */"),
     ("empty match reported",
-     "        if (k >= 1) pv_push(X->out, (uint32_t)k, (uint32_t)l, (uint32_t)(X->z0 - z));",
-     "        pv_push(X->out, (uint32_t)k, (uint32_t)l, (uint32_t)(X->z0 - z));"),
+     "if (s.k >= 1) pv_push(X->out, (uint32_t)s.k, (uint32_t)s.l, (uint32_t)(X->z0 - s.z));",
+     "pv_push(X->out, (uint32_t)s.k, (uint32_t)s.l, (uint32_t)(X->z0 - s.z));"),
     ("D window keeps the failing symbol", "            z++;\n            lo = 0;\n            hi = ix->n + 1;\n            d = 0;",
      "            z++;\n            lo = 0;\n            hi = ix->n + 1;\n            d = 0;\n            narrow(ix, &lo, &hi, 0, W[i]);\n            d = 1;"),
     ("D counts every failing extension twice", "            z++;\n            lo = 0;",
@@ -75,29 +75,30 @@ MUTANTS = [
      "            if (p + d >= n) { /* suffix reaches $ first: smaller */\n                rel = 1;"),
     ("hamming window inclusive bound", "        if (mm <= z) hits++;", "        if (mm < z) hits++;"),
     ("cost counts the differences left",
-     "        if (k >= 1) pv_push(X->out, (uint32_t)k, (uint32_t)l, (uint32_t)(X->z0 - z));",
-     "        if (k >= 1) pv_push(X->out, (uint32_t)k, (uint32_t)l, (uint32_t)z);"),
+     "if (s.k >= 1) pv_push(X->out, (uint32_t)s.k, (uint32_t)s.l, (uint32_t)(X->z0 - s.z));",
+     "if (s.k >= 1) pv_push(X->out, (uint32_t)s.k, (uint32_t)s.l, (uint32_t)s.z);"),
     ("dedup keeps an arbitrary cost", "    for (int t = 0; t < 3; ++t)\n        if (x[t] != y[t])",
      "    for (int t = 0; t < 2; ++t)\n        if (x[t] != y[t])"),
     ("canonical: no match after any insertion",
-     "        if (W[i] == W[i + 1]) may_match = 0;", "        may_match = 0;"),
+     "                if (W[i] == W[i + 1]) match_ok = 0;", "                match_ok = 0;"),
     ("canonical: mismatch allowed after an insertion",
-     "        may_del = 0;\n        may_mis = 0;\n", "        may_del = 0;\n"),
+     "                del_ok = 0;\n                mis_ok = 0;\n", "                del_ok = 0;\n"),
     ("canonical: deletion rule also at W[0]",
-     "        may_ins = 0;\n        if (i >= 1) {", "        may_ins = 0;\n        if (i >= 0) {"),
+     "                ins_ok = 0;\n                if (i >= 1) {",
+     "                ins_ok = 0;\n                if (i >= 0) {"),
     ("canonical: no insertion after any mismatch",
-     "        if (W[i] == lb) may_ins = 0;", "        may_ins = 0;"),
+     "                if (W[i] == s.lb) ins_ok = 0;", "                ins_ok = 0;"),
     ("canonical: pass-through call counted as a node",
-     "    if (!may_del && !may_mis && !may_match) return;\n", ""),
+     "        if (canonical && !del_ok && !mis_ok && !match_ok) continue;\n", ""),
     ("deletion not charged",
-     "del_allowed(X, i)) inex_recur(X, i, z - 1, gaps + 1, k2, l2);",
-     "del_allowed(X, i)) inex_recur(X, i, z, gaps + 1, k2, l2);"),
+     "st_push(&S, i, s.z - 1, s.gaps + 1, nk[b], nl[b], 3, b);",
+     "st_push(&S, i, s.z, s.gaps + 1, nk[b], nl[b], 3, b);"),
     ("insertion not charged",
-     "ins_allowed(X, i)) inex_recur(X, i - 1, z - 1, gaps + 1, k, l);",
-     "ins_allowed(X, i)) inex_recur(X, i - 1, z, gaps + 1, k, l);"),
+     "st_push(&S, i - 1, s.z - 1, s.gaps + 1, s.k, s.l, 2, 0);",
+     "st_push(&S, i - 1, s.z, s.gaps + 1, s.k, s.l, 2, 0);"),
     ("block count takes l instead of l+1",
-     "    X->blocks += (k / X->interval == (l + 1) / X->interval) ? 1 : 2;\n    const or_index *ix",
-     "    X->blocks += (k / X->interval == l / X->interval) ? 1 : 2;\n    const or_index *ix"),
+     "X->blocks += (s.k / X->interval == (s.l + 1) / X->interval) ? 1 : 2;",
+     "X->blocks += (s.k / X->interval == s.l / X->interval) ? 1 : 2;"),
     ("closed form: l misses the -1", "    J->l_out[q] = less + pre - 1;",
      "    J->l_out[q] = less + pre;"),
     ("closed form: Occ at l drops the matching rows",
