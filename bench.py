@@ -9,8 +9,10 @@ Beside it, in the same line:
   * the plain per-read kernel on the same batch (bit-exact comparison of the two);
   * best_hits: the same batch with per-interval minimum costs, keeping each query's best;
   * end_restricted: the same batch with indel columns kept 5 read symbols from either end;
-  * e2e: the same step through the C ABI with the reads in pinned host memory, the
-    host->device copy of the reads and the device->host copy of the interval sets timed;
+  * e2e: the same batch end to end through the C ABI with host buffers (fm_server_submit /
+    fm_server_poll: reads copied from host memory, interval sets read back to host memory),
+    and beside it the device-pointer call with torch copies of the reads in and the interval
+    sets out;
   * serving: mixed-mode requests on the resident index, offline and under Poisson arrivals;
   * locate: SA positions of 2^24 random rows (Eq. 4-5);
   * occ8: the Occ micro-benchmark, 2^28 eight-Occ queries on a 2 Gbp i.i.d. 41% GC index
@@ -85,11 +87,18 @@ def parse():
     ap.add_argument("--canonical", type=int, default=1, choices=[1, 2],
                     help="1: enumerate canonical alignments (same interval sets, fewer nodes); "
                          "2: every call of Listing 2")
-    ap.add_argument("--pair-steps", type=int, default=1, choices=[1, 2],
-                    help="1: exact continuations two symbols per step (pair table); 2: one")
-    ap.add_argument("--kmer-depth", type=int, default=0xFE,
+    ap.add_argument("--pair-steps", type=int, default=None, choices=[1, 2],
+                    help="1: exact continuations two symbols per step (pair table); 2: one "
+                         "(default: the autotuner's choice, else 1)")
+    ap.add_argument("--kmer-depth", type=int, default=None,
                     help="interval tables of short strings: 1..14 levels, 254 automatic "
-                         "(floor(log4(n+1)) - 2), 255 none")
+                         "(floor(log4(n+1)) - 2), 255 none (default: the autotuner's choice, "
+                         "else automatic)")
+    ap.add_argument("--refill", type=int, default=0,
+                    help="persistent kernel: take queries below this pool level (0: library)")
+    ap.add_argument("--chain2-min", type=int, default=0,
+                    help="persistent kernel: step second exact chains when this many lanes hold "
+                         "one (0: library default)")
     ap.add_argument("--tune-reads", type=int, default=200_000)
     ap.add_argument("--tune-cache", default=None, help="JSON cache of tuning results")
     ap.add_argument("--cpu-sample-reads", type=int, default=200_000)
@@ -198,6 +207,65 @@ def cpu_baseline(args):
             "seconds": dt, "nodes_per_read": float(res["nodes"].sum()) / len(reads)}
 
 
+def cpu_configs(args):
+    """The oracle timed on bounded samples of the other configurations, on one host thread and
+    on all of them (index builds not timed): exact search and fm_occ8-style queries of
+    config 1, the occ8 query mix of config 2 on a 32 Mbp reference of the same generator (the
+    oracle's index of 2 Gbp takes over ten minutes), config 3's read model, and a one-thread
+    sample of the main read model."""
+    import oracle
+    from paper_1811_06127_gb300 import synth
+    thr = oracle.default_threads()
+    out = {"cores": thr}
+
+    def timed(fn, n, unit, sample):
+        res = {"sample": sample, "unit": unit}
+        for name, t in (("one_thread", 1), ("all_cores", thr)):
+            t0 = time.perf_counter()
+            fn(t, n[name])
+            res[name] = n[name] / (time.perf_counter() - t0)
+        return res
+
+    R1 = synth.uniform_text(SEED_EXACT, 1_000_000)
+    ix1 = oracle.Index(R1, "sais")
+    rd1 = synth.exact_reads(SEED_EXACT, R1, 10_000, 32)
+    k1, l1 = synth.occ_queries_uniform(SEED_EXACT, R1.size, 1_000_000)
+    out["cfg1_exact"] = timed(lambda t, n: ix1.exact(rd1.codes, rd1.offs, threads=t),
+                              {"one_thread": 10_000, "all_cores": 10_000}, "reads/s",
+                              "config 1 in full: 10,000 reads of 32 bp on 1 Mbp")
+    out["cfg1_occ8"] = timed(lambda t, n: ix1.occ8(k1[:n], l1[:n], threads=t),
+                             {"one_thread": 1_000_000, "all_cores": 1_000_000}, "8-Occ/s",
+                             "config 1 in full: 10^6 queries on 1 Mbp")
+    R2 = synth.gc_text(SEED_OCC, 32_000_000, 0.41)
+    ix2 = oracle.Index(R2, "sais")
+    k2, l2 = synth.occ_queries_mixed(SEED_OCC, R2.size, 1 << 22, 64)
+    out["cfg2_occ8"] = timed(lambda t, n: ix2.occ8(k2[:n], l2[:n], threads=t),
+                             {"one_thread": 1 << 20, "all_cores": 1 << 22}, "8-Occ/s",
+                             "config 2's query mix on a 32 Mbp 41% GC reference: 2^20 queries "
+                             "(1 thread), 2^22 (all cores)")
+    del ix2, R2
+    R3 = synth.repeat_text(1811061273, 64_000_000)
+    ix3 = oracle.Index(R3, "sais")
+    rd3 = synth.sample_reads(1811061273, R3, 40_000, 100, 100, sub_rate=0.005,
+                             both_strands=True, random_frac=0.05)
+
+    def cfg3(t, n):
+        sub = rd3.subset(np.arange(n))
+        ix3.inexact(sub.codes, sub.offs, 2, 0, strands=2, threads=t)
+    out["cfg3_inexact"] = timed(cfg3, {"one_thread": 2_000, "all_cores": 40_000}, "reads/s",
+                                "config 3 in full size (64 Mbp), 2,000 reads (1 thread) and "
+                                "40,000 (all cores) of its 10^6")
+    del ix3, R3
+    ix4, rd4 = oracle_sample(args, 4_000, seed_off=1)
+    t0 = time.perf_counter()
+    ix4.inexact(rd4.codes, rd4.offs, 2, 1, strands=2, threads=1)
+    out["cfg4_inexact_one_thread"] = {"value": len(rd4) / (time.perf_counter() - t0),
+                                      "unit": "reads/s",
+                                      "sample": f"4,000 reads of the main read model on the "
+                                                f"{args.cpu_sample_ref} bp sample reference"}
+    return out
+
+
 def run_reference(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
@@ -294,10 +362,14 @@ def main():
     notes["build_s"] = time.time() - t0
     if tuned:
         autotune.apply(h, tuned)
-    fmocc.fm_set_tuning(h, canonical=args.canonical, kmer_depth=args.kmer_depth,
-                        pair_steps=args.pair_steps)
-    kdepth = fmocc.fm_get_tuning(h)["kmer_depth"]
+    fmocc.fm_set_tuning(h, canonical=args.canonical,
+                        kmer_depth=args.kmer_depth if args.kmer_depth is not None else 0,
+                        pair_steps=args.pair_steps if args.pair_steps is not None else 0,
+                        refill=args.refill, chain2_min=args.chain2_min)
+    tun = fmocc.fm_get_tuning(h)
+    kdepth = tun["kmer_depth"]
     kdepth = 0 if kdepth == fmocc.KMER_OFF else kdepth
+    args.pair_steps = tun["pair_steps"]
     del R
     codes_h = torch.from_numpy(reads.codes).pin_memory()
     offs_h = torch.from_numpy(reads.offs.view(np.int32)).pin_memory()
@@ -352,6 +424,22 @@ def main():
     alg_bytes = blocks_per_step * bbytes + tables_per_step * 32
     achieved = alg_bytes / (k_ms / 1000.0) / 1e9
     same = bool(torch.equal(p1, ref_pairs) and torch.equal(o1, ref_offsets))
+
+    # step fill of the persistent kernel: one more (untimed) search with its counters on
+    fprof = fmocc.fm_profile()
+    fprof.fill_counters = 1
+    search("persistent", pairs)
+    fmocc.fm_inexact(h, codes, offs, 2, 1, strands=2, counts=counts, offsets=offsets, pairs=pairs,
+                     profile=fprof)
+    fd = fprof.as_dict()
+    fill = {"exact_steps": fd["exact_steps"], "general_steps": fd["general_steps"],
+            "lanes_per_exact_step": (fd["exact_lanes"] + fd["exact_lanes2"]) / max(fd["exact_steps"], 1),
+            "first_chain_lanes_per_exact_step": fd["exact_lanes"] / max(fd["exact_steps"], 1),
+            "lanes_per_general_step": fd["general_lanes"] / max(fd["general_steps"], 1),
+            "queries_per_admission": fd["admitted"] / max(fd["admissions"], 1),
+            "exact_steps_with_parked_second_chains": fd["parked"],
+            "note": "exact steps run up to two chains per lane (64 per warp step); general "
+                    "steps up to 32 nodes"}
 
     # ---- plain per-read kernel on the same batch ----------------------------------------
     plain = None
@@ -456,6 +544,7 @@ def main():
                "h2d_bytes_per_step": codes_h.numel() + offs_h.numel() * 4,
                "d2h_bytes_per_step": int(d2h), "wall_s": time.perf_counter() - t0}
     serving = None if args.skip_serving else bench_serving(args, fmocc, h, reads)
+    e2e_abi = None if args.skip_e2e else bench_e2e_serving_abi(args, fmocc, h, reads, world)
     ceil_main = gather_ceiling(torch, fmocc, dev, fmocc.fm_info(h)["n_blocks"] * bbytes, flush)
     locate = bench_locate(args, torch, fmocc, h, dev, flush)
     h.close()
@@ -472,9 +561,10 @@ def main():
     cfg3 = None if args.skip_cfg3 else bench_cfg3(args, torch, fmocc, synth, dev, flush, barrier,
                                                    hbm_peak)
 
-    cpu = None
+    cpu = cpu_cfg = None
     if not args.skip_cpu and rank == 0 and world == 1:
         cpu = cpu_baseline(args)
+        cpu_cfg = cpu_configs(args)
 
     traffic_key = (args.interval, args.ref_n, args.reads, args.canonical == 1, kdepth,
                    args.pair_steps == 1)
@@ -496,9 +586,13 @@ def main():
                                        if kdepth else "none"),
                    "reference_bp": args.ref_n, "reads_per_step": args.reads,
                    "queries_per_step": nq, "interval": args.interval,
-                   "tuning": ({k: tuned[k] for k in ("interval", "warps_per_block",
-                                                      "blocks_per_sm", "chunk", "trials",
-                                                      "tune_seconds")} if tuned else None),
+                   "tuning": ({k: tuned.get(k) for k in ("interval", "warps_per_block",
+                                                          "blocks_per_sm", "chunk", "kmer_depth",
+                                                          "pair_steps", "trials", "tune_seconds",
+                                                          "cached")} if tuned else None),
+                   "scheduler": {k: tun[k] for k in ("warps_per_block", "blocks_per_sm", "chunk",
+                                                     "refill", "chain2_min", "kmer_depth",
+                                                     "pair_steps")},
                    "parallelism": f"replicas x{world} (read sharding)",
                    "l2": (f"flushed between timed steps ({flush_bytes >> 20} MB write; L2 "
                           f"{l2_bytes >> 20} MB read from the device); index 2x1 GB > L2")},
@@ -514,8 +608,14 @@ def main():
                                        "dram.md"}),
                      "kernel": "k_inexact_persistent", "kernel_ms": k_ms,
                      "gather_ceiling": ceil_main,
-                     "blocks_per_s_over_gather_ceiling": (blocks_per_step / (k_ms / 1000) / 1e9
-                                                          / ceil_main["g_gathers_s"]),
+                     # every 32-byte unit the kernel gathers (checkpoint blocks and table or pair
+                     # sectors) per second, over the live random 32-byte gather ceiling; above 1
+                     # where shallow table sectors hit in L2
+                     "gathers_per_s_over_gather_ceiling": (
+                         (blocks_per_step * bbytes / 32 + tables_per_step) / (k_ms / 1000) / 1e9
+                         / ceil_main["g_gathers_s"]),
+                     "checkpoint_blocks_per_s_over_gather_ceiling": (
+                         blocks_per_step / (k_ms / 1000) / 1e9 / ceil_main["g_gathers_s"]),
                      "algorithmic_bytes": alg_bytes, "peak_kind": peak_kind,
                      "per_unit": f"{bbytes} B per checkpoint block read and 32 B per "
                                  f"interval-table or pair-table sector read; "
@@ -527,12 +627,15 @@ def main():
         "search": {"nodes_per_step": nodes_per_step, "blocks_per_step": blocks_per_step,
                    "table_sectors_per_step": tables_per_step,
                    "intervals_per_step": int(ref_offsets[-1].item()),
-                   "bit_exact_repeat": same, "step_ms": step_ms,
+                   "bit_exact_repeat": same, "step_ms": step_ms, "fill": fill,
                    "profile_last": prof.as_dict()},
         "plain": plain,
         "best_hits": best,
         "end_restricted": endr,
-        "e2e": e2e,
+        # end to end through the C ABI with host buffers (the serving calls); the device-pointer
+        # call with torch copies of the same batch beside it
+        "e2e": e2e_abi,
+        "e2e_device_api_with_copies": e2e,
         "occ8": occ8,
         "exact": exact,
         "inexact_64mbp": cfg3,
@@ -540,6 +643,7 @@ def main():
         "serving": serving,
         "locate": locate,
         "cpu_baseline": cpu,
+        "cpu_baseline_configs": cpu_cfg,
         "setup": notes,
     }
     if rank == 0:
@@ -684,6 +788,35 @@ def bench_locate(args, torch, fmocc, h, dev, flush):
     st = int(steps.item()) / 3
     return {"rows": 1 << 24, "rows_per_s": (1 << 24) / t, "ms": t * 1000,
             "steps_per_row": st / (1 << 24), "steps_per_s": st / t}
+
+
+def bench_e2e_serving_abi(args, fmocc, h, reads, world):
+    """The main batch end to end through the host-buffer serving ABI: the 10^7 reads submitted
+    from host memory as requests of the server's maximum batch (fm_server_submit copies them),
+    searched by the server's workers (two batches in flight), and every result read back to host
+    memory (fm_server_poll); timed from the first submission to the last result."""
+    chunk = 262_144
+    nr = len(reads)
+    with fmocc.Server(h, max_batch_reads=chunk, strands=2) as srv:
+        # one untimed request sizes the workers' buffers and scratch
+        w = reads.subset(np.arange(min(chunk, nr)))
+        srv.wait(srv.submit(w.codes, w.offs, 2, 1))
+        t0 = time.perf_counter()
+        tickets = []
+        for a in range(0, nr, chunk):
+            b = min(nr, a + chunk)
+            offs = reads.offs[a:b + 1]
+            tickets.append(srv.submit(reads.codes[offs[0]:offs[-1]], offs - offs[0], 2, 1))
+        d2h = 0
+        for t in tickets:
+            r = srv.wait(t)
+            d2h += r["counts"].nbytes + r["offsets"].nbytes + r["pairs"].nbytes
+        dt = time.perf_counter() - t0
+    return {"value": nr * world / dt, "unit": "reads/s", "seconds": dt,
+            "h2d_bytes_per_step": int(reads.codes.nbytes + reads.offs.nbytes),
+            "d2h_bytes_per_step": int(d2h),
+            "what": f"fm_server_submit/poll with host buffers, {len(tickets)} requests of up to "
+                    f"{chunk} reads, z=2 with 1 gap, both strands; host clock"}
 
 
 def bench_serving(args, fmocc, h, reads):

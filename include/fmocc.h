@@ -141,7 +141,10 @@ int fm_exact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n
              uint32_t *k_out, uint32_t *l_out, void *stream);
 
 /* Per-call profile of fm_inexact (optional): phase times from CUDA events recorded on the
- * call's stream around the library's own launches, and the number of kernels launched. */
+ * call's stream around the library's own launches, and the number of kernels launched.
+ * With fill_counters set to 1 by the caller (an input; the call keeps it), the persistent
+ * kernel also counts how full its warp steps were (measurement only, no counterpart in the
+ * paper; the counting adds a few instructions per step). */
 typedef struct fm_profile {
     float ms_dcalc;    /* D lower bound (one launch) */
     float ms_search;   /* the search kernel (last pass when scratch had to be regrown) */
@@ -150,7 +153,15 @@ typedef struct fm_profile {
     uint32_t launches; /* kernels launched by the call */
     uint32_t passes;   /* search passes (1 unless scratch was regrown) */
     uint32_t graph;    /* 1 when the call replayed a captured CUDA graph, 0 when eager */
-    uint32_t reserved;
+    uint32_t fill_counters; /* in: 1 to collect the counters below (persistent kernel) */
+    uint64_t exact_steps;   /* warp steps over exact continuations (z = 0 chains) */
+    uint64_t exact_lanes;   /*   lanes stepping their first chain, summed over those steps */
+    uint64_t exact_lanes2;  /*   lanes stepping their second chain, summed */
+    uint64_t general_steps; /* warp steps of the full eight-Occ expansion */
+    uint64_t general_lanes; /*   lanes expanding a node, summed */
+    uint64_t admissions;    /* chunks of queries taken from the work queue */
+    uint64_t admitted;      /* queries admitted with a root node (length >= 1, z >= D) */
+    uint64_t parked;        /* exact steps in which sparse second chains waited */
 } fm_profile;
 
 /* Locate (Sec. 2, Eq. 4-5): pos_out[q] = SA[rows[q]], the text position of the suffix in
@@ -269,23 +280,30 @@ int fm_inexact_noalloc(fm_index *h, const uint8_t *reads, const uint32_t *offs, 
 /* ------------------------------------------------------------------------------------------
  * Serving: a request loop over a resident index (the paper has no serving layer; it states the
  * search per read, Listing 1 and Listing 2, and this loop runs those searches for a stream of
- * requests).  A server thread owned by the library keeps the index resident and forms device
- * batches continuously: requests that arrive while a batch is on the GPU wait in a FIFO and
- * are admitted into the next batch as its read slots and device-memory budget allow; one batch
- * holds requests of one search mode (z, max_gaps), and requests of any size share it (their
- * queries run together in the persistent kernel).  Each request's result is exactly what
- * fm_inexact returns for that request alone.  While a server runs, no other call may use its
- * index handle.
+ * requests).  Continuous batching with several batches in flight: the server runs `inflight`
+ * worker threads, each with its own search scratch, stream and batch buffers on the same
+ * resident index.  A worker that is free takes the pending requests in arrival order, of any
+ * search mode (z, max_gaps are carried read by read), while their reads fit the batch's read
+ * slots and the worker's share of the frontier budget, and searches them as one batch.  A
+ * request that arrives while a batch is on the GPU starts as soon as a worker is free, while
+ * that batch is still running, and the two batches overlap on the device.  Each request's
+ * result is exactly what fm_inexact returns for that request alone.  While a server runs, no
+ * other call may use its index handle.
  * ---------------------------------------------------------------------------------------- */
 typedef struct fm_server fm_server;
 
 typedef struct fm_server_params {
     uint32_t max_batch_reads; /* read slots per device batch (0: 262,144) */
     uint32_t strands;         /* 1 or 2, for every request */
-    uint64_t frontier_budget; /* device bytes the search scratch of one batch may use
-                                 (0: 64 GiB); bounds the reads admitted per batch */
+    uint64_t frontier_budget; /* device bytes the search scratch of the batches in flight may
+                                 use together (0: 64 GiB), shared equally by the workers: a
+                                 worker sizes each batch by a model of the scratch its search
+                                 allocates (raw intervals per query learned from its batches);
+                                 a search that would still grow past the worker's share fails
+                                 that growth and the batch is split in two (a single request
+                                 that does not fit finishes with FM_ENOMEM) */
     uint32_t kernel;          /* FM_KERNEL_* */
-    uint32_t reserved;
+    uint32_t inflight;        /* batches in flight, one worker thread each (0: 2; at most 4) */
 } fm_server_params;
 
 /* Result of one request, owned by the server until fm_server_release. */
@@ -299,7 +317,7 @@ typedef struct fm_server_result {
     uint64_t t_start_ns;
     uint64_t t_done_ns;
     uint32_t batch_reads;    /* reads in the batch that held the request */
-    uint32_t reserved;
+    uint32_t batch_id;       /* the batch that held it (1, 2, ... in order of completion) */
 } fm_server_result;
 
 /* Start the server thread on h (serving: no counterpart in the paper; every request runs the
@@ -323,7 +341,8 @@ int fm_server_poll(fm_server *s, uint64_t ticket, uint32_t wait_ms, fm_server_re
 int fm_server_release(fm_server *s, uint64_t ticket);
 
 /* Serving counters (no counterpart in the paper): batches run, reads searched, requests
- * finished, GPU busy milliseconds. */
+ * finished, and the milliseconds the batches took, summed over the workers (batches in
+ * flight together count once each). */
 int fm_server_stats(fm_server *s, uint64_t out[4]);
 
 /* Finish the queued requests, stop the thread and free the server (results not released are
@@ -386,6 +405,20 @@ typedef struct fm_tuning {
                                    and results are unchanged; an inexact search's stats[0] then
                                    omits the middle node of a two-symbol step that ends the
                                    branch.  2: one symbol per step (stats exactly as described) */
+    uint32_t refill;            /* persistent kernel: a warp takes more queries from the work
+                                   queue when its node pools hold fewer nodes than this
+                                   (1..288; default 32) */
+    uint32_t chain2_min;        /* persistent kernel: each lane holds up to two exact chains;
+                                   the warp steps the second ones only while at least this many
+                                   lanes hold one, else they wait for a first place (1..32;
+                                   default 1: always) */
+    uint32_t stage;             /* persistent kernel: 1 stages each query a warp works on in
+                                   shared memory (its 2-bit symbols, D breakpoints, length, mode
+                                   and number; 16 slots per warp, taken and freed in groups of
+                                   4); 2 (default) reads them through L1 from device memory,
+                                   which measured faster on GB300: staging bounds the queries a
+                                   warp holds at once, and its expansions run fewer nodes per
+                                   step.  Results are the same either way */
 } fm_tuning;
 
 #define FM_KMER_AUTO 0xfeu

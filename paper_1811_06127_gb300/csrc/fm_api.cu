@@ -134,6 +134,48 @@ void release(fm_index *h) {
     delete h;
 }
 
+}  // namespace
+
+fm_index *new_search_context(fm_index *h) {
+    fm_index *c = new fm_index(*h);
+    c->borrowed = true;
+    c->err.clear();
+    fm::Scratch *ss[] = {&c->s_qmeta, &c->s_raw, &c->s_spill, &c->s_group, &c->s_scan, &c->s_plain,
+                         &c->s_misc};
+    for (auto *sc : ss) *sc = fm::Scratch{};
+    c->scratch_budget = 0;
+    c->d_err = nullptr;
+    c->last_valid = false;
+    c->cap_stream = nullptr;
+    c->gexec = nullptr;
+    c->gkey = fm::GraphKey{};
+    for (auto &e : c->gev) e = nullptr;
+    c->graph_replays = c->graph_captures = 0;
+    DeviceGuard g(h->device);
+    if (alloc_common(c) != FM_OK) {
+        cudaFree(c->d_err);
+        delete c;
+        return nullptr;
+    }
+    return c;
+}
+
+void free_search_context(fm_index *c) {
+    if (!c || !c->borrowed) return;
+    DeviceGuard g(c->device);
+    cudaFree(c->d_err);
+    fm::Scratch *ss[] = {&c->s_qmeta, &c->s_raw, &c->s_spill, &c->s_group, &c->s_scan, &c->s_plain,
+                         &c->s_misc};
+    for (auto *sc : ss) cudaFree(sc->ptr);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (auto &e : c->gev)
+        if (e) cudaEventDestroy(e);
+    delete c;
+}
+
+namespace {
+
 // the context's L2 fetch granularity, when the tuning asks for one
 void apply_l2(fm_index *h) {
     if (h->tune.l2_fetch) {
@@ -517,6 +559,9 @@ int fm_set_tuning(fm_index *h, const fm_tuning *t) {
     if (t->pair_steps > 2) return set_error(h, FM_EINVAL, "pair_steps must be 0, 1 or 2");
     if (t->kmer_depth > fm::kMaxKmerDepth && t->kmer_depth != FM_KMER_AUTO && t->kmer_depth != FM_KMER_OFF)
         return set_error(h, FM_EINVAL, "kmer_depth must be 0, 1..14, FM_KMER_AUTO or FM_KMER_OFF");
+    if (t->refill > 288) return set_error(h, FM_EINVAL, "refill must be 0..288");
+    if (t->chain2_min > 32) return set_error(h, FM_EINVAL, "chain2_min must be 0..32");
+    if (t->stage > 2) return set_error(h, FM_EINVAL, "stage must be 0, 1 or 2");
     if (t->warps_per_block) h->tune.warps_per_block = t->warps_per_block;
     if (t->blocks_per_sm) h->tune.blocks_per_sm = t->blocks_per_sm;
     if (t->chunk) h->tune.chunk = t->chunk;
@@ -527,6 +572,9 @@ int fm_set_tuning(fm_index *h, const fm_tuning *t) {
     if (t->kmer_depth) h->tune.kmer = t->kmer_depth;
     if (t->pair_steps) h->tune.pairs = t->pair_steps == 1 ? 1u : 0u;
     if (t->graphs) h->use_graphs = t->graphs == 1;
+    if (t->refill) h->tune.refill = t->refill;
+    if (t->chain2_min) h->tune.chain2_min = t->chain2_min;
+    if (t->stage) h->tune.stage = t->stage == 1 ? 1u : 0u;
     return FM_OK;
 }
 
@@ -544,6 +592,9 @@ int fm_get_tuning(const fm_index *h, fm_tuning *t) {
     const uint32_t kd = fm::kmer_depth_for(h);
     t->kmer_depth = kd ? kd : FM_KMER_OFF;
     t->pair_steps = h->tune.pairs ? 1u : 2u;
+    t->refill = h->tune.refill;
+    t->chain2_min = h->tune.chain2_min;
+    t->stage = h->tune.stage ? 1u : 2u;
     return FM_OK;
 }
 

@@ -22,8 +22,11 @@
 //     in shared memory, pops up to 32 of them per step (one per lane), expands them, and
 //     pushes the surviving children back with a warp-ballot/shuffle prefix sum.  When its pool
 //     runs low the warp takes the next chunk of queries from a device work queue (an atomic
-//     counter); when the pool would overflow it spills to a per-warp region of device memory.
-//     A warp leaves when the queue is drained and its pool and spill are empty.
+//     counter) and stages each of them in a shared-memory slot (the query's 2-bit symbols,
+//     oriented for its strand, its D breakpoints and length), so that no expansion reads
+//     query data from device memory; when the pool would overflow it spills to a per-warp
+//     region of device memory.  A warp leaves when the queue is drained and its pool and spill
+//     are empty.
 // Leaves are appended to a raw result buffer (warp-aggregated atomics).  The raw results are
 // then grouped by query, sorted and deduplicated (canonical sets, Listing 2's set union), and
 // compacted into the caller's counts/offsets/pairs.
@@ -39,7 +42,7 @@ constexpr uint32_t FULL = 0xffffffffu;
 struct SearchCfg {
     IndexView ix;
     const uint8_t *reads;
-    const uint4 *qmeta;
+    const uint4 *qmeta;          // plain kernel: one uint4 per query; persistent: kStageU4
     uint32_t nq;
     uint32_t z, max_gaps;
     uint32_t chunk;
@@ -51,6 +54,9 @@ struct SearchCfg {
     uint32_t *err;
     uint32_t canon;              // enumerate canonical alignments only (see expand)
     uint32_t end_skip;           // indel columns need this many read symbols on each side
+    uint32_t refill;             // persistent: take queries when the pools hold fewer nodes
+    uint32_t chain2_min;         // persistent: step second exact chains when this many are live
+    unsigned long long *fill;    // persistent: step-fill counters (kFillCounters), or null
 };
 
 // The canonical rewrites move indel columns across read positions, so under an end
@@ -67,8 +73,78 @@ __device__ __forceinline__ uint32_t d_at(const uint4 &mt, int i) {
 
 __device__ __forceinline__ uint32_t w_at(const uint8_t *reads, const uint4 &mt, uint32_t i) {
     const uint32_t m = mt.w & 255u;
-    if (mt.w >> 8) return 3u - reads[mt.z + m - 1u - i];
+    if ((mt.w >> 8) & 1u) return 3u - reads[mt.z + m - 1u - i];   // bit 8: the strand
     return reads[mt.z + i];
+}
+
+// A query as the node expansion sees it: W[i] (oriented for the query's strand), D(i) and the
+// length m.  GQuery reads the concatenated reads in device memory and the query's metadata
+// word (plain kernel); SQuery reads the query's shared-memory slot (persistent kernel).
+struct GQuery {
+    const uint8_t *reads;
+    uint4 mt;
+    __device__ __forceinline__ uint32_t w(uint32_t i) const { return w_at(reads, mt, i); }
+    __device__ __forceinline__ uint32_t d(int i) const { return d_at(mt, i); }
+    __device__ __forceinline__ uint32_t len() const { return mt.w & 255u; }
+    __device__ __forceinline__ uint32_t z0() const { return (mt.w >> 16) & 15u; }
+    __device__ __forceinline__ uint32_t gaps() const { return (mt.w >> 20) & 15u; }
+};
+
+// Shared-memory query slots of the persistent kernel (with staging): kSlots per warp, in
+// kGroups groups of kGroupSlots, kSlotWords words each: words 0-15 the query's symbols, W[i]
+// at bits 2(i%16) of word i/16; words 16-17 its D breakpoints; word 18 its length m (bits
+// 0-7) and its search mode (bits 16-19 the differences allowed, 20-23 the indel columns
+// allowed); word 19 the query number.  A node carries its query's slot in bits 25-29 of its
+// state word.  The 80-byte stride keeps each slot 16-byte aligned and spreads the slots of 8
+// lanes over distinct banks.
+constexpr int kGroupSlots = 4;
+constexpr int kGroups = 4;
+constexpr int kSlots = kGroups * kGroupSlots;
+constexpr int kSlotWords = 20;
+constexpr uint32_t kSlotShift = 25u;
+constexpr uint32_t kSlotBits = 31u << kSlotShift;
+constexpr int kFillCounters = 8;
+static_assert(kSlots <= 32, "a node holds a 5-bit slot");
+__device__ __forceinline__ uint32_t slot_of(const uint4 &nd) { return (nd.y >> kSlotShift) & 31u; }
+
+struct SQuery {
+    const uint32_t *s;
+    __device__ __forceinline__ uint32_t w(uint32_t i) const { return (s[i >> 4] >> (2u * (i & 15u))) & 3u; }
+    __device__ __forceinline__ uint32_t d(int i) const { return d_at(make_uint4(s[16], s[17], 0u, 0u), i); }
+    __device__ __forceinline__ uint32_t len() const { return s[18] & 255u; }
+    __device__ __forceinline__ uint32_t z0() const { return (s[18] >> 16) & 15u; }
+    __device__ __forceinline__ uint32_t gaps() const { return (s[18] >> 20) & 15u; }
+    __device__ __forceinline__ uint32_t q() const { return s[19]; }
+};
+
+// The node pools of one warp: stk entries.  Without staging a node is one uint4 (query number,
+// state word, k, l); with staging the query number lives in the node's slot and the pools keep
+// three 32-bit arrays (state word, k, l), 12 bytes per node, so that the pools and the slots
+// of a warp together take the 16-byte pools' shared memory.
+template <bool STAGE>
+struct Pool;
+template <>
+struct Pool<false> {
+    uint4 *e;
+    __device__ __forceinline__ uint4 get(int t) const { return e[t]; }
+    __device__ __forceinline__ void put(int t, const uint4 &v) const { e[t] = v; }
+    static constexpr int kWords = 4;   // per entry
+};
+template <>
+struct Pool<true> {
+    uint32_t *y, *k, *l;
+    __device__ __forceinline__ uint4 get(int t) const { return make_uint4(0u, y[t], k[t], l[t]); }
+    __device__ __forceinline__ void put(int t, const uint4 &v) const {
+        y[t] = v.y;
+        k[t] = v.z;
+        l[t] = v.w;
+    }
+    static constexpr int kWords = 3;
+};
+
+// 32-bit words of shared memory per warp of the persistent kernel
+__host__ __device__ constexpr int warp_smem_words(int stk, bool stage, bool fill) {
+    return stk * (stage ? 3 : 4) + (stage ? kSlots * kSlotWords : 0) + (fill ? kFillCounters : 0);
 }
 
 // Node word y: bits 0-7 i, 8-11 z left, 12-15 indel columns used, 16-17 the operation that
@@ -112,8 +188,8 @@ __device__ __forceinline__ unsigned long long step_cost(uint32_t nb) {
 // A node none of whose Occ children is allowed takes no Occ step and is not counted; a child
 // that could take no step at all is not created.  The rewrites move indel columns, so they
 // are not applied together with an end restriction (the host clears canon).
-template <int I>
-__device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, const uint4 &mt,
+template <int I, class Q>
+__device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, const Q &qv,
                                        uint32_t k2[4], uint32_t l2[4], uint32_t &push,
                                        uint32_t &leaf, uint32_t &nblocks, uint32_t &counted,
                                        uint32_t &wi_out) {
@@ -121,7 +197,7 @@ __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, cons
     const uint32_t z = (nd.y >> 8) & 15u;
     const uint32_t g = (nd.y >> 12) & 15u;
     const uint32_t k = nd.z, l = nd.w;
-    const uint32_t wi = w_at(c.reads, mt, (uint32_t)i);
+    const uint32_t wi = qv.w((uint32_t)i);
     wi_out = wi;
     bool ins_r = true, mis_r = true, del_r = true, match_r = true;
     uint32_t del_keep = 0xfu;
@@ -129,7 +205,7 @@ __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, cons
     if (c.canon) {
         const uint32_t op = (nd.y >> 16) & 3u, pb = (nd.y >> 18) & 3u;
         if (op == kOpIns || op == kOpMis) {
-            const uint32_t wn = w_at(c.reads, mt, (uint32_t)i + 1u);
+            const uint32_t wn = qv.w((uint32_t)i + 1u);
             if (op == kOpIns) {
                 del_r = false;
                 mis_r = false;
@@ -145,17 +221,18 @@ __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, cons
                 match_r = wi != pb;
             }
         }
-        if (i >= 1) wp = w_at(c.reads, mt, (uint32_t)i - 1u);
+        if (i >= 1) wp = qv.w((uint32_t)i - 1u);
     }
     if (c.end_skip) {
-        const uint32_t m = mt.w & 255u, e = c.end_skip;
+        const uint32_t m = qv.len(), e = c.end_skip;
         if ((uint32_t)i < e || (uint32_t)i + e >= m) ins_r = false;
         if ((uint32_t)i + 1u < e || (uint32_t)i + e >= m) del_r = false;
     }
-    const bool gap_ok = z >= 1u && g < c.max_gaps;
+    const uint32_t max_gaps = qv.gaps();
+    const bool gap_ok = z >= 1u && g < max_gaps;
     const bool need = (gap_ok && del_r) || (z >= 1u && mis_r) || match_r;
     // a new indel child can take another indel only with a gap and a difference to spare
-    const bool more_gaps = g + 1u < c.max_gaps && z >= 2u;
+    const bool more_gaps = g + 1u < max_gaps && z >= 2u;
     const bool shallow = (nd.y & kShallow) != 0u;
     const uint32_t d = (nd.y >> 20) & 15u;
     uint32_t alive = 0;   // bit b: the child string bX occurs
@@ -199,8 +276,8 @@ __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, cons
             alive |= (k2[b] <= l2[b] ? 1u : 0u) << b;
         }
     }
-    const uint32_t d_here = d_at(mt, i);
-    const uint32_t d_next = d_at(mt, i - 1);
+    const uint32_t d_here = qv.d(i);
+    const uint32_t d_next = qv.d(i - 1);
     const bool del_ok = gap_ok && del_r && z - 1u >= d_here;
     const bool last = i == 0;
     push = 0;
@@ -236,16 +313,16 @@ __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, cons
 // so the eight-Occ step reduces to rank(W[i], k) and rank(W[i], l+1), i.e. one step of
 // Listing 1.  The single child replaces the node (out), or the interval is a result (leaf at
 // i = 0), or the branch ends (empty interval).  The child needs no D test: every node is
-// created with z >= D(i), D never decreases with i, so here D(i-1) <= D(i) = 0.  Only mt.z
-// and mt.w (read start, length and strand) are used.
-template <int I>
-__device__ __forceinline__ void exact_step(const SearchCfg &c, const uint4 &nd, const uint4 &mt,
+// created with z >= D(i), D never decreases with i, so here D(i-1) <= D(i) = 0.  Only the
+// query's symbols are used.
+template <int I, class Q>
+__device__ __forceinline__ void exact_step(const SearchCfg &c, const uint4 &nd, const Q &qv,
                                            uint4 &out, bool &survive, bool &is_leaf,
                                            uint32_t &nblocks) {
     const uint32_t i = nd.y & 255u;
-    const uint32_t b = w_at(c.reads, mt, i);
+    const uint32_t b = qv.w(i);
     const uint32_t k = nd.z, l = nd.w;
-    uint32_t k2 = 0u, l2 = 0u, ybits = nd.y & 0xf000u;   // z = 0, created by a match
+    uint32_t k2 = 0u, l2 = 0u, ybits = nd.y & (0xf000u | kSlotBits);   // z = 0, created by a match
     bool alive;
     if (nd.y & kShallow) {
         const uint32_t d = (nd.y >> 20) & 15u, code = 4u * k + b;
@@ -290,12 +367,12 @@ __device__ __forceinline__ void exact_step(const SearchCfg &c, const uint4 &nd, 
 // interval of two single steps, both of whose nodes are counted (nn = 2); when empty the
 // branch ends either way and only this node is counted (the middle one may or may not have
 // been non-empty).  Sectors read go to the table-sector field of nblocks.
-template <int I>
-__device__ __forceinline__ void pair_step(const SearchCfg &c, const uint4 &nd, const uint4 &mt,
+template <int I, class Q>
+__device__ __forceinline__ void pair_step(const SearchCfg &c, const uint4 &nd, const Q &qv,
                                           uint4 &out, bool &survive, bool &is_leaf,
                                           uint32_t &nblocks, uint32_t &nn) {
     const uint32_t i = nd.y & 255u;
-    const uint32_t b2 = w_at(c.reads, mt, i), b1 = w_at(c.reads, mt, i - 1u);
+    const uint32_t b2 = qv.w(i), b1 = qv.w(i - 1u);
     const uint32_t pc = 4u * b1 + b2, pk = nd.z, pl = nd.w + 1u;
     const uint32_t jk = pk / kPairRows, jl = pl / kPairRows;
     const uint32_t c2 = __ldg(c.ix.pc2 + pc);
@@ -310,18 +387,18 @@ __device__ __forceinline__ void pair_step(const SearchCfg &c, const uint4 &nd, c
     nn = alive ? 2u : 1u;
     is_leaf = alive && i == 1u;
     survive = alive && i >= 2u;
-    out = make_uint4(nd.x, (i - 2u) | (nd.y & 0xf000u), k2, l2);
+    out = make_uint4(nd.x, (i - 2u) | (nd.y & (0xf000u | kSlotBits)), k2, l2);
 }
 
 // an exact continuation: two symbols from the pair table where it applies, else one
-template <int I>
-__device__ __forceinline__ void chain_step(const SearchCfg &c, const uint4 &nd, const uint4 &mt,
+template <int I, class Q>
+__device__ __forceinline__ void chain_step(const SearchCfg &c, const uint4 &nd, const Q &qv,
                                            uint4 &out, bool &survive, bool &is_leaf,
                                            uint32_t &nblocks, uint32_t &nn) {
     if (c.ix.pairs && !(nd.y & kShallow) && (nd.y & 255u) >= 1u) {
-        pair_step<I>(c, nd, mt, out, survive, is_leaf, nblocks, nn);
+        pair_step<I>(c, nd, qv, out, survive, is_leaf, nblocks, nn);
     } else {
-        exact_step<I>(c, nd, mt, out, survive, is_leaf, nblocks);
+        exact_step<I>(c, nd, qv, out, survive, is_leaf, nblocks);
         nn = 1u;
     }
 }
@@ -338,12 +415,13 @@ __device__ __forceinline__ uint4 make_child(const uint4 &nd, int t, const uint32
     const uint32_t g = (nd.y >> 12) & 15u;
     const uint32_t d = (nd.y >> 20) & 15u;
     // a child one symbol longer stays shallow below the table depth
-    const uint32_t sh = ((nd.y & kShallow) && d + 1u < kdepth) ? (kShallow | ((d + 1u) << 20)) : 0u;
+    const uint32_t sh = (((nd.y & kShallow) && d + 1u < kdepth) ? (kShallow | ((d + 1u) << 20)) : 0u) |
+                        (nd.y & kSlotBits);
     uint4 ch;
     ch.x = nd.x;
     if (t == 0) {
         ch.y = (i - 1u) | ((z - 1u) << 8) | ((g + 1u) << 12) | (kOpIns << 16) |
-               (nd.y & (kShallow | kDepthBits));
+               (nd.y & (kShallow | kDepthBits | kSlotBits));
         ch.z = nd.z;
         ch.w = nd.w;
     } else if (t <= 4) {
@@ -375,9 +453,10 @@ __device__ __forceinline__ uint2 leaf_of(const SearchCfg &c, const uint4 &nd, in
 __device__ __forceinline__ uint4 root_of(const SearchCfg &c, uint32_t q, const uint4 &mt,
                                          bool &ok) {
     const uint32_t m = mt.w & 255u;
-    ok = m >= 1u && c.z >= d_at(mt, (int)m - 1);
-    if (c.ix.kdepth) return make_uint4(q, (m - 1u) | (c.z << 8) | kShallow, 0u, 0u);   // X empty
-    return make_uint4(q, (m - 1u) | (c.z << 8), 0u, c.ix.n);
+    const uint32_t z0 = (mt.w >> 16) & 15u;   // the query's differences allowed
+    ok = m >= 1u && z0 >= d_at(mt, (int)m - 1);
+    if (c.ix.kdepth) return make_uint4(q, (m - 1u) | (z0 << 8) | kShallow, 0u, 0u);   // X empty
+    return make_uint4(q, (m - 1u) | (z0 << 8), 0u, c.ix.n);
 }
 
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
@@ -389,10 +468,12 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
     return v;
 }
 
-// append this warp's leaves to the raw buffer: (query, k, l, differences used)
+// append this warp's leaves to the raw buffer: (query, k, l, differences used); z0 is the
+// query's differences allowed, q its number
 __device__ __forceinline__ void emit_leaves(const SearchCfg &c, int lane, bool act,
                                             const uint4 &nd, uint32_t leaf, const uint32_t k2[4],
-                                            const uint32_t l2[4], uint32_t wi) {
+                                            const uint32_t l2[4], uint32_t wi, uint32_t z0,
+                                            uint32_t q) {
     if (!__any_sync(FULL, act && leaf != 0u)) return;
     const int lc = act ? __popc(leaf) : 0;
     const int incl = warp_incl_scan(lc, lane);
@@ -410,7 +491,7 @@ __device__ __forceinline__ void emit_leaves(const SearchCfg &c, int lane, bool a
             const uint2 kl = leaf_of(c, nd, t, k2, l2);
             // z left after the leaf column: the match keeps z, insertion and mismatch spend one
             const uint32_t zl = ((nd.y >> 8) & 15u) - ((t >= 5 && (uint32_t)(t - 5) == wi) ? 0u : 1u);
-            c.raw[pos] = make_uint4(nd.x, kl.x, kl.y, c.z - zl);
+            c.raw[pos] = make_uint4(q, kl.x, kl.y, z0 - zl);
         }
         ++pos;
     }
@@ -423,101 +504,222 @@ __device__ __forceinline__ void emit_leaves(const SearchCfg &c, int lane, bool a
 // z >= 1, growing up from entry 0) and E (nodes with z = 0, growing down from entry stk-1).
 // E nodes are exact continuations (one cheap step each, the child replacing the node); G nodes
 // take the full eight-value expansion.  Policy per step:
-//   * E holds >= 32 nodes, or only E has work: one exact step for up to 32 E nodes, the
-//     survivors go back to E (ballot compaction);
-//   * else a G step: up to 32 G nodes expanded; children with z' = 0 go to E, the others to G
-//     (two warp prefix sums); if they would not fit, G is first moved to the warp's spill
-//     region in device memory (E holds < 32 then, so 288 children always fit after that);
+//   * E holds >= 32 nodes, or only E has work: exact steps (below) until E runs dry;
+//   * else a G step: up to min(32, (stk - |E|) / 9) G nodes expanded, so that their children
+//     (at most 9 each) always fit beside E once G is out of the way; children with z' = 0 go
+//     to E, the others to G (two warp prefix sums); if they would not fit, G is first moved to
+//     the warp's spill region in device memory (E holds < 32 nodes at a G step);
 //   * G empty but spilled nodes waiting: reload a batch;
-//   * both pools low: take the next chunk of queries from the work queue (their roots).
+//   * pools below the refill level: take up to `chunk` queries from the work queue and push
+//     their roots (with STAGE, no more queries than the free slot groups hold, each staged in
+//     a slot).
 // A warp leaves when the queue is drained and both pools and its spill are empty.
-template <int I>
-__global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk, uint4 *spill_all,
+//
+// STAGE: every query a warp works on is staged in one of its shared-memory slots (its 2-bit
+// symbols oriented for its strand, D breakpoints, length, search mode and number), so that no
+// expansion or exact step reads query data from device memory.  Slots are taken and freed in
+// groups of kGroupSlots.  The warp keeps, in registers, the number of live nodes of each
+// group's queries (nodes in the pools, in the spill region or held by a lane): a G step adds,
+// per group, the children of its nodes minus the nodes (one warp reduction per group), and the
+// exact chains that end during an exact phase are counted per lane and subtracted when the
+// phase ends (or every kFlushSteps steps).  A count can only lag behind, never run ahead, so a
+// group is freed only when no node of its queries is left.  Every group a warp holds has a
+// live node, so the warp never waits for a slot.  Without STAGE the query data is read through
+// L1 from the staging records in device memory.
+constexpr int kFlushSteps = 512;   // exact steps between two flushes of the ended-chain counts
+constexpr int kPoolEntries = 320;  // node pool entries per warp
+
+template <int I, bool STAGE>
+__global__ void __launch_bounds__(256, I <= 128 ? 4 : 2) k_inexact_persistent(SearchCfg c, int stk, uint4 *spill_all,
                                                             uint32_t spill_cap) {
     extern __shared__ uint4 smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    uint4 *st = smem + (size_t)wib * stk;
+    const bool prof = c.fill != nullptr;
+    uint32_t *wbase = reinterpret_cast<uint32_t *>(smem) + (size_t)wib * warp_smem_words(stk, STAGE, prof);
+    Pool<STAGE> st;
+    if constexpr (STAGE) {
+        st.y = wbase;
+        st.k = wbase + stk;
+        st.l = wbase + 2 * stk;
+    } else {
+        st.e = reinterpret_cast<uint4 *>(wbase);
+    }
+    uint32_t *slots = wbase + Pool<STAGE>::kWords * stk;                // kSlots x kSlotWords
+    uint32_t *fillc = slots + (STAGE ? kSlots * kSlotWords : 0);         // step-fill counters
     const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     uint4 *spill = spill_all + gw * spill_cap;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    int gtop = 0;         // G: st[0, gtop)
-    int etop = 0;         // E: st[stk - etop, stk), top at st[stk - etop]
+    int gtop = 0;         // G: entries [0, gtop)
+    int etop = 0;         // E: entries [stk - etop, stk), top at stk - etop
     uint32_t stop = 0;    // spilled G nodes (warp-uniform)
     bool qdone = false;
+    uint32_t fgroups = (1u << kGroups) - 1u;   // free slot groups (warp-uniform)
+    int gcount[kGroups];                       // live nodes per slot group (warp-uniform)
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) gcount[g] = 0;
     unsigned long long my_nodes = 0, my_blocks = 0;
+    if (prof && lane < kFillCounters) fillc[lane] = 0u;
+    __syncwarp();
+    // metadata records: with STAGE the staging records (kStageU4 uint4 per query, the query's
+    // symbols after its metadata word), else one uint4 per query
+    constexpr uint32_t QS = STAGE ? kStageU4 : 1u;
+    // the query data of node nd (with q, its number without STAGE)
+    auto query = [&](const uint4 &nd) {
+        if constexpr (STAGE) return SQuery{slots + slot_of(nd) * kSlotWords};
+        else return GQuery{c.reads, c.qmeta[nd.x]};
+    };
+    // group counts: add the per-lane changes delta of the lanes holding a node of group g
+    auto count_groups = [&](bool has, uint32_t grp, int delta) {
+#pragma unroll
+        for (int g = 0; g < kGroups; ++g) {
+            gcount[g] += __reduce_add_sync(FULL, (has && grp == (uint32_t)g) ? delta : 0);
+            if (gcount[g] == 0) fgroups |= 1u << g;
+        }
+    };
 
     for (;;) {
-        if (gtop + etop < 32 && stop == 0 && !qdone) {
+        if (gtop + etop < (int)c.refill && stop == 0 && !qdone && (!STAGE || fgroups != 0u)) {
+            const uint32_t room = STAGE ? (uint32_t)(__popc(fgroups) * kGroupSlots) : 32u;
+            const uint32_t take = c.chunk < room ? c.chunk : room;
             uint32_t q0 = 0;
-            if (lane == 0) q0 = atomicAdd(c.next_q, c.chunk);
+            if (lane == 0) q0 = atomicAdd(c.next_q, take);
             q0 = __shfl_sync(FULL, q0, 0);
             if (q0 >= c.nq) {
                 qdone = true;
             } else {
                 const uint32_t q = q0 + lane;
                 bool ok = false;
-                uint4 nd;
-                if ((uint32_t)lane < c.chunk && q < c.nq) nd = root_of(c, q, c.qmeta[q], ok);
-                const uint32_t bal = __ballot_sync(FULL, ok);
-                const int pos = __popc(bal & lt_mask);
-                if (c.z == 0) {
-                    if (ok) st[stk - 1 - (etop + pos)] = nd;
-                    etop += __popc(bal);
-                } else {
-                    if (ok) st[gtop + pos] = nd;
-                    gtop += __popc(bal);
+                uint4 nd = make_uint4(0, 0, 0, 0);
+                uint32_t grp = 0;
+                if ((uint32_t)lane < take && q < c.nq) {
+                    const uint4 *src = c.qmeta + (size_t)q * QS;
+                    const uint4 mt = src[0];
+                    const uint32_t m = mt.w & 255u, z0 = (mt.w >> 16) & 15u;
+                    ok = m >= 1u && z0 >= d_at(mt, (int)m - 1);
+                    uint32_t sb = 0;
+                    if constexpr (STAGE) {
+                        uint32_t fg = fgroups;   // lanes 4j..4j+3 take the j-th free group
+                        for (int t = 0; t < lane / kGroupSlots; ++t) fg &= fg - 1u;
+                        grp = (uint32_t)__ffs(fg) - 1u;
+                        const uint32_t sl = grp * kGroupSlots + (uint32_t)(lane % kGroupSlots);
+                        uint4 *dst = reinterpret_cast<uint4 *>(slots + sl * kSlotWords);
+                        dst[0] = src[1];
+                        dst[1] = src[2];
+                        dst[2] = src[3];
+                        dst[3] = src[4];
+                        dst[4] = make_uint4(mt.x, mt.y, m | (mt.w & 0x00ff0000u), q);
+                        sb = sl << kSlotShift;
+                    }
+                    nd = c.ix.kdepth ? make_uint4(q, (m - 1u) | (z0 << 8) | kShallow | sb, 0u, 0u)
+                                     : make_uint4(q, (m - 1u) | (z0 << 8) | sb, 0u, c.ix.n);
+                }
+                if constexpr (STAGE) {
+                    // groups that received a root are taken (the rest stay free)
+                    count_groups(ok, grp, 1);
+                    fgroups &= ~__reduce_or_sync(FULL, ok ? 1u << grp : 0u);
+                }
+                // roots with no difference allowed are exact continuations (E), the rest G
+                const bool ex = ok && ((nd.y >> 8) & 15u) == 0u;
+                const uint32_t bale = __ballot_sync(FULL, ex), balg = __ballot_sync(FULL, ok && !ex);
+                if (ex) st.put(stk - 1 - (etop + __popc(bale & lt_mask)), nd);
+                if (ok && !ex) st.put(gtop + __popc(balg & lt_mask), nd);
+                etop += __popc(bale);
+                gtop += __popc(balg);
+                if (prof && lane == 0) {
+                    fillc[5] += 1u;
+                    fillc[6] += __popc(bale | balg);
                 }
                 __syncwarp();
             }
         }
         if (etop >= 32 || (etop > 0 && gtop == 0 && stop == 0)) {
-            // Exact steps: each lane runs up to two chains (slots 0 and 1) with their read
-            // start and length in registers, their gathers in flight together.  A chain stays
-            // in its slot from step to step; a slot whose chain ended (empty interval, or a
-            // result at i = 0) is refilled from E.  The phase ends when fewer than 32 chains
-            // run and E is empty (unless nothing else is left to do), and the survivors go
-            // back to E (fewer than 32, so E stays below 32 for the next G step).
+            // Exact steps: each lane holds up to two chains (n0, n1).  A chain stays in its lane
+            // from step to step; a lane whose first chain ended moves its second one up, and
+            // free chain places are refilled from E.  Second chains are stepped only while at
+            // least chain2_min lanes hold one (otherwise they wait for a first place, so that
+            // a sparse second pass does not run with most lanes idle).  The phase ends when
+            // fewer than 32 chains are live and E is empty (unless nothing else is left to
+            // do), and the survivors go back to E (fewer than 32, so E stays below 32 for the
+            // next G step).
             uint4 n0 = make_uint4(0, 0, 0, 0), n1 = make_uint4(0, 0, 0, 0);
-            uint2 r0 = make_uint2(0, 0), r1 = make_uint2(0, 0);   // qmeta .z, .w
+            uint2 r0 = make_uint2(0, 0), r1 = make_uint2(0, 0);   // without STAGE: read start, m
             bool a0 = false, a1 = false;
+            uint32_t ended01 = 0, ended23 = 0;   // STAGE: ended chains of groups 0..3, 16-bit fields
+            int since_flush = 0;
+            auto flush = [&]() {
+                if constexpr (STAGE) {
+#pragma unroll
+                    for (int g = 0; g < kGroups; ++g) {
+                        const uint32_t w = g < 2 ? ended01 : ended23;
+                        gcount[g] -= __reduce_add_sync(FULL, (int)((w >> (16 * (g & 1))) & 0xffffu));
+                        if (gcount[g] == 0) fgroups |= 1u << g;
+                    }
+                    ended01 = ended23 = 0;
+                }
+            };
             for (;;) {
-                // refill free slots from E (slot 0 first)
+                if (!a0 && a1) {
+                    n0 = n1;
+                    r0 = r1;
+                    a0 = true;
+                    a1 = false;
+                }
+                // refill free chain places from E (first places first)
                 {
                     const uint32_t f0 = __ballot_sync(FULL, !a0), f1 = __ballot_sync(FULL, !a1);
                     const int nf0 = __popc(f0);
                     const int t0 = nf0 < etop ? nf0 : etop;
                     const int p0 = __popc(f0 & lt_mask);
                     if (!a0 && p0 < t0) {
-                        n0 = st[stk - etop + p0];
-                        const uint4 m = c.qmeta[n0.x];
-                        r0 = make_uint2(m.z, m.w);
+                        n0 = st.get(stk - etop + p0);
+                        if constexpr (!STAGE) {
+                            const uint4 m = c.qmeta[n0.x];
+                            r0 = make_uint2(m.z, m.w);
+                        }
                         a0 = true;
                     }
                     const int rest = etop - t0;
                     const int t1 = __popc(f1) < rest ? __popc(f1) : rest;
                     const int p1 = __popc(f1 & lt_mask);
                     if (!a1 && p1 < t1) {
-                        n1 = st[stk - etop + t0 + p1];
-                        const uint4 m = c.qmeta[n1.x];
-                        r1 = make_uint2(m.z, m.w);
+                        n1 = st.get(stk - etop + t0 + p1);
+                        if constexpr (!STAGE) {
+                            const uint4 m = c.qmeta[n1.x];
+                            r1 = make_uint2(m.z, m.w);
+                        }
                         a1 = true;
                     }
                     etop -= t0 + t1;
                     __syncwarp();
                 }
+                const int live1 = __popc(__ballot_sync(FULL, a1));
+                const bool step1 = a1 && live1 >= (int)c.chain2_min;
                 uint4 c0 = make_uint4(0, 0, 0, 0), c1 = make_uint4(0, 0, 0, 0);
                 bool s0 = false, s1 = false, e0 = false, e1 = false;
                 uint32_t b0 = 0, b1 = 0, x0 = 0, x1 = 0;
+                auto cq = [&](const uint4 &n, const uint2 &r) {
+                    if constexpr (STAGE) return SQuery{slots + slot_of(n) * kSlotWords};
+                    else return GQuery{c.reads, make_uint4(0u, 0u, r.x, r.y)};
+                };
                 if (a0) {
-                    chain_step<I>(c, n0, make_uint4(0, 0, r0.x, r0.y), c0, s0, e0, b0, x0);
+                    chain_step<I>(c, n0, cq(n0, r0), c0, s0, e0, b0, x0);
                     my_nodes += x0;
                     my_blocks += step_cost(b0);
                 }
-                if (a1) {
-                    chain_step<I>(c, n1, make_uint4(0, 0, r1.x, r1.y), c1, s1, e1, b1, x1);
+                if (step1) {
+                    chain_step<I>(c, n1, cq(n1, r1), c1, s1, e1, b1, x1);
                     my_nodes += x1;
                     my_blocks += step_cost(b1);
+                }
+                if (prof) {   // warp-uniform
+                    const int live0 = __popc(__ballot_sync(FULL, a0));
+                    if (lane == 0) {
+                        fillc[0] += 1u;
+                        fillc[1] += (uint32_t)live0;
+                        fillc[2] += live1 >= (int)c.chain2_min ? (uint32_t)live1 : 0u;
+                        fillc[7] += (live1 > 0 && live1 < (int)c.chain2_min) ? 1u : 0u;
+                    }
                 }
                 const uint32_t lb0 = __ballot_sync(FULL, e0), lb1 = __ballot_sync(FULL, e1);
                 if (lb0 | lb1) {
@@ -527,55 +729,101 @@ __global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk
                     base = __shfl_sync(FULL, base, 0);
                     const uint64_t q0 = base + __popc(lb0 & lt_mask);
                     const uint64_t q1 = base + __popc(lb0) + __popc(lb1 & lt_mask);
-                    if (e0 && q0 < c.raw_cap) c.raw[q0] = make_uint4(n0.x, c0.z, c0.w, c.z);
-                    if (e1 && q1 < c.raw_cap) c.raw[q1] = make_uint4(n1.x, c1.z, c1.w, c.z);
+                    // a z = 0 leaf used all of its query's differences
+                    if constexpr (STAGE) {
+                        if (e0 && q0 < c.raw_cap) {
+                            const SQuery qv = cq(n0, r0);
+                            c.raw[q0] = make_uint4(qv.q(), c0.z, c0.w, qv.z0());
+                        }
+                        if (e1 && q1 < c.raw_cap) {
+                            const SQuery qv = cq(n1, r1);
+                            c.raw[q1] = make_uint4(qv.q(), c1.z, c1.w, qv.z0());
+                        }
+                    } else {
+                        if (e0 && q0 < c.raw_cap) c.raw[q0] = make_uint4(n0.x, c0.z, c0.w, cq(n0, r0).z0());
+                        if (e1 && q1 < c.raw_cap) c.raw[q1] = make_uint4(n1.x, c1.z, c1.w, cq(n1, r1).z0());
+                    }
+                }
+                if constexpr (STAGE) {   // an ended chain: one node less for its group
+                    if (a0 && !s0) {
+                        const uint32_t g = slot_of(n0) / kGroupSlots;
+                        (g < 2 ? ended01 : ended23) += 1u << (16u * (g & 1u));
+                    }
+                    if (step1 && !s1) {
+                        const uint32_t g = slot_of(n1) / kGroupSlots;
+                        (g < 2 ? ended01 : ended23) += 1u << (16u * (g & 1u));
+                    }
+                    if (++since_flush == kFlushSteps) {
+                        flush();
+                        since_flush = 0;
+                    }
                 }
                 if (s0) n0 = c0;
                 if (s1) n1 = c1;
                 a0 = s0;
-                a1 = s1;
+                if (step1) a1 = s1;
                 const int live = __popc(__ballot_sync(FULL, a0)) + __popc(__ballot_sync(FULL, a1));
                 if (live == 0 && etop == 0) break;
                 if (live < 32 && etop == 0 && !(gtop == 0 && stop == 0 && qdone)) {
                     // survivors back to E
                     const uint32_t v0 = __ballot_sync(FULL, a0), v1 = __ballot_sync(FULL, a1);
-                    if (a0) st[stk - 1 - (etop + __popc(v0 & lt_mask))] = n0;
-                    if (a1) st[stk - 1 - (etop + __popc(v0) + __popc(v1 & lt_mask))] = n1;
+                    if (a0) st.put(stk - 1 - (etop + __popc(v0 & lt_mask)), n0);
+                    if (a1) st.put(stk - 1 - (etop + __popc(v0) + __popc(v1 & lt_mask)), n1);
                     etop += __popc(v0) + __popc(v1);
                     __syncwarp();
                     break;
                 }
             }
+            flush();
             continue;
         }
+        // nodes one G step may take: their children (at most 9 each) fit beside E
+        const int cap_take = min(32, (stk - etop) / 9);
         if (gtop == 0 && stop > 0) {
-            // reload spilled G nodes: keep room for the children of one G step (288) plus E
-            int room = stk - 256 - etop;
-            uint32_t nmove = stop < (uint32_t)room ? stop : (uint32_t)room;
-            for (uint32_t t = lane; t < nmove; t += 32) st[t] = spill[stop - nmove + t];
+            // reload spilled G nodes: one G step takes cap_take of them and pushes at most
+            // 9 cap_take children, so stk - |E| - 8 cap_take (>= cap_take) fit without a spill
+            const int room = stk - etop - 8 * cap_take;
+            const uint32_t nmove = stop < (uint32_t)room ? stop : (uint32_t)room;
+            for (uint32_t t = lane; t < nmove; t += 32) st.put((int)t, spill[stop - nmove + t]);
             stop -= nmove;
             gtop = (int)nmove;
             __syncwarp();
             continue;
         }
         if (gtop == 0) {
-            if (qdone && etop == 0 && stop == 0) break;
+            if (etop == 0 && stop == 0) {
+                if (qdone) break;
+                if constexpr (STAGE) {
+                    // the warp holds no node: every slot group is empty (this also frees the
+                    // groups of nodes dropped on a spill overflow, whose pass is rerun)
+                    fgroups = (1u << kGroups) - 1u;
+#pragma unroll
+                    for (int g = 0; g < kGroups; ++g) gcount[g] = 0;
+                }
+            }
             continue;
         }
-        // general step on up to 32 G nodes
-        const int take = gtop < 32 ? gtop : 32;
+        // general step on up to cap_take G nodes
+        const int take = gtop < cap_take ? gtop : cap_take;
         const bool act = lane < take;
-        uint4 nd = make_uint4(0, 0, 0, 0), mt = make_uint4(0, 0, 0, 0);
-        if (act) nd = st[gtop - 1 - lane];
+        uint4 nd = make_uint4(0, 0, 0, 0);
+        if (act) nd = st.get(gtop - 1 - lane);
         gtop -= take;
         __syncwarp();
         uint32_t k2[4] = {0, 0, 0, 0}, l2[4] = {0, 0, 0, 0}, push = 0, leaf = 0, nb = 0, wi = 0;
+        uint32_t z0 = 0, qn = nd.x;   // the query's differences allowed, and its number
         if (act) {
-            mt = c.qmeta[nd.x];
+            const auto qv = query(nd);
             uint32_t cn = 0;
-            expand<I>(c, nd, mt, k2, l2, push, leaf, nb, cn, wi);
+            expand<I>(c, nd, qv, k2, l2, push, leaf, nb, cn, wi);
+            z0 = qv.z0();
+            if constexpr (STAGE) qn = qv.q();
             my_nodes += cn;
             my_blocks += step_cost(nb);
+        }
+        if (prof && lane == 0) {
+            fillc[3] += 1u;
+            fillc[4] += (uint32_t)take;
         }
         // children with z' = 0 (every child but the match of a z = 1 node) go to E
         const uint32_t z = (nd.y >> 8) & 15u;
@@ -587,12 +835,12 @@ __global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk
         const int gtot = __shfl_sync(FULL, gincl, 31);
         const int etot = __shfl_sync(FULL, eincl, 31);
         if (gtop + gtot + etop + etot > stk) {
-            // pools full: move G to the spill region (E holds < 32 nodes here)
+            // pools full: move G to the spill region
             if (stop + (uint32_t)gtop > spill_cap) {
                 if (lane == 0) atomicOr(c.err, kErrSpill);
                 gtop = 0;   // work dropped: the host grows the spill region and reruns
             } else {
-                for (int t = lane; t < gtop; t += 32) spill[stop + t] = st[t];
+                for (int t = lane; t < gtop; t += 32) spill[stop + t] = st.get(t);
                 stop += (uint32_t)gtop;
                 gtop = 0;
             }
@@ -606,13 +854,15 @@ __global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk
                 const int t = __ffs(mset) - 1;
                 mset &= mset - 1;
                 const uint4 chd = make_child(nd, t, k2, l2, wi, c.ix.kdepth);
-                if ((emask >> t) & 1u) st[stk - 1 - (epos++)] = chd;
-                else st[gpos++] = chd;
+                if ((emask >> t) & 1u) st.put(stk - 1 - (epos++), chd);
+                else st.put(gpos++, chd);
             }
         }
         gtop += gtot;
         etop += etot;
-        emit_leaves(c, lane, act, nd, leaf, k2, l2, wi);
+        // live nodes per slot group: the children replace the expanded node
+        if constexpr (STAGE) count_groups(act, slot_of(nd) / kGroupSlots, gc + ec - 1);
+        emit_leaves(c, lane, act, nd, leaf, k2, l2, wi, z0, qn);
         __syncwarp();
     }
     if (c.stats) {
@@ -626,6 +876,10 @@ __global__ void __launch_bounds__(256) k_inexact_persistent(SearchCfg c, int stk
             atomicAdd(c.stats + 1, my_blocks & 0xffffffffull);
             atomicAdd(c.stats + 3, my_blocks >> 32);
         }
+    }
+    if (prof) {
+        __syncwarp();
+        if (lane < kFillCounters) atomicAdd(c.fill + lane, (unsigned long long)fillc[lane]);
     }
 }
 
@@ -665,6 +919,7 @@ __global__ void __launch_bounds__(256) k_inexact_plain(SearchCfg c, uint4 *stack
         uint4 nd = make_uint4(0, 0, 0, 0);
         uint32_t k2[4] = {0, 0, 0, 0}, l2[4] = {0, 0, 0, 0}, push = 0, leaf = 0, nb = 0, wi = 0;
         uint32_t counted = 1;   // an exact step is always a counted node
+        uint32_t z0 = 0;        // the query's differences allowed
         bool ex_leaf = false;
         uint4 ex_out = make_uint4(0, 0, 0, 0);
         if (act) {
@@ -675,16 +930,17 @@ __global__ void __launch_bounds__(256) k_inexact_plain(SearchCfg c, uint4 *stack
                 --sp;
             }
             cur = false;
-            const uint4 mt = c.qmeta[nd.x];
+            const GQuery qv{c.reads, c.qmeta[nd.x]};
+            z0 = qv.z0();
             if (((nd.y >> 8) & 15u) == 0u) {
                 bool survive = false;
-                chain_step<I>(c, nd, mt, ex_out, survive, ex_leaf, nb, counted);
+                chain_step<I>(c, nd, qv, ex_out, survive, ex_leaf, nb, counted);
                 if (survive) {
                     curnd = ex_out;
                     cur = true;
                 }
             } else {
-                expand<I>(c, nd, mt, k2, l2, push, leaf, nb, counted, wi);
+                expand<I>(c, nd, qv, k2, l2, push, leaf, nb, counted, wi);
                 uint32_t mset = push;
                 while (mset) {
                     const int t = __ffs(mset) - 1;
@@ -701,14 +957,14 @@ __global__ void __launch_bounds__(256) k_inexact_plain(SearchCfg c, uint4 *stack
             my_blocks += step_cost(nb);
             if (sp == 0 && !cur) have = false;
         }
-        emit_leaves(c, lane, act, nd, leaf, k2, l2, wi);
+        emit_leaves(c, lane, act, nd, leaf, k2, l2, wi, z0, nd.x);
         const uint32_t lb = __ballot_sync(FULL, ex_leaf);
         if (lb) {
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(c.raw_count, (unsigned long long)__popc(lb));
             base = __shfl_sync(FULL, base, 0);
             const uint64_t pos = base + __popc(lb & ((1u << lane) - 1u));
-            if (ex_leaf && pos < c.raw_cap) c.raw[pos] = make_uint4(nd.x, ex_out.z, ex_out.w, c.z);
+            if (ex_leaf && pos < c.raw_cap) c.raw[pos] = make_uint4(nd.x, ex_out.z, ex_out.w, z0);
         }
     }
     if (c.stats) {
@@ -1149,8 +1405,21 @@ static int scan_u32(fm_index *h, const uint32_t *in, uint64_t n, uint64_t *out, 
     return FM_OK;
 }
 
+uint64_t scratch_total(const fm_index *h) {
+    return h->s_qmeta.bytes + h->s_raw.bytes + h->s_spill.bytes + h->s_group.bytes +
+           h->s_scan.bytes + h->s_plain.bytes + h->s_misc.bytes;
+}
+
 int ensure_scratch(fm_index *h, Scratch &s, size_t bytes) {
     if (s.bytes >= bytes && s.ptr) return FM_OK;
+    if (h->scratch_budget) {
+        const size_t want = bytes < 256 ? 256 : bytes;
+        const uint64_t total = scratch_total(h) - s.bytes + want;
+        if (total > h->scratch_budget)
+            return set_error(h, FM_ENOMEM, "search scratch of " + std::to_string(total) +
+                                               " bytes would exceed its budget of " +
+                                               std::to_string(h->scratch_budget));
+    }
     if (s.ptr) {
         cudaFree(s.ptr);
         s.ptr = nullptr;
@@ -1167,6 +1436,42 @@ int ensure_scratch(fm_index *h, Scratch &s, size_t bytes) {
     return FM_OK;
 }
 
+// shared memory of one persistent CTA: per warp, stk pool entries plus its query slots and
+// step-fill counters (without staging, the counters only when they are collected: the
+// carveout, and so the L1 left beside it, follows the shared memory of the launch)
+static size_t persistent_smem(int block, int stk, bool stage, bool fill = false) {
+    return (size_t)(block / 32) * (size_t)warp_smem_words(stk, stage, fill) * 4;
+}
+
+// node pool entries per warp.  Smaller pools would leave more of the SM's memory to L1, but a
+// G step then expands fewer nodes at once (measured slower at every size below 320)
+static int pool_entries(const Tuning &) { return kPoolEntries; }
+
+// the tuning knobs of the persistent scheduler, into a search configuration
+static void set_sched(SearchCfg &c, const Tuning &tu) {
+    c.chunk = tu.chunk;
+    // roots of one chunk (at most 32) always fit: the pools take queries below pool - 32
+    c.refill = tu.refill + 32u <= (uint32_t)kPoolEntries ? tu.refill : (uint32_t)kPoolEntries - 32u;
+    c.chain2_min = tu.chain2_min;
+    c.fill = nullptr;
+}
+
+// step-fill counters of the persistent kernel: 8 x uint64 in s_misc at this offset (after the
+// counters at 0-31, the search stats at 32-63 and the status words of a graph at 64-103)
+constexpr size_t kMiscFill = 128;
+static_assert(kMiscFill + 64 <= 256, "s_misc holds 256 bytes");
+
+static void copy_fill(fm_profile *prof, const unsigned long long *v) {
+    prof->exact_steps = v[0];
+    prof->exact_lanes = v[1];
+    prof->exact_lanes2 = v[2];
+    prof->general_steps = v[3];
+    prof->general_lanes = v[4];
+    prof->admissions = v[5];
+    prof->admitted = v[6];
+    prof->parked = v[7];
+}
+
 template <int I>
 static int launch_search(fm_index *h, const SearchCfg &c, uint32_t kernel, uint4 *spill,
                          uint32_t spill_cap, int grid, int block, int stk, uint4 *stacks,
@@ -1175,33 +1480,61 @@ static int launch_search(fm_index *h, const SearchCfg &c, uint32_t kernel, uint4
         const int pb = (int)h->tune.plain_block;
         k_inexact_plain<I><<<(T + pb - 1) / pb, pb, 0, st>>>(c, stacks, cap, T);
     } else {
-        const size_t smem = (size_t)(block / 32) * stk * sizeof(uint4);
-        k_inexact_persistent<I><<<grid, block, smem, st>>>(c, stk, spill, spill_cap);
+        const bool fill = c.fill != nullptr;
+        if (h->tune.stage)
+            k_inexact_persistent<I, true><<<grid, block, persistent_smem(block, stk, true, fill), st>>>(
+                c, stk, spill, spill_cap);
+        else
+            k_inexact_persistent<I, false><<<grid, block, persistent_smem(block, stk, false, fill), st>>>(
+                c, stk, spill, spill_cap);
     }
     FM_CUDA_TRY(h, cudaGetLastError());
     return FM_OK;
 }
 
 template <int I>
-static cudaError_t set_smem_attr(size_t smem) {
-    return cudaFuncSetAttribute(k_inexact_persistent<I>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
+static cudaError_t set_smem_attr(size_t smem, bool stage) {
+    return stage ? cudaFuncSetAttribute(k_inexact_persistent<I, true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                 : cudaFuncSetAttribute(k_inexact_persistent<I, false>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 template <int I>
-static int occupancy_blocks(int block, size_t smem) {
+static int occupancy_blocks(int block, size_t smem, bool stage) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_inexact_persistent<I>, block, smem);
+    if (stage) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_inexact_persistent<I, true>, block, smem);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_inexact_persistent<I, false>, block, smem);
     return nb;
+}
+
+static cudaError_t set_smem_attr_any(uint32_t I, size_t smem, bool stage) {
+    return I == 32 ? set_smem_attr<32>(smem, stage)
+                   : (I == 64 ? set_smem_attr<64>(smem, stage)
+                              : (I == 128 ? set_smem_attr<128>(smem, stage) : set_smem_attr<256>(smem, stage)));
+}
+
+static int occupancy_any(uint32_t I, int block, size_t smem, bool stage) {
+    return I == 32 ? occupancy_blocks<32>(block, smem, stage)
+                   : (I == 64 ? occupancy_blocks<64>(block, smem, stage)
+                              : (I == 128 ? occupancy_blocks<128>(block, smem, stage)
+                                          : occupancy_blocks<256>(block, smem, stage)));
 }
 
 // fills the profile from the phase events: ev[0] start, ev[1] before the (last) search pass,
 // ev[2] after it, ev[3] end of the canonical sets
 static int finish_profile(fm_index *h, fm_profile *prof, cudaEvent_t *ev, uint32_t launches,
-                          cudaStream_t st) {
+                          cudaStream_t st, const unsigned long long *fill = nullptr) {
     if (!prof) return FM_OK;
     FM_CUDA_TRY(h, cudaEventRecord(ev[3], st));
     FM_CUDA_TRY(h, cudaEventSynchronize(ev[3]));
+    if (fill) {
+        unsigned long long fv[8];
+        FM_CUDA_TRY(h, cudaMemcpyAsync(fv, fill, sizeof(fv), cudaMemcpyDeviceToHost, st));
+        FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+        copy_fill(prof, fv);
+        prof->fill_counters = 1;
+    }
     float a = 0, b = 0, c = 0, d = 0;
     FM_CUDA_TRY(h, cudaEventElapsedTime(&a, ev[0], ev[4] ? ev[4] : ev[1]));
     FM_CUDA_TRY(h, cudaEventElapsedTime(&b, ev[1], ev[2]));
@@ -1260,17 +1593,21 @@ struct GroupLayout {
 static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *offs,
                              uint32_t n_reads, const fm_search_params *sp, uint32_t *counts,
                              uint64_t *offsets, uint32_t *pairs, uint64_t pair_capacity,
-                             uint64_t *pairs_needed, cudaStream_t st, bool *fallback) {
+                             uint64_t *pairs_needed, cudaStream_t st, bool *fallback,
+                             const uint8_t *modes) {
     *fallback = true;
     const uint32_t nq = n_reads * sp->strands;
     const uint32_t I = h->interval;
     const Tuning &tu = h->tune;
     const int block = (int)tu.warps_per_block * 32;
-    const int stk = 320;
-    const size_t smem = (size_t)(block / 32) * stk * sizeof(uint4);
+    const int stk = pool_entries(tu);
+    fm_profile *prof = sp->profile;
+    const bool want_fill = prof && prof->fill_counters;
+    // the kernel's shared-memory attribute is the launch's own size: the driver sizes the
+    // carveout (and so the L1 left beside it) from it
+    const size_t smem = persistent_smem(block, stk, tu.stage != 0, want_fill);
     int bps = (int)tu.blocks_per_sm;
-    const int occ = I == 32 ? occupancy_blocks<32>(block, smem) : I == 64 ? occupancy_blocks<64>(block, smem)
-                            : (I == 128 ? occupancy_blocks<128>(block, smem) : occupancy_blocks<256>(block, smem));
+    const int occ = occupancy_any(I, block, smem, tu.stage != 0);
     if (bps <= 0 || bps > occ) bps = occ;
     if (bps <= 0) return FM_OK;
     const int grid = h->sms * bps;
@@ -1280,11 +1617,11 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
     const uint32_t spill_cap = (uint32_t)(h->s_spill.bytes / sizeof(uint4) / nwarps);
     if (raw_cap < (uint64_t)nq * 4 || spill_cap < 4096) return FM_OK;
     int rc;
-    if ((rc = ensure_scratch(h, h->s_qmeta, (size_t)nq * sizeof(uint4)))) return rc;
+    const uint32_t qstride = tu.stage ? kStageU4 : 1u;
+    if ((rc = ensure_scratch(h, h->s_qmeta, (size_t)nq * qstride * sizeof(uint4)))) return rc;
     const GroupLayout L(nq, raw_cap);
     if ((rc = ensure_scratch(h, h->s_group, L.total))) return rc;
     if (!h->cap_stream) FM_CUDA_TRY(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-    fm_profile *prof = sp->profile;
     if (prof && !h->gev[0])
         for (auto &e : h->gev) FM_CUDA_TRY(h, cudaEventCreate(&e));
 
@@ -1295,9 +1632,11 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
     key.pair_capacity = pair_capacity; key.raw_cap = raw_cap; key.n_reads = n_reads;
     key.strands = sp->strands; key.z = sp->z; key.max_gaps = sp->max_gaps; key.interval = I;
     key.grid = (uint32_t)grid; key.block = (uint32_t)block; key.chunk = tu.chunk;
-    key.spill_cap = spill_cap; key.profile = prof ? 1u : 0u; key.canon = search_canon(tu, sp);
-    key.end_skip = sp->indel_end_skip;
-    key.kt = h->d_kt; key.kdepth = h->kt_depth | (view_fwd(h).pairs << 16);
+    key.spill_cap = spill_cap; key.profile = prof ? (want_fill ? 2u : 1u) : 0u;
+    key.canon = search_canon(tu, sp);
+    key.end_skip = sp->indel_end_skip; key.refill = tu.refill; key.chain2 = tu.chain2_min;
+    key.pool = (uint32_t)stk | (tu.stage << 16);
+    key.kt = h->d_kt; key.kdepth = h->kt_depth | (view_fwd(h).pairs << 16); key.modes = modes;
 
     char *misc = (char *)h->s_misc.ptr;
     unsigned long long *d_raw_count = (unsigned long long *)misc;
@@ -1317,8 +1656,7 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
             cudaGraphExecDestroy(h->gexec);
             h->gexec = nullptr;
         }
-        cudaError_t e = I == 32 ? set_smem_attr<32>(smem) : (I == 64 ? set_smem_attr<64>(smem)
-                        : (I == 128 ? set_smem_attr<128>(smem) : set_smem_attr<256>(smem)));
+        cudaError_t e = set_smem_attr_any(I, smem, tu.stage != 0);
         if (e != cudaSuccess) return cuda_status(h, e, "cudaFuncSetAttribute");
         FM_CUDA_TRY(h, cudaFuncSetAttribute(k_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)(8192 * sizeof(uint64_t))));
@@ -1329,10 +1667,11 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
         do {
             if (prof && cudaEventRecordWithFlags(h->gev[0], cs, cudaEventRecordExternal)) { crc = FM_ECUDA; break; }
             if (cudaMemsetAsync(h->d_err + kErrDcalc, 0, 8, cs)) { crc = FM_ECUDA; break; }
-            if ((crc = launch_dcalc(h, reads, offs, n_reads, sp->strands, (uint4 *)h->s_qmeta.ptr, nullptr, cs))) break;
+            if ((crc = launch_dcalc(h, reads, offs, n_reads, sp->strands, (uint4 *)h->s_qmeta.ptr, nullptr, cs, qstride,
+                                    modes, sp->z | (sp->max_gaps << 4)))) break;
             ++launches;
             if (prof && cudaEventRecordWithFlags(h->gev[1], cs, cudaEventRecordExternal)) { crc = FM_ECUDA; break; }
-            if (cudaMemsetAsync(misc, 0, 64, cs)) { crc = FM_ECUDA; break; }
+            if (cudaMemsetAsync(misc, 0, kMiscFill + 64, cs)) { crc = FM_ECUDA; break; }
             SearchCfg c;
             c.ix = view_fwd(h);
             c.reads = reads;
@@ -1340,7 +1679,8 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
             c.nq = nq;
             c.z = sp->z;
             c.max_gaps = sp->max_gaps;
-            c.chunk = tu.chunk;
+            set_sched(c, tu);
+            if (want_fill) c.fill = (unsigned long long *)(misc + kMiscFill);
             c.next_q = d_next_q;
             c.raw = (uint4 *)h->s_raw.ptr;
             c.raw_count = d_raw_count;
@@ -1398,6 +1738,10 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
         h->glaunches = launches;
         h->graph_captures += 1;
     }
+    {   // an eager call since the capture may have set another size: restore the graph's
+        cudaError_t e = set_smem_attr_any(I, smem, tu.stage != 0);
+        if (e != cudaSuccess) return cuda_status(h, e, "cudaFuncSetAttribute");
+    }
     FM_CUDA_TRY(h, cudaGraphLaunch(h->gexec, st));
     h->graph_replays += 1;
     unsigned long long status[5] = {0, 0, 0, 0, 0};
@@ -1419,7 +1763,14 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
     h->last_valid = true;
     if (pairs_needed) *pairs_needed = need;
     if (prof) {
+        unsigned long long fv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (want_fill) {
+            FM_CUDA_TRY(h, cudaMemcpyAsync(fv, misc + kMiscFill, sizeof(fv), cudaMemcpyDeviceToHost, st));
+            FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+        }
         memset(prof, 0, sizeof(*prof));
+        copy_fill(prof, fv);
+        prof->fill_counters = want_fill ? 1u : 0u;
         float a = 0, b = 0, cc = 0, d = 0;
         FM_CUDA_TRY(h, cudaEventElapsedTime(&a, h->gev[0], h->gev[1]));
         FM_CUDA_TRY(h, cudaEventElapsedTime(&b, h->gev[1], h->gev[2]));
@@ -1441,18 +1792,20 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
 
 int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
                 const fm_search_params *sp, uint32_t *counts, uint64_t *offsets, uint32_t *pairs,
-                uint64_t pair_capacity, uint64_t *pairs_needed, cudaStream_t st) {
+                uint64_t pair_capacity, uint64_t *pairs_needed, cudaStream_t st,
+                const uint8_t *modes) {
     if (int krc = ensure_kmer(h, st)) return krc;
     if (int prc = ensure_pairs(h, st)) return prc;
     const bool want_cost = sp->costs != nullptr || sp->best;   // eager path only
     if (h->use_graphs && sp->kernel != FM_KERNEL_PLAIN && n_reads > 0 && !want_cost) {
         bool fallback = true;
         const int grc = run_inexact_graph(h, reads, offs, n_reads, sp, counts, offsets, pairs,
-                                          pair_capacity, pairs_needed, st, &fallback);
+                                          pair_capacity, pairs_needed, st, &fallback, modes);
         if (!fallback) return grc;
         if (grc) return grc;
     }
     h->last_valid = false;   // only this call's results may be fetched after it
+    FM_CUDA_TRY(h, cudaMemsetAsync(h->d_err + kErrDcalc, 0, 8, st));   // D pass and search words
     const uint32_t strands = sp->strands;
     const uint64_t nq64 = (uint64_t)n_reads * strands;
     if (nq64 > 0xffffffffull) return set_error(h, FM_EINVAL, "too many queries");
@@ -1476,6 +1829,7 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
 
     // phase events on the call's stream (profile requested)
     fm_profile *prof = sp->profile;
+    const bool want_fill = prof && prof->fill_counters && sp->kernel != FM_KERNEL_PLAIN;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     struct EvGuard {
         cudaEvent_t *e;
@@ -1485,31 +1839,32 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
         }
     } evg{ev};
     if (prof) {
-        memset(prof, 0, sizeof(*prof));
+        memset(prof, 0, sizeof(*prof));   // the fill_counters request was read above
         for (int i = 0; i < 5; ++i) FM_CUDA_TRY(h, cudaEventCreate(&ev[i]));
         FM_CUDA_TRY(h, cudaEventRecord(ev[0], st));
     }
     uint32_t launches = 0;
 
-    // D lower bound and per-query metadata
-    if ((rc = ensure_scratch(h, h->s_qmeta, (size_t)nq * sizeof(uint4)))) return rc;
+    // D lower bound and per-query metadata (the persistent kernel's staging records)
+    const uint32_t qstride = (sp->kernel != FM_KERNEL_PLAIN && h->tune.stage) ? kStageU4 : 1u;
+    if ((rc = ensure_scratch(h, h->s_qmeta, (size_t)nq * qstride * sizeof(uint4)))) return rc;
     uint4 *qmeta = (uint4 *)h->s_qmeta.ptr;
-    if ((rc = launch_dcalc(h, reads, offs, n_reads, strands, qmeta, nullptr, st))) return rc;
+    if ((rc = launch_dcalc(h, reads, offs, n_reads, strands, qmeta, nullptr, st, qstride, modes,
+                           sp->z | (sp->max_gaps << 4))))
+        return rc;
     ++launches;
     if (prof) FM_CUDA_TRY(h, cudaEventRecord(ev[4], st));   // end of the D pass
 
     const uint32_t I = h->interval;
     const Tuning &tu = h->tune;
     const int block = (int)tu.warps_per_block * 32;
-    const int stk = 320;   // pool entries per warp: G + E never exceed 31 + 288 (see the kernel)
-    const size_t smem = (size_t)(block / 32) * stk * sizeof(uint4);
-    cudaError_t e = I == 32 ? set_smem_attr<32>(smem) : (I == 64 ? set_smem_attr<64>(smem) : (I == 128 ? set_smem_attr<128>(smem)
-                                                                  : set_smem_attr<256>(smem)));
+    const int stk = pool_entries(tu);   // pool entries per warp (see the kernel)
+    // the attribute is the launch's own size (see the graph path)
+    const size_t smem = persistent_smem(block, stk, tu.stage != 0, want_fill);
+    cudaError_t e = set_smem_attr_any(I, smem, tu.stage != 0);
     if (e != cudaSuccess) return cuda_status(h, e, "cudaFuncSetAttribute");
     int bps = (int)tu.blocks_per_sm;
-    const int occ = I == 32 ? occupancy_blocks<32>(block, smem) : I == 64 ? occupancy_blocks<64>(block, smem)
-                            : (I == 128 ? occupancy_blocks<128>(block, smem)
-                                        : occupancy_blocks<256>(block, smem));
+    const int occ = occupancy_any(I, block, smem, tu.stage != 0);
     if (bps <= 0 || bps > occ) bps = occ;
     if (bps <= 0) return set_error(h, FM_ECUDA, "persistent kernel does not fit on an SM");
     int grid = h->sms * bps;
@@ -1536,7 +1891,7 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
         if ((rc = ensure_scratch(h, h->s_raw, raw_cap * sizeof(uint4)))) return rc;
         if (sp->kernel != FM_KERNEL_PLAIN)
             if ((rc = ensure_scratch(h, h->s_spill, nwarps * spill_cap * sizeof(uint4)))) return rc;
-        FM_CUDA_TRY(h, cudaMemsetAsync(h->s_misc.ptr, 0, 64, st));
+        FM_CUDA_TRY(h, cudaMemsetAsync(h->s_misc.ptr, 0, kMiscFill + 64, st));
         FM_CUDA_TRY(h, cudaMemsetAsync(h->d_err + kErrSearch, 0, 4, st));
         SearchCfg c;
         c.ix = view_fwd(h);
@@ -1545,7 +1900,8 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
         c.nq = nq;
         c.z = sp->z;
         c.max_gaps = sp->max_gaps;
-        c.chunk = tu.chunk;
+        set_sched(c, tu);
+        if (want_fill) c.fill = (unsigned long long *)((char *)h->s_misc.ptr + kMiscFill);
         c.next_q = d_next_q;
         c.raw = (uint4 *)h->s_raw.ptr;
         c.raw_count = d_raw_count;
@@ -1673,8 +2029,10 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
                 FM_CUDA_TRY(h, cudaGetLastError());
                 ++launches;
             }
+            const unsigned long long *fillp =
+                want_fill ? (const unsigned long long *)((char *)h->s_misc.ptr + kMiscFill) : nullptr;
             if (need > pair_capacity) {
-                if ((rc = finish_profile(h, prof, ev, launches, st))) return rc;
+                if ((rc = finish_profile(h, prof, ev, launches, st, fillp))) return rc;
                 return set_error(h, FM_ETRUNC, "pair capacity " + std::to_string(pair_capacity) +
                                                    " below the " + std::to_string(need) + " intervals found");
             }
@@ -1693,7 +2051,7 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
                 FM_CUDA_TRY(h, cudaGetLastError());
                 launches += sp->costs && !sp->best ? 2u : 1u;
             }
-            if ((rc = finish_profile(h, prof, ev, launches, st))) return rc;
+            if ((rc = finish_profile(h, prof, ev, launches, st, fillp))) return rc;
             return FM_OK;
         }
     }
@@ -1818,7 +2176,9 @@ int run_inexact_noalloc(fm_index *h, const uint8_t *reads, const uint32_t *offs,
         return FM_OK;
     }
     FM_CUDA_TRY(h, cudaMemsetAsync(h->d_err + kErrSearch, 0, 4, st));
-    if ((rc = launch_dcalc(h, reads, offs, n_reads, sp->strands, qmeta, nullptr, st))) return rc;
+    if ((rc = launch_dcalc(h, reads, offs, n_reads, sp->strands, qmeta, nullptr, st, 1, nullptr,
+                           sp->z | (sp->max_gaps << 4))))
+        return rc;
 
     SearchCfg c;
     c.ix = view_fwd(h);
@@ -1827,7 +2187,7 @@ int run_inexact_noalloc(fm_index *h, const uint8_t *reads, const uint32_t *offs,
     c.nq = nq;
     c.z = sp->z;
     c.max_gaps = sp->max_gaps;
-    c.chunk = h->tune.chunk;
+    set_sched(c, h->tune);
     c.next_q = d_next_q;
     c.raw = raw;
     c.raw_count = d_raw_count;

@@ -70,19 +70,21 @@ struct Scratch {
 // What a captured search graph depends on; a call with another key captures a new graph.
 struct GraphKey {
     const void *reads, *offs, *counts, *offsets, *pairs, *stats;
-    const void *qmeta, *raw, *spill, *group, *misc, *kt;
+    const void *qmeta, *raw, *spill, *group, *misc, *kt, *modes;
     uint64_t pair_capacity, raw_cap;
     uint32_t n_reads, strands, z, max_gaps, interval, grid, block, chunk, spill_cap, profile, canon,
-        kdepth, end_skip;
+        kdepth, end_skip, refill, chain2, pool;
     bool operator==(const GraphKey &o) const {
         return reads == o.reads && offs == o.offs && counts == o.counts && offsets == o.offsets &&
                pairs == o.pairs && stats == o.stats && qmeta == o.qmeta && raw == o.raw &&
+               modes == o.modes &&
                spill == o.spill && group == o.group && misc == o.misc &&
                pair_capacity == o.pair_capacity && raw_cap == o.raw_cap && n_reads == o.n_reads &&
                strands == o.strands && z == o.z && max_gaps == o.max_gaps &&
                interval == o.interval && grid == o.grid && block == o.block && chunk == o.chunk &&
                spill_cap == o.spill_cap && profile == o.profile && canon == o.canon && kt == o.kt &&
-               kdepth == o.kdepth && end_skip == o.end_skip;
+               kdepth == o.kdepth && end_skip == o.end_skip && refill == o.refill &&
+               chain2 == o.chain2 && pool == o.pool;
     }
 };
 
@@ -96,6 +98,9 @@ struct Tuning {
     uint32_t kmer = FM_KMER_AUTO;   // interval-table depth setting (FM_KMER_AUTO, FM_KMER_OFF, 1..14)
     uint32_t pairs = 1;             // exact continuations two symbols per step from the pair table
     uint32_t l2_fetch = 0;   // 0: leave the context's limit alone
+    uint32_t refill = 32;    // a warp takes more queries when its pools hold fewer nodes
+    uint32_t chain2_min = 1; // lanes whose second exact chain is live for the warp to step it
+    uint32_t stage = 0;      // persistent kernel stages its queries in shared memory
 };
 
 }  // namespace fm
@@ -126,6 +131,9 @@ struct fm_index {
     bool pairs_built = false;
     // grow-on-demand scratch of the search calls
     fm::Scratch s_qmeta, s_raw, s_spill, s_group, s_scan, s_plain, s_misc;
+    uint64_t scratch_budget = 0;     // 0: unbounded; else growth past it fails with FM_ENOMEM
+    bool borrowed = false;           // a search context: the index tables belong to another
+                                     // handle (see new_search_context)
     fm::Tuning tune;
     std::string err;
     // canonical results of the last search (in s_group), for fm_inexact_fetch
@@ -150,6 +158,13 @@ int set_error(fm_index *h, int code, const std::string &msg);
 int set_global_error(int code, const std::string &msg);
 int cuda_status(fm_index *h, cudaError_t e, const char *what);
 int ensure_scratch(fm_index *h, Scratch &s, size_t bytes);
+uint64_t scratch_total(const fm_index *h);
+// A search context: a second handle onto h's resident index (every table shared, none owned)
+// with scratch, error words, graph state and fetchable results of its own, so that searches
+// on h and on its contexts can run at the same time on different streams and host threads.
+// Valid while h lives and its tables are not rebuilt; freed by free_search_context only.
+fm_index *new_search_context(fm_index *h);
+void free_search_context(fm_index *c);
 int device_sms(int device);
 
 #define FM_CUDA_TRY(h, call)                                   \
@@ -179,13 +194,21 @@ int ensure_kmer(fm_index *h, cudaStream_t st);
 int ensure_pairs(fm_index *h, cudaStream_t st);
 constexpr uint32_t kPairRows = 64, kPairSuper = 32768;
 constexpr uint32_t kMaxKmerDepth = 14;
-// D lower bound per query; qmeta (uint4 per query) and/or D_out (uint8 per position)
+// D lower bound per query; qmeta (one uint4 per query, or with stride kStageU4 the staging
+// record of the persistent search: that uint4, then the query as 2-bit symbols) and/or D_out
+// (uint8 per position)
+constexpr uint32_t kStageU4 = 5;
+// modes: optional device uint8 per read, its search mode (z | max_gaps << 4); else defmode
 int launch_dcalc(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
-                 uint32_t strands, uint4 *qmeta, uint8_t *D_out, cudaStream_t st);
+                 uint32_t strands, uint4 *qmeta, uint8_t *D_out, cudaStream_t st,
+                 uint32_t stride = 1, const uint8_t *modes = nullptr, uint32_t defmode = 0);
 int fetch_inexact(fm_index *h, uint32_t *pairs, uint64_t pair_capacity, cudaStream_t st);
+// modes: optional device uint8 per read (z | max_gaps << 4), overriding sp->z and
+// sp->max_gaps read by read (serving batches that mix search modes)
 int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
                 const fm_search_params *sp, uint32_t *counts, uint64_t *offsets, uint32_t *pairs,
-                uint64_t pair_capacity, uint64_t *pairs_needed, cudaStream_t st);
+                uint64_t pair_capacity, uint64_t *pairs_needed, cudaStream_t st,
+                const uint8_t *modes = nullptr);
 
 // error word slots
 enum ErrSlot { kErrOcc = 0, kErrExact = 1, kErrDcalc = 2, kErrSearch = 3, kErrBuild = 4,
@@ -209,6 +232,37 @@ __device__ __forceinline__ void ldg256(const void *p, uint4 &a, uint4 &b) {
                  : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z),
                    "=r"(b.w)
                  : "l"(p));
+}
+
+// L1 policy of the random gathers.  Checkpoint blocks, pair blocks and the interval-table
+// sectors of levels >= kL1TableLevel are read once per search node at uniformly random places
+// of a table far larger than L1; they are loaded without allocating L1 lines, so that they do
+// not evict the lines that are reused (the shallow table levels, the occurrence bits, the pair
+// superblock counts), which stay in L1 across nodes, queries and warps of the SM.
+constexpr bool kGatherNoL1 = true;
+constexpr uint32_t kL1TableLevel = 8;
+__device__ __forceinline__ void ldg256_na(const void *p, uint4 &a, uint4 &b) {
+    if constexpr (kGatherNoL1) {
+        asm("ld.global.nc.L1::no_allocate.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+            : "l"(p));
+    } else {
+        ldg256(p, a, b);
+    }
+}
+
+__device__ __forceinline__ uint32_t ldg32_na(const uint32_t *p) {
+    uint32_t v;
+    if constexpr (kGatherNoL1) asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    else v = __ldg(p);
+    return v;
+}
+
+__device__ __forceinline__ uint2 ldg64_na(const uint2 *p) {
+    uint2 v;
+    if constexpr (kGatherNoL1) asm("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    else v = __ldg(p);
+    return v;
 }
 
 __device__ __forceinline__ uint64_t u64of(uint32_t lo, uint32_t hi) {
@@ -243,21 +297,21 @@ __device__ __forceinline__ void load_block(const uint8_t *blocks, uint32_t j, ui
                                            Blk<I> &B) {
     const uint8_t *p = blocks + (size_t)j * block_bytes(I);
     uint4 a, b;
-    ldg256(p, a, b);
+    ldg256_na(p, a, b);
     B.cnt = a;
     B.w[0] = u64of(b.x, b.y);
     if constexpr (I >= 64) B.w[1] = u64of(b.z, b.w);
     if constexpr (I >= 128) {
         // every word is assigned once; a sector no offset needs is not read
         uint4 c = make_uint4(0, 0, 0, 0), d = make_uint4(0, 0, 0, 0);
-        if (upto > 64) ldg256(p + 32, c, d);
+        if (upto > 64) ldg256_na(p + 32, c, d);
         B.w[2] = u64of(c.x, c.y);
         B.w[3] = u64of(c.z, c.w);
         if constexpr (I == 256) {
             uint4 e = make_uint4(0, 0, 0, 0), f;
             B.w[4] = u64of(d.x, d.y);
             B.w[5] = u64of(d.z, d.w);
-            if (upto > 192) ldg256(p + 64, e, f);
+            if (upto > 192) ldg256_na(p + 64, e, f);
             B.w[6] = u64of(e.x, e.y);
             B.w[7] = u64of(e.z, e.w);
         }
@@ -267,7 +321,7 @@ __device__ __forceinline__ void load_block(const uint8_t *blocks, uint32_t j, ui
 // Interval-table access (see IndexView): level j starts at entry (and bit) 4^j.
 __device__ __forceinline__ uint32_t kt_base(uint32_t j) { return 1u << (2u * j); }
 __device__ __forceinline__ uint2 kt_get(const IndexView &ix, uint32_t j, uint32_t code) {
-    return __ldg(ix.kt + kt_base(j) + code);
+    return j >= kL1TableLevel ? ldg64_na(ix.kt + kt_base(j) + code) : __ldg(ix.kt + kt_base(j) + code);
 }
 // occurrence bits of the four extensions 4c .. 4c+3 at level j >= 1 (bit b: extension b)
 __device__ __forceinline__ uint32_t kt_occ4(const IndexView &ix, uint32_t j, uint32_t c) {
@@ -282,7 +336,8 @@ __device__ __forceinline__ uint32_t kt_occ1(const IndexView &ix, uint32_t j, uin
 __device__ __forceinline__ void kt_get4(const IndexView &ix, uint32_t j, uint32_t c, uint32_t k[4],
                                         uint32_t l[4]) {
     uint4 a, b;
-    ldg256(ix.kt + kt_base(j) + 4u * c, a, b);
+    if (j >= kL1TableLevel) ldg256_na(ix.kt + kt_base(j) + 4u * c, a, b);
+    else ldg256(ix.kt + kt_base(j) + 4u * c, a, b);
     k[0] = a.x; l[0] = a.y; k[1] = a.z; l[1] = a.w;
     k[2] = b.x; l[2] = b.y; k[3] = b.z; l[3] = b.w;
 }
@@ -303,8 +358,8 @@ struct PairBlk {
 
 __device__ __forceinline__ void load_pair_block(const IndexView &ix, uint32_t j, uint32_t c, PairBlk &B) {
     const uint8_t *p = ix.pblk + (size_t)j * 64;
-    B.cw = __ldg((const uint32_t *)p + (c >> 1));
-    ldg256(p + 32, B.s0, B.s1);
+    B.cw = ldg32_na((const uint32_t *)p + (c >> 1));
+    ldg256_na(p + 32, B.s0, B.s1);
 }
 
 // Bit 3 of each nibble of the result is set exactly where that nibble of w equals pair c:

@@ -194,15 +194,20 @@ __global__ void __launch_bounds__(128) k_exact(IndexView ix, const uint8_t *__re
 
 // -------------------------------------------------------------------------------------------
 // D lower bound by forward extension on the index of reverse(R), one thread per query.
-// qmeta[q] = { D breakpoints 0..3, D breakpoints 4..7, read start, m | strand << 8 }, with
-// breakpoint j = first position i at which D(i) >= j+1 (255: never), so that
-// D(i) = #{j : bp_j <= i}.
+// qmeta[q * stride] = { D breakpoints 0..3, D breakpoints 4..7, read start,
+// m | strand << 8 | mode << 16 }, mode = the query's search mode byte (differences allowed in
+// bits 0-3, indel columns allowed in bits 4-7: modes[r] for read r, or defmode),
+// with breakpoint j = first position i at which D(i) >= j+1 (255: never), so that
+// D(i) = #{j : bp_j <= i}.  With stride kStageU4 (the staging record of the persistent search)
+// the next four uint4 hold the query itself, oriented for its strand: W[i] at bits 2(i%16) of
+// 32-bit word i/16 (words past the query's end are left as they were).
 // -------------------------------------------------------------------------------------------
 template <int I>
 __global__ void __launch_bounds__(128) k_dcalc(IndexView rv, const uint8_t *__restrict__ reads,
                                                const uint32_t *__restrict__ offs, uint32_t nr,
                                                uint32_t strands, uint4 *__restrict__ qmeta,
-                                               uint8_t *__restrict__ D_out,
+                                               uint32_t stride, const uint8_t *__restrict__ modes,
+                                               uint32_t defmode, uint8_t *__restrict__ D_out,
                                                uint32_t *__restrict__ err) {
     const uint32_t nq = nr * strands;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
@@ -216,6 +221,8 @@ __global__ void __launch_bounds__(128) k_dcalc(IndexView rv, const uint8_t *__re
         if (bad) atomicOr(err, kErrReadLen);
         uint32_t k = 0, l = rv.n, z = 0;
         uint8_t *Dq = D_out ? D_out + (size_t)strands * s + (size_t)strand * m : nullptr;
+        uint32_t *Wq = (qmeta && stride == kStageU4) ? (uint32_t *)(qmeta + (size_t)q * stride + 1) : nullptr;
+        uint32_t wacc = 0;   // symbols of the current 16-symbol word of W
         for (uint32_t i = 0; i < m && !bad; ++i) {
             uint32_t b = strand ? reads[s + m - 1 - i] : reads[s + i];
             if (b > 3u) {
@@ -224,6 +231,13 @@ __global__ void __launch_bounds__(128) k_dcalc(IndexView rv, const uint8_t *__re
                 break;
             }
             if (strand) b = 3u - b;
+            if (Wq) {
+                wacc |= b << (2u * (i & 15u));
+                if ((i & 15u) == 15u || i + 1u == m) {
+                    Wq[i >> 4] = wacc;
+                    wacc = 0;
+                }
+            }
             const uint32_t pk = k, pl = l + 1u;
             const uint32_t jk = pk / I, jl = pl / I;
             Blk<I> Bk, Bl;
@@ -256,8 +270,8 @@ __global__ void __launch_bounds__(128) k_dcalc(IndexView rv, const uint8_t *__re
             mt.y = bp_hi;
             mt.z = s;
             // a bad query is given length 0: the search then reports nothing for it
-            mt.w = (bad ? 0u : m) | (strand << 8);
-            qmeta[q] = mt;
+            mt.w = (bad ? 0u : m) | (strand << 8) | ((modes ? (uint32_t)modes[r] : defmode) << 16);
+            qmeta[(size_t)q * stride] = mt;
         }
     }
 }
@@ -490,6 +504,7 @@ uint32_t kmer_depth_for(const fm_index *h) {
 }
 
 int ensure_kmer(fm_index *h, cudaStream_t st) {
+    if (h->borrowed) return FM_OK;   // a search context uses its owner's tables as they are
     const uint32_t L = kmer_depth_for(h);
     if (L == h->kt_depth) return FM_OK;
     FM_CUDA_TRY(h, cudaStreamSynchronize(st));   // no kernel of this stream reads the old tables
@@ -531,7 +546,7 @@ int ensure_kmer(fm_index *h, cudaStream_t st) {
 }
 
 int ensure_pairs(fm_index *h, cudaStream_t st) {
-    if (!h->tune.pairs || h->pairs_built) return FM_OK;
+    if (!h->tune.pairs || h->pairs_built || h->borrowed) return FM_OK;
     const uint64_t N = h->n + 1;                    // rows
     const uint64_t nblk = N / kPairRows + 1;        // rank positions 0..N
     const uint64_t nsb = N / kPairSuper + 1;
@@ -630,7 +645,8 @@ int launch_exact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32
 }
 
 int launch_dcalc(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
-                 uint32_t strands, uint4 *qmeta, uint8_t *D_out, cudaStream_t st) {
+                 uint32_t strands, uint4 *qmeta, uint8_t *D_out, cudaStream_t st, uint32_t stride,
+                 const uint8_t *modes, uint32_t defmode) {
     uint64_t nq = (uint64_t)n_reads * strands;
     if (nq == 0) return FM_OK;
     IndexView rv = view_rev(h);
@@ -638,10 +654,10 @@ int launch_dcalc(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32
     const int block = 128;
     int grid = grid_occ(h, nq, block);
     switch (h->interval) {
-        case 32: k_dcalc<32><<<grid, block, 0, st>>>(rv, reads, offs, n_reads, strands, qmeta, D_out, err); break;
-        case 64: k_dcalc<64><<<grid, block, 0, st>>>(rv, reads, offs, n_reads, strands, qmeta, D_out, err); break;
-        case 128: k_dcalc<128><<<grid, block, 0, st>>>(rv, reads, offs, n_reads, strands, qmeta, D_out, err); break;
-        default: k_dcalc<256><<<grid, block, 0, st>>>(rv, reads, offs, n_reads, strands, qmeta, D_out, err); break;
+        case 32: k_dcalc<32><<<grid, block, 0, st>>>(rv, reads, offs, n_reads, strands, qmeta, stride, modes, defmode, D_out, err); break;
+        case 64: k_dcalc<64><<<grid, block, 0, st>>>(rv, reads, offs, n_reads, strands, qmeta, stride, modes, defmode, D_out, err); break;
+        case 128: k_dcalc<128><<<grid, block, 0, st>>>(rv, reads, offs, n_reads, strands, qmeta, stride, modes, defmode, D_out, err); break;
+        default: k_dcalc<256><<<grid, block, 0, st>>>(rv, reads, offs, n_reads, strands, qmeta, stride, modes, defmode, D_out, err); break;
     }
     FM_CUDA_TRY(h, cudaGetLastError());
     return FM_OK;

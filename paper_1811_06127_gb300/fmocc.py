@@ -47,7 +47,11 @@ class fm_info_t(C.Structure):
 class fm_profile(C.Structure):
     _fields_ = [("ms_dcalc", C.c_float), ("ms_search", C.c_float), ("ms_canon", C.c_float),
                 ("ms_total", C.c_float), ("launches", C.c_uint32), ("passes", C.c_uint32),
-                ("graph", C.c_uint32), ("reserved", C.c_uint32)]
+                ("graph", C.c_uint32), ("fill_counters", C.c_uint32),
+                ("exact_steps", C.c_uint64), ("exact_lanes", C.c_uint64),
+                ("exact_lanes2", C.c_uint64), ("general_steps", C.c_uint64),
+                ("general_lanes", C.c_uint64), ("admissions", C.c_uint64),
+                ("admitted", C.c_uint64), ("parked", C.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -65,13 +69,14 @@ class fm_tuning(C.Structure):
                 ("chunk", C.c_uint32), ("plain_block", C.c_uint32), ("graphs", C.c_uint32),
                 ("occ_per_thread", C.c_uint32), ("l2_fetch_bytes", C.c_uint32),
                 ("canonical", C.c_uint32), ("kmer_depth", C.c_uint32),
-                ("pair_steps", C.c_uint32)]
+                ("pair_steps", C.c_uint32), ("refill", C.c_uint32), ("chain2_min", C.c_uint32),
+                ("stage", C.c_uint32)]
 
 
 class fm_server_params(C.Structure):
     _fields_ = [("max_batch_reads", C.c_uint32), ("strands", C.c_uint32),
                 ("frontier_budget", C.c_uint64), ("kernel", C.c_uint32),
-                ("reserved", C.c_uint32)]
+                ("inflight", C.c_uint32)]
 
 
 class fm_server_result(C.Structure):
@@ -79,7 +84,7 @@ class fm_server_result(C.Structure):
                 ("counts", C.POINTER(C.c_uint32)), ("offsets", C.POINTER(C.c_uint64)),
                 ("pairs", C.POINTER(C.c_uint32)), ("t_submit_ns", C.c_uint64),
                 ("t_start_ns", C.c_uint64), ("t_done_ns", C.c_uint64),
-                ("batch_reads", C.c_uint32), ("reserved", C.c_uint32)]
+                ("batch_reads", C.c_uint32), ("batch_id", C.c_uint32)]
 
 
 # every symbol include/fmocc.h declares
@@ -435,13 +440,13 @@ def fm_inexact_fetch(h: Index, pairs: torch.Tensor, stream=None):
 
 def fm_set_tuning(h: Index, warps_per_block=0, blocks_per_sm=0, chunk=0, plain_block=0,
                   graphs=0, occ_per_thread=0, l2_fetch_bytes=0, canonical=0, kmer_depth=0,
-                  pair_steps=0):
+                  pair_steps=0, refill=0, chain2_min=0, stage=0):
     """Zero keeps a knob; graphs, canonical and pair_steps: 1 on, 2 off; kmer_depth: 1..14,
     KMER_AUTO or KMER_OFF.  Speed and memory only, never results (the tables and pair steps
     answer the cache-locality question of Sec. 4.2; the rest have no counterpart in the
     paper)."""
     t = fm_tuning(warps_per_block, blocks_per_sm, chunk, plain_block, graphs, occ_per_thread,
-                  l2_fetch_bytes, canonical, kmer_depth, pair_steps)
+                  l2_fetch_bytes, canonical, kmer_depth, pair_steps, refill, chain2_min, stage)
     _check(load_library().fm_set_tuning(h.ptr, C.byref(t)), h)
 
 
@@ -452,7 +457,8 @@ def fm_get_tuning(h: Index) -> dict:
     return {"warps_per_block": t.warps_per_block, "blocks_per_sm": t.blocks_per_sm,
             "chunk": t.chunk, "plain_block": t.plain_block, "graphs": t.graphs,
             "occ_per_thread": t.occ_per_thread, "l2_fetch_bytes": t.l2_fetch_bytes,
-            "canonical": t.canonical, "kmer_depth": t.kmer_depth, "pair_steps": t.pair_steps}
+            "canonical": t.canonical, "kmer_depth": t.kmer_depth, "pair_steps": t.pair_steps,
+            "refill": t.refill, "chain2_min": t.chain2_min, "stage": t.stage}
 
 
 def fm_probe_gather(buf: torch.Tensor, granule: int, threads: int, per_thread: int,
@@ -474,12 +480,12 @@ class Server:
     interval sets.  While it runs, the index handle belongs to the server."""
 
     def __init__(self, h: Index, max_batch_reads: int = 0, strands: int = 2,
-                 frontier_budget: int = 0, kernel="persistent"):
+                 frontier_budget: int = 0, kernel="persistent", inflight: int = 0):
         self.lib = load_library()
         self.h = h
         self.strands = strands
         kern = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
-        p = fm_server_params(max_batch_reads, strands, frontier_budget, kern, 0)
+        p = fm_server_params(max_batch_reads, strands, frontier_budget, kern, inflight)
         out = C.c_void_p()
         _check(self.lib.fm_server_start(h.ptr, C.byref(p), C.byref(out)), h)
         self.ptr = out
@@ -510,7 +516,8 @@ class Server:
                "pairs": (np.ctypeslib.as_array(r.pairs, shape=(2 * tot,)).reshape(tot, 2).copy()
                          if tot else np.zeros((0, 2), np.uint32)),
                "t_submit_ns": r.t_submit_ns, "t_start_ns": r.t_start_ns,
-               "t_done_ns": r.t_done_ns, "batch_reads": r.batch_reads}
+               "t_done_ns": r.t_done_ns, "batch_reads": r.batch_reads,
+               "batch_id": r.batch_id}
         _check(self.lib.fm_server_release(self.ptr, ticket))
         return out
 

@@ -297,6 +297,33 @@ def test_inexact_matches_oracle(fm, z, gaps):
     _inexact_case(fm, R, reads, z, gaps, 64)
 
 
+@pytest.mark.parametrize("z,gaps,n_reads,min_len,max_len", [(2, 1, 600, 30, 150), (5, 3, 40, 8, 20)])
+def test_scheduler_options_same_results(fm, z, gaps, n_reads, min_len, max_len):
+    """The persistent kernel's scheduler options change speed only: queries staged in shared
+    memory or read through L1, the threshold for stepping second exact chains, and the pool
+    level below which a warp takes queries, each equal to Listing 2.  The second case (short
+    reads, z = 5 with 3 gaps) fills the pools past their size and spills."""
+    R = synth.repeat_text(1811061282, 300_000, families=30, min_len=300, max_len=3000)
+    reads = synth.sample_reads(33, R, n_reads, min_len, max_len, sub_rate=0.02,
+                               indel_rate=0.005, both_strands=True, random_frac=0.05)
+    want = oracle.Index(R, "sais").inexact(reads.codes, reads.offs, z, gaps, strands=2,
+                                           canonical=True)
+    h = fm.fm_build(R)
+    codes, offs = fm.to_device_reads(reads)
+    for stage in (1, 2):
+        for chain2_min, refill in ((1, 32), (16, 32), (32, 96), (16, 288)):
+            fm.fm_set_tuning(h, stage=stage, chain2_min=chain2_min, refill=refill, chunk=8)
+            t = fm.fm_get_tuning(h)
+            assert (t["stage"], t["chain2_min"], t["refill"]) == (stage, chain2_min, refill)
+            for _ in range(2):   # eager, then graph replay
+                c, o, p = fm.fm_inexact(h, codes, offs, z, gaps, strands=2)
+                tag = (stage, chain2_min, refill)
+                assert np.array_equal(_u32(c), want["counts"]), tag
+                assert np.array_equal(o.cpu().numpy().astype(np.uint64), want["offsets"]), tag
+                assert np.array_equal(_u32(p), want["pairs"]), tag
+    h.close()
+
+
 def _best_of(want):
     """Per query, the intervals of its minimum cost (from the oracle's sets and costs)."""
     counts, pairs, costs = [], [], []

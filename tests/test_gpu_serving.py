@@ -81,6 +81,101 @@ def test_alone_equals_mixed(fm):
     h.close()
 
 
+def _alone(fm, h, reads, z, g):
+    codes, offs = fm.to_device_reads(reads)
+    c, o, p = fm.fm_inexact(h, codes, offs, z, g, strands=2)
+    return (c.cpu().numpy().view(np.uint32), o.cpu().numpy().astype(np.uint64),
+            p.cpu().numpy().view(np.uint32))
+
+
+def _check_same(got, want):
+    assert got["status"] == 0
+    assert np.array_equal(got["counts"], want[0])
+    assert np.array_equal(got["offsets"], want[1])
+    assert np.array_equal(got["pairs"], want[2])
+
+
+@pytest.mark.parametrize("inflight", [1, 2])
+def test_request_starts_while_a_batch_runs(fm, inflight):
+    """A request submitted while a long batch is on the GPU starts before that batch
+    finishes when two batches may be in flight (and only after it with one), and its result is
+    what fm_inexact returns for it alone."""
+    R = synth.repeat_text(1811061277, 8_000_000, families=100, min_len=300, max_len=6000)
+    h = fm.fm_build(R)
+    # a batch of about a second: z = 4 with 2 gaps on long reads
+    big = synth.sample_reads(71, R, 200_000, 150, 250, sub_rate=0.02, indel_rate=0.002,
+                             both_strands=True)
+    small = synth.sample_reads(72, R, 50, 50, 150, sub_rate=0.01, both_strands=True)
+    want_big, want_small = _alone(fm, h, big, 4, 2), _alone(fm, h, small, 1, 0)
+    with fm.Server(h, max_batch_reads=200_000, strands=2, inflight=inflight) as srv:
+        ta = srv.submit(big.codes, big.offs, 4, 2)
+        time.sleep(0.1)   # the long batch has been taken by a worker
+        tb = srv.submit(small.codes, small.offs, 1, 0)
+        ra, rb = srv.wait(ta), srv.wait(tb)
+    _check_same(ra, want_big)
+    _check_same(rb, want_small)
+    # the premise: the small request arrived while the long batch ran
+    assert ra["t_start_ns"] < rb["t_submit_ns"] < ra["t_done_ns"], \
+        (ra["t_start_ns"], rb["t_submit_ns"], ra["t_done_ns"])
+    assert ra["batch_id"] != rb["batch_id"]
+    if inflight == 2:
+        # it started before the long batch finished (its kernels take SMs as the long
+        # batch's persistent CTAs drain)
+        assert rb["t_start_ns"] < ra["t_done_ns"]
+    else:
+        assert rb["t_start_ns"] >= ra["t_done_ns"]        # one batch at a time
+    h.close()
+
+
+def test_one_batch_mixes_search_modes(fm):
+    """Requests of different search modes that wait together are searched in one batch
+    (z and max_gaps are carried read by read), each with its own mode's result."""
+    R = synth.repeat_text(1811061278, 4_000_000, families=60, min_len=300, max_len=4000)
+    h = fm.fm_build(R)
+    blockers = [synth.sample_reads(73 + i, R, 100_000, 100, 250, sub_rate=0.02,
+                                   indel_rate=0.002, both_strands=True) for i in range(2)]
+    reqs = [(synth.sample_reads(80 + i, R, 20 + 7 * i, 50, 250, sub_rate=0.01,
+                                indel_rate=0.0005, both_strands=True), MODES[i % 3])
+            for i in range(24)]
+    want = [_alone(fm, h, r, z, g) for r, (z, g) in reqs]
+    with fm.Server(h, max_batch_reads=200_000, strands=2, inflight=2) as srv:
+        tk = [srv.submit(b.codes, b.offs, 3, 2) for b in blockers]   # both workers busy
+        time.sleep(0.02)
+        ts = [srv.submit(r.codes, r.offs, z, g) for r, (z, g) in reqs]
+        res = [srv.wait(t) for t in ts]
+        for t in tk:
+            srv.wait(t)
+    for got, w in zip(res, want):
+        _check_same(got, w)
+    modes_by_batch = {}
+    for got, (_, m) in zip(res, reqs):
+        modes_by_batch.setdefault(got["batch_id"], set()).add(m)
+    assert max(len(v) for v in modes_by_batch.values()) == 3
+    h.close()
+
+
+def test_frontier_budget_splits_batches(fm):
+    """With a frontier budget that holds the search scratch of only part of the backlog, the
+    backlog runs as several batches (sized by the scratch model, and split when a search
+    would outgrow the budget), and every result is still the request's own."""
+    R = synth.repeat_text(1811061279, 4_000_000, families=60, min_len=300, max_len=4000)
+    h = fm.fm_build(R)
+    reqs = [synth.sample_reads(90 + i, R, 4000, 50, 250, sub_rate=0.01, indel_rate=0.0005,
+                               both_strands=True) for i in range(16)]
+    want = [_alone(fm, h, r, 2, 1) for r in reqs]
+    budget = 420 << 20   # the spill region of the persistent kernel plus a few tens of MB
+    with fm.Server(h, max_batch_reads=262_144, strands=2, inflight=1,
+                   frontier_budget=budget) as srv:
+        ts = [srv.submit(r.codes, r.offs, 2, 1) for r in reqs]
+        res = [srv.wait(t) for t in ts]
+        st = srv.stats()
+    for got, w in zip(res, want):
+        _check_same(got, w)
+    assert len({g["batch_id"] for g in res}) >= 2
+    assert st["batches"] >= 2
+    h.close()
+
+
 def test_server_errors(fm):
     R = synth.uniform_text(3, 50_000)
     h = fm.fm_build(R)
