@@ -407,11 +407,11 @@ typedef struct fm_tuning {
                                    branch.  2: one symbol per step (stats exactly as described) */
     uint32_t refill;            /* persistent kernel: a warp takes more queries from the work
                                    queue when its node pools hold fewer nodes than this
-                                   (1..288; default 32) */
+                                   (1..288; default 48) */
     uint32_t chain2_min;        /* persistent kernel: each lane holds up to two exact chains;
                                    the warp steps the second ones only while at least this many
                                    lanes hold one, else they wait for a first place (1..32;
-                                   default 1: always) */
+                                   default 12; 1: always) */
     uint32_t stage;             /* persistent kernel: 1 stages each query a warp works on in
                                    shared memory (its 2-bit symbols, D breakpoints, length, mode
                                    and number; 16 slots per warp, taken and freed in groups of

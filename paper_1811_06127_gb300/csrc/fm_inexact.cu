@@ -529,13 +529,15 @@ __device__ __forceinline__ void emit_leaves(const SearchCfg &c, int lane, bool a
 constexpr int kFlushSteps = 512;   // exact steps between two flushes of the ended-chain counts
 constexpr int kPoolEntries = 320;  // node pool entries per warp
 
-template <int I, bool STAGE>
+// PROF: the instantiation that counts the step fill (c.fill); the counting is compiled out of
+// the others, where its live state alone cost 6% of the search time under the 64-register cap.
+template <int I, bool STAGE, bool PROF>
 __global__ void __launch_bounds__(256, I <= 128 ? 4 : 2) k_inexact_persistent(SearchCfg c, int stk, uint4 *spill_all,
                                                             uint32_t spill_cap) {
     extern __shared__ uint4 smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const bool prof = c.fill != nullptr;
+    constexpr bool prof = PROF;
     uint32_t *wbase = reinterpret_cast<uint32_t *>(smem) + (size_t)wib * warp_smem_words(stk, STAGE, prof);
     Pool<STAGE> st;
     if constexpr (STAGE) {
@@ -1481,44 +1483,54 @@ static int launch_search(fm_index *h, const SearchCfg &c, uint32_t kernel, uint4
         k_inexact_plain<I><<<(T + pb - 1) / pb, pb, 0, st>>>(c, stacks, cap, T);
     } else {
         const bool fill = c.fill != nullptr;
-        if (h->tune.stage)
-            k_inexact_persistent<I, true><<<grid, block, persistent_smem(block, stk, true, fill), st>>>(
-                c, stk, spill, spill_cap);
-        else
-            k_inexact_persistent<I, false><<<grid, block, persistent_smem(block, stk, false, fill), st>>>(
-                c, stk, spill, spill_cap);
+        const size_t sm = persistent_smem(block, stk, h->tune.stage != 0, fill);
+        if (h->tune.stage) {
+            if (fill) k_inexact_persistent<I, true, true><<<grid, block, sm, st>>>(c, stk, spill, spill_cap);
+            else k_inexact_persistent<I, true, false><<<grid, block, sm, st>>>(c, stk, spill, spill_cap);
+        } else {
+            if (fill) k_inexact_persistent<I, false, true><<<grid, block, sm, st>>>(c, stk, spill, spill_cap);
+            else k_inexact_persistent<I, false, false><<<grid, block, sm, st>>>(c, stk, spill, spill_cap);
+        }
     }
     FM_CUDA_TRY(h, cudaGetLastError());
     return FM_OK;
 }
 
 template <int I>
-static cudaError_t set_smem_attr(size_t smem, bool stage) {
-    return stage ? cudaFuncSetAttribute(k_inexact_persistent<I, true>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                 : cudaFuncSetAttribute(k_inexact_persistent<I, false>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+static cudaError_t set_smem_attr(size_t smem, bool stage, bool fill) {
+    const int v = (int)smem;
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (stage) return fill ? cudaFuncSetAttribute(k_inexact_persistent<I, true, true>, a, v)
+                           : cudaFuncSetAttribute(k_inexact_persistent<I, true, false>, a, v);
+    return fill ? cudaFuncSetAttribute(k_inexact_persistent<I, false, true>, a, v)
+                : cudaFuncSetAttribute(k_inexact_persistent<I, false, false>, a, v);
 }
 
 template <int I>
-static int occupancy_blocks(int block, size_t smem, bool stage) {
+static int occupancy_blocks(int block, size_t smem, bool stage, bool fill) {
     int nb = 0;
-    if (stage) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_inexact_persistent<I, true>, block, smem);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_inexact_persistent<I, false>, block, smem);
+    if (stage) {
+        if (fill) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_inexact_persistent<I, true, true>, block, smem);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_inexact_persistent<I, true, false>, block, smem);
+    } else {
+        if (fill) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_inexact_persistent<I, false, true>, block, smem);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_inexact_persistent<I, false, false>, block, smem);
+    }
     return nb;
 }
 
-static cudaError_t set_smem_attr_any(uint32_t I, size_t smem, bool stage) {
-    return I == 32 ? set_smem_attr<32>(smem, stage)
-                   : (I == 64 ? set_smem_attr<64>(smem, stage)
-                              : (I == 128 ? set_smem_attr<128>(smem, stage) : set_smem_attr<256>(smem, stage)));
+static cudaError_t set_smem_attr_any(uint32_t I, size_t smem, bool stage, bool fill) {
+    return I == 32 ? set_smem_attr<32>(smem, stage, fill)
+                   : (I == 64 ? set_smem_attr<64>(smem, stage, fill)
+                              : (I == 128 ? set_smem_attr<128>(smem, stage, fill)
+                                          : set_smem_attr<256>(smem, stage, fill)));
 }
 
-static int occupancy_any(uint32_t I, int block, size_t smem, bool stage) {
-    return I == 32 ? occupancy_blocks<32>(block, smem, stage)
-                   : (I == 64 ? occupancy_blocks<64>(block, smem, stage)
-                              : (I == 128 ? occupancy_blocks<128>(block, smem, stage)
-                                          : occupancy_blocks<256>(block, smem, stage)));
+static int occupancy_any(uint32_t I, int block, size_t smem, bool stage, bool fill) {
+    return I == 32 ? occupancy_blocks<32>(block, smem, stage, fill)
+                   : (I == 64 ? occupancy_blocks<64>(block, smem, stage, fill)
+                              : (I == 128 ? occupancy_blocks<128>(block, smem, stage, fill)
+                                          : occupancy_blocks<256>(block, smem, stage, fill)));
 }
 
 // fills the profile from the phase events: ev[0] start, ev[1] before the (last) search pass,
@@ -1607,7 +1619,7 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
     // carveout (and so the L1 left beside it) from it
     const size_t smem = persistent_smem(block, stk, tu.stage != 0, want_fill);
     int bps = (int)tu.blocks_per_sm;
-    const int occ = occupancy_any(I, block, smem, tu.stage != 0);
+    const int occ = occupancy_any(I, block, smem, tu.stage != 0, want_fill);
     if (bps <= 0 || bps > occ) bps = occ;
     if (bps <= 0) return FM_OK;
     const int grid = h->sms * bps;
@@ -1656,7 +1668,7 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
             cudaGraphExecDestroy(h->gexec);
             h->gexec = nullptr;
         }
-        cudaError_t e = set_smem_attr_any(I, smem, tu.stage != 0);
+        cudaError_t e = set_smem_attr_any(I, smem, tu.stage != 0, want_fill);
         if (e != cudaSuccess) return cuda_status(h, e, "cudaFuncSetAttribute");
         FM_CUDA_TRY(h, cudaFuncSetAttribute(k_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)(8192 * sizeof(uint64_t))));
@@ -1739,7 +1751,7 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
         h->graph_captures += 1;
     }
     {   // an eager call since the capture may have set another size: restore the graph's
-        cudaError_t e = set_smem_attr_any(I, smem, tu.stage != 0);
+        cudaError_t e = set_smem_attr_any(I, smem, tu.stage != 0, want_fill);
         if (e != cudaSuccess) return cuda_status(h, e, "cudaFuncSetAttribute");
     }
     FM_CUDA_TRY(h, cudaGraphLaunch(h->gexec, st));
@@ -1861,10 +1873,10 @@ int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_
     const int stk = pool_entries(tu);   // pool entries per warp (see the kernel)
     // the attribute is the launch's own size (see the graph path)
     const size_t smem = persistent_smem(block, stk, tu.stage != 0, want_fill);
-    cudaError_t e = set_smem_attr_any(I, smem, tu.stage != 0);
+    cudaError_t e = set_smem_attr_any(I, smem, tu.stage != 0, want_fill);
     if (e != cudaSuccess) return cuda_status(h, e, "cudaFuncSetAttribute");
     int bps = (int)tu.blocks_per_sm;
-    const int occ = occupancy_any(I, block, smem, tu.stage != 0);
+    const int occ = occupancy_any(I, block, smem, tu.stage != 0, want_fill);
     if (bps <= 0 || bps > occ) bps = occ;
     if (bps <= 0) return set_error(h, FM_ECUDA, "persistent kernel does not fit on an SM");
     int grid = h->sms * bps;

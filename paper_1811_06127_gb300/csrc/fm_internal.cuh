@@ -49,8 +49,10 @@ struct IndexView {
     // Pair table (0 when absent): for every row i, the two symbols before suffix SA[i],
     // BWT[LF(i)] and BWT[i], as one 4-bit code 4 b1 + b2, so that one rank over pairs moves an
     // interval back two symbols.  64-row blocks of 64 bytes: uint16 cnt[16] (pairs in the
-    // rows of its superblock of 32768 rows before the block, special rows excluded), then 64
-    // nibbles (row r of the block at bits 4(r%8) of 32-bit word r/8).  psb[s][c]: pairs c in
+    // rows of its superblock of 32768 rows before the block, special rows excluded), then the
+    // 64 rows' 4-bit pair codes as bit planes: 32-bit word 4h + p holds bit p of the codes of
+    // rows 32h .. 32h+31 (row 32h + r at bit r), so one uint4 holds all four planes of a half
+    // block.  psb[s][c]: pairs c in
     // the rows before superblock s; pc2[c]: rows whose suffix sorts before every string
     // starting with pair c.  The $ row and the row whose LF is the $ row have no pair: stored
     // as pair 0 and excluded from the counts (prow_a, prow_b).
@@ -98,8 +100,8 @@ struct Tuning {
     uint32_t kmer = FM_KMER_AUTO;   // interval-table depth setting (FM_KMER_AUTO, FM_KMER_OFF, 1..14)
     uint32_t pairs = 1;             // exact continuations two symbols per step from the pair table
     uint32_t l2_fetch = 0;   // 0: leave the context's limit alone
-    uint32_t refill = 32;    // a warp takes more queries when its pools hold fewer nodes
-    uint32_t chain2_min = 1; // lanes whose second exact chain is live for the warp to step it
+    uint32_t refill = 48;    // a warp takes more queries when its pools hold fewer nodes
+    uint32_t chain2_min = 12; // lanes whose second exact chain is live for the warp to step it
     uint32_t stage = 0;      // persistent kernel stages its queries in shared memory
 };
 
@@ -350,7 +352,7 @@ __device__ __forceinline__ uint32_t low_mask(uint32_t width) {
 }
 
 // The part of a pair block one rank of pair c needs: the word holding cnt[c] (two uint16 per
-// word, low half first) and the 64 nibbles.
+// word, low half first) and the bit planes of the 64 rows (s0: rows 0-31, s1: rows 32-63).
 struct PairBlk {
     uint32_t cw;
     uint4 s0, s1;
@@ -362,30 +364,19 @@ __device__ __forceinline__ void load_pair_block(const IndexView &ix, uint32_t j,
     ldg256_na(p + 32, B.s0, B.s1);
 }
 
-// Bit 3 of each nibble of the result is set exactly where that nibble of w equals pair c:
-// with x = w ^ (c in every nibble), (x & 7) + 7 reaches bit 3 of its nibble only when the low
-// three bits are not all zero (and never carries into the next nibble), and OR-ing x adds bit 3
-// itself.
-__device__ __forceinline__ uint32_t pair_flags(uint32_t w, uint32_t pat) {
-    const uint32_t x = w ^ pat;
-    return ~(((x & 0x77777777u) + 0x77777777u) | x) & 0x88888888u;
-}
-
-// rows of a word (8 nibbles) below prefix length o, as a mask of nibble bit 3s
-__device__ __forceinline__ uint32_t pair_prefix(uint32_t o, int w) {
-    const int32_t left = (int32_t)o - 8 * w;
-    const uint32_t t = left <= 0 ? 0u : (left >= 8 ? 8u : (uint32_t)left);
-    return low_mask(4u * t) & 0x88888888u;
+// Rows among the 32 of one half block whose pair code is c: a row matches where every bit
+// plane agrees with the corresponding bit of c (planes XOR-ed with that bit spread over the
+// word are zero there).
+__device__ __forceinline__ uint32_t pair_eq32(const uint4 &pl, uint32_t c) {
+    const uint32_t s0 = 0u - (c & 1u), s1 = 0u - ((c >> 1) & 1u), s2 = 0u - ((c >> 2) & 1u),
+                   s3 = 0u - (c >> 3);
+    return ~((pl.x ^ s0) | (pl.y ^ s1) | (pl.z ^ s2) | (pl.w ^ s3));
 }
 
 // Pairs c among the first o rows (o in [0, 64]) of a pair block.
 __device__ __forceinline__ uint32_t pair_count_in(const PairBlk &B, uint32_t c, uint32_t o) {
-    const uint32_t s[8] = {B.s0.x, B.s0.y, B.s0.z, B.s0.w, B.s1.x, B.s1.y, B.s1.z, B.s1.w};
-    const uint32_t pat = c * 0x11111111u;
-    uint32_t n = 0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) n += __popc(pair_flags(s[w], pat) & pair_prefix(o, w));
-    return n;
+    const uint32_t olo = o < 32u ? o : 32u;
+    return __popc(pair_eq32(B.s0, c) & low_mask(olo)) + __popc(pair_eq32(B.s1, c) & low_mask(o - olo));
 }
 
 // Pairs c in rows [0, p) (rows without a pair excluded), B the pair block of p loaded for c.

@@ -366,18 +366,19 @@ __global__ void __launch_bounds__(256) k_kmer_bits(const uint2 *__restrict__ kt,
 
 // -------------------------------------------------------------------------------------------
 // Pair table.  Row i's pair is (BWT[LF(i)], BWT[i]) with LF(i) = C[b] + rank(b, i) + 1 for
-// b = BWT[i] (Eq. 4-5): the two symbols before suffix SA[i].  Thread per 8 rows (one nibble
-// word); the $ row and the row whose LF is the $ row have none (stored as 0, row b recorded).
+// b = BWT[i] (Eq. 4-5): the two symbols before suffix SA[i].  Thread per 32 rows (the four bit
+// planes of one half block); the $ row and the row whose LF is the $ row have none (stored as
+// 0, row b recorded).
 // -------------------------------------------------------------------------------------------
 template <int I>
 __global__ void __launch_bounds__(256) k_pair_sym(IndexView ix, uint8_t *__restrict__ pblk, uint64_t N,
                                                   uint32_t *__restrict__ row_b) {
-    const uint64_t words = (N + 7) / 8;
-    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < words;
+    const uint64_t halves = (N + 31) / 32;
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < halves;
          w += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t word = 0;
-        for (uint32_t t = 0; t < 8u; ++t) {
-            const uint64_t i64 = 8 * w + t;
+        uint32_t plane[4] = {0u, 0u, 0u, 0u};
+        for (uint32_t t = 0; t < 32u; ++t) {
+            const uint64_t i64 = 32 * w + t;
             if (i64 >= N) break;
             const uint32_t i = (uint32_t)i64;
             if (i == ix.dollar) continue;
@@ -395,10 +396,14 @@ __global__ void __launch_bounds__(256) k_pair_sym(IndexView ix, uint8_t *__restr
             Blk<I> L;
             load_block<I>(ix.blocks, jl, lf - jl * I + 1u, L);
             const uint32_t b1 = sym_in<I>(L, jl, lf);
-            word |= (4u * b1 + b) << (4u * t);
+            const uint32_t code = 4u * b1 + b;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) plane[p] |= ((code >> p) & 1u) << t;
         }
-        const uint64_t r0 = 8 * w;
-        *(uint32_t *)(pblk + (r0 / kPairRows) * 64 + 32 + ((r0 % kPairRows) / 8) * 4) = word;
+        const uint64_t r0 = 32 * w;
+        uint32_t *dst = (uint32_t *)(pblk + (r0 / kPairRows) * 64 + 32 + ((r0 % kPairRows) / 32) * 16);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) dst[p] = plane[p];
     }
 }
 
@@ -412,24 +417,18 @@ __global__ void __launch_bounds__(256) k_pair_counts(uint8_t *__restrict__ pblk,
          t += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t sbi = t / 16;
         const uint32_t c = (uint32_t)(t % 16);
-        const uint32_t pat = c * 0x11111111u;
         uint32_t acc = 0;
         const uint64_t j1 = (sbi + 1) * per < nblk ? (sbi + 1) * per : nblk;
         for (uint64_t j = sbi * per; j < j1; ++j) {
             uint8_t *blk = pblk + j * 64;
             *(uint16_t *)(blk + 2 * c) = (uint16_t)acc;
-            const uint32_t *sw = (const uint32_t *)(blk + 32);
+            const uint4 *sw = (const uint4 *)(blk + 32);
             const uint64_t r0 = j * kPairRows;
             const uint32_t rows = N > r0 ? (uint32_t)(N - r0 < kPairRows ? N - r0 : kPairRows) : 0u;
-            uint32_t n = 0;
-            for (uint32_t q = 0; q < 8u; ++q) {
-                const int32_t left = (int32_t)rows - 8 * (int32_t)q;
-                const uint32_t m = left <= 0 ? 0u : (left >= 8 ? 8u : (uint32_t)left);
-                uint32_t x = sw[q] ^ pat;
-                x |= x >> 1;
-                x |= x >> 2;
-                n += __popc(~x & 0x11111111u & low_mask(4u * m));
-            }
+            PairBlk P;
+            P.s0 = sw[0];
+            P.s1 = sw[1];
+            uint32_t n = pair_count_in(P, c, rows);   // rows >= N hold code 0 and are not counted
             if (c == 0u)
                 n -= (prow_a >= r0 && prow_a < r0 + rows ? 1u : 0u) +
                      (prow_b >= r0 && prow_b < r0 + rows ? 1u : 0u);
