@@ -52,10 +52,8 @@ BLOCK_BYTES = {32: 32, 64: 32, 128: 64, 256: 96}
 # keyed by (interval, reference bp, reads, canonical enumeration on, interval-table depth, pair
 # steps on) and reported only when the run matches that configuration.  An entry is removed
 # when the kernel changes and added back from a fresh capture.
-TRAFFIC_NCU = {}
-# the last capture, taken before the kernel gained the end-restriction test (a uniform branch
-# on a kernel argument, not taken when the restriction is off): reported beside a null traffic
-TRAFFIC_PREVIOUS = {(64, 2_000_000_000, 10_000_000, True, 13, True): 3.204977914368e12 + 9.60976640e8}
+TRAFFIC_NCU = {(64, 2_000_000_000, 10_000_000, True, 13, True): 2.240493413888e12 + 5.34695168e8,
+               (32, 2_000_000_000, 10_000_000, True, 13, True): 2.272186729984e12 + 5.33291008e8}
 
 
 def parse():
@@ -599,13 +597,12 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
                      "traffic": TRAFFIC_NCU.get(traffic_key),
-                     "traffic_previous_kernel": (
-                         None if traffic_key in TRAFFIC_NCU or traffic_key not in TRAFFIC_PREVIOUS
-                         else {"bytes": TRAFFIC_PREVIOUS[traffic_key],
-                               "note": "ncu DRAM bytes per launch of the search kernel before "
-                                       "its end-restriction test was added (not re-captured "
-                                       "since); profiles/k_inexact_persistent_2gbp_10m_reads_"
-                                       "dram.md"}),
+                     "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                        "full-size launch of the current kernel, "
+                                        "profiles/k_inexact_persistent_2gbp_10m_reads_dram.md"
+                                        if traffic_key in TRAFFIC_NCU else
+                                        "no capture of this configuration (interval, size, "
+                                        "tables, pair steps)"),
                      "kernel": "k_inexact_persistent", "kernel_ms": k_ms,
                      "gather_ceiling": ceil_main,
                      # every 32-byte unit the kernel gathers (checkpoint blocks and table or pair

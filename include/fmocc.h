@@ -366,7 +366,7 @@ int fm_probe_gather(const void *buf, uint64_t bytes, uint32_t granule, uint32_t 
 typedef struct fm_tuning {
     uint32_t warps_per_block;   /* persistent kernel: warps per CTA (1..8) */
     uint32_t blocks_per_sm;     /* persistent kernel: resident CTAs per SM (occupancy) */
-    uint32_t chunk;             /* queries a warp takes from the work queue at once (1..32) */
+    uint32_t chunk;             /* queries a warp takes from the work queue at once (1..32; default 8) */
     uint32_t plain_block;       /* plain kernel threads per CTA (a multiple of 32, <= 256) */
     uint32_t graphs;            /* 1: run the persistent search as a CUDA graph (captured on the
                                    first call with given buffers and sizes, replayed after);

@@ -90,6 +90,22 @@ struct GQuery {
     __device__ __forceinline__ uint32_t gaps() const { return (mt.w >> 20) & 15u; }
 };
 
+// An exact chain's query without staging: base is the index in reads of W[0] (the read's first
+// symbol, or its last for the reverse complement), md the query's metadata word; then
+// W[i] = reads[base + i], or 3 - reads[base - i] = reads[base - i] ^ 3 on the reverse strand.
+struct CQuery {
+    const uint8_t *reads;
+    uint32_t base, md;
+    __device__ __forceinline__ uint32_t w(uint32_t i) const {
+        const uint32_t rc = (md >> 8) & 1u;
+        return (uint32_t)reads[rc ? base - i : base + i] ^ (rc * 3u);
+    }
+    __device__ __forceinline__ uint32_t z0() const { return (md >> 16) & 15u; }
+};
+__device__ __forceinline__ uint2 chain_base(const uint4 &mt) {
+    return make_uint2(((mt.w >> 8) & 1u) ? mt.z + (mt.w & 255u) - 1u : mt.z, mt.w);
+}
+
 // Shared-memory query slots of the persistent kernel (with staging): kSlots per warp, in
 // kGroups groups of kGroupSlots, kSlotWords words each: words 0-15 the query's symbols, W[i]
 // at bits 2(i%16) of word i/16; words 16-17 its D breakpoints; word 18 its length m (bits
@@ -560,7 +576,9 @@ __global__ void __launch_bounds__(256, I <= 128 ? 4 : 2) k_inexact_persistent(Se
     int gcount[kGroups];                       // live nodes per slot group (warp-uniform)
 #pragma unroll
     for (int g = 0; g < kGroups; ++g) gcount[g] = 0;
-    unsigned long long my_nodes = 0, my_blocks = 0;
+    // this lane's nodes, checkpoint blocks and table sectors (32 bits: a lane expands well
+    // under 2^32 nodes in one launch)
+    uint32_t my_nodes = 0, my_blocks = 0, my_sects = 0;
     if (prof && lane < kFillCounters) fillc[lane] = 0u;
     __syncwarp();
     // metadata records: with STAGE the staging records (kStageU4 uint4 per query, the query's
@@ -645,7 +663,7 @@ __global__ void __launch_bounds__(256, I <= 128 ? 4 : 2) k_inexact_persistent(Se
             // do), and the survivors go back to E (fewer than 32, so E stays below 32 for the
             // next G step).
             uint4 n0 = make_uint4(0, 0, 0, 0), n1 = make_uint4(0, 0, 0, 0);
-            uint2 r0 = make_uint2(0, 0), r1 = make_uint2(0, 0);   // without STAGE: read start, m
+            uint2 r0 = make_uint2(0, 0), r1 = make_uint2(0, 0);   // without STAGE: chain_base
             bool a0 = false, a1 = false;
             uint32_t ended01 = 0, ended23 = 0;   // STAGE: ended chains of groups 0..3, 16-bit fields
             int since_flush = 0;
@@ -676,8 +694,7 @@ __global__ void __launch_bounds__(256, I <= 128 ? 4 : 2) k_inexact_persistent(Se
                     if (!a0 && p0 < t0) {
                         n0 = st.get(stk - etop + p0);
                         if constexpr (!STAGE) {
-                            const uint4 m = c.qmeta[n0.x];
-                            r0 = make_uint2(m.z, m.w);
+                            r0 = chain_base(c.qmeta[n0.x]);
                         }
                         a0 = true;
                     }
@@ -687,8 +704,7 @@ __global__ void __launch_bounds__(256, I <= 128 ? 4 : 2) k_inexact_persistent(Se
                     if (!a1 && p1 < t1) {
                         n1 = st.get(stk - etop + t0 + p1);
                         if constexpr (!STAGE) {
-                            const uint4 m = c.qmeta[n1.x];
-                            r1 = make_uint2(m.z, m.w);
+                            r1 = chain_base(c.qmeta[n1.x]);
                         }
                         a1 = true;
                     }
@@ -702,17 +718,19 @@ __global__ void __launch_bounds__(256, I <= 128 ? 4 : 2) k_inexact_persistent(Se
                 uint32_t b0 = 0, b1 = 0, x0 = 0, x1 = 0;
                 auto cq = [&](const uint4 &n, const uint2 &r) {
                     if constexpr (STAGE) return SQuery{slots + slot_of(n) * kSlotWords};
-                    else return GQuery{c.reads, make_uint4(0u, 0u, r.x, r.y)};
+                    else return CQuery{c.reads, r.x, r.y};
                 };
                 if (a0) {
                     chain_step<I>(c, n0, cq(n0, r0), c0, s0, e0, b0, x0);
                     my_nodes += x0;
-                    my_blocks += step_cost(b0);
+                    my_blocks += b0 & 0xffffu;
+                    my_sects += b0 >> 16;
                 }
                 if (step1) {
                     chain_step<I>(c, n1, cq(n1, r1), c1, s1, e1, b1, x1);
                     my_nodes += x1;
-                    my_blocks += step_cost(b1);
+                    my_blocks += b1 & 0xffffu;
+                    my_sects += b1 >> 16;
                 }
                 if (prof) {   // warp-uniform
                     const int live0 = __popc(__ballot_sync(FULL, a0));
@@ -821,7 +839,8 @@ __global__ void __launch_bounds__(256, I <= 128 ? 4 : 2) k_inexact_persistent(Se
             z0 = qv.z0();
             if constexpr (STAGE) qn = qv.q();
             my_nodes += cn;
-            my_blocks += step_cost(nb);
+            my_blocks += nb & 0xffffu;
+            my_sects += nb >> 16;
         }
         if (prof && lane == 0) {
             fillc[3] += 1u;
@@ -868,15 +887,17 @@ __global__ void __launch_bounds__(256, I <= 128 ? 4 : 2) k_inexact_persistent(Se
         __syncwarp();
     }
     if (c.stats) {
+        unsigned long long tn = my_nodes, tb = my_blocks, ts = my_sects;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            my_nodes += __shfl_down_sync(FULL, my_nodes, o);
-            my_blocks += __shfl_down_sync(FULL, my_blocks, o);
+            tn += __shfl_down_sync(FULL, tn, o);
+            tb += __shfl_down_sync(FULL, tb, o);
+            ts += __shfl_down_sync(FULL, ts, o);
         }
         if (lane == 0) {
-            atomicAdd(c.stats + 0, my_nodes);
-            atomicAdd(c.stats + 1, my_blocks & 0xffffffffull);
-            atomicAdd(c.stats + 3, my_blocks >> 32);
+            atomicAdd(c.stats + 0, tn);
+            atomicAdd(c.stats + 1, tb);
+            atomicAdd(c.stats + 3, ts);
         }
     }
     if (prof) {
@@ -1800,6 +1821,24 @@ static int run_inexact_graph(fm_index *h, const uint8_t *reads, const uint32_t *
         return set_error(h, FM_ETRUNC, "pair capacity " + std::to_string(pair_capacity) +
                                            " below the " + std::to_string(need) + " intervals found");
     return FM_OK;
+}
+
+int reserve_search_scratch(fm_index *h, uint64_t nq) {
+    // the sizes run_inexact starts from for nq queries of the persistent kernel
+    const Tuning &tu = h->tune;
+    const int block = (int)tu.warps_per_block * 32;
+    const size_t smem = persistent_smem(block, kPoolEntries, tu.stage != 0);
+    int bps = (int)tu.blocks_per_sm;
+    const int occ = occupancy_any(h->interval, block, smem, tu.stage != 0, false);
+    if (bps <= 0 || bps > occ) bps = occ;
+    const uint64_t nwarps = (uint64_t)h->sms * (bps > 0 ? bps : 1) * (block / 32);
+    const uint64_t raw_cap = nq * 4 + (1u << 20);
+    int rc;
+    if ((rc = ensure_scratch(h, h->s_misc, 256))) return rc;
+    if ((rc = ensure_scratch(h, h->s_qmeta, (size_t)nq * (tu.stage ? kStageU4 : 1u) * sizeof(uint4)))) return rc;
+    if ((rc = ensure_scratch(h, h->s_raw, raw_cap * sizeof(uint4)))) return rc;
+    if ((rc = ensure_scratch(h, h->s_spill, nwarps * 4096 * sizeof(uint4)))) return rc;
+    return ensure_scratch(h, h->s_group, GroupLayout((uint32_t)nq, raw_cap).total);
 }
 
 int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,

@@ -93,7 +93,7 @@ struct GraphKey {
 struct Tuning {
     uint32_t warps_per_block = 8;
     uint32_t blocks_per_sm = 0;     // 0: from the occupancy calculator
-    uint32_t chunk = 16;
+    uint32_t chunk = 8;      // queries a warp takes from the work queue at once
     uint32_t plain_block = 128;
     uint32_t occ_q = 2;
     uint32_t canon = 1;      // inexact search enumerates canonical alignments only
@@ -127,6 +127,8 @@ struct fm_index {
     uint2 *d_kt = nullptr;           // interval tables of short strings (forward index)
     uint32_t *d_kbits = nullptr;     // their occurrence bits
     uint32_t kt_depth = 0;           // levels built (0: none)
+    uint2 *d_kt_rev = nullptr;       // the same tables of the index of reverse(R) (D bound)
+    uint32_t *d_kbits_rev = nullptr;
     uint8_t *d_pblk = nullptr;       // pair table (see IndexView)
     uint32_t *d_psb = nullptr;       // its superblock counts, then pc2[16]
     uint32_t prow_a = 0, prow_b = 0;
@@ -205,6 +207,9 @@ int launch_dcalc(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32
                  uint32_t strands, uint4 *qmeta, uint8_t *D_out, cudaStream_t st,
                  uint32_t stride = 1, const uint8_t *modes = nullptr, uint32_t defmode = 0);
 int fetch_inexact(fm_index *h, uint32_t *pairs, uint64_t pair_capacity, cudaStream_t st);
+// grow h's search scratch now to the sizes a persistent search of nq queries starts from (so
+// that such searches allocate, and free, nothing)
+int reserve_search_scratch(fm_index *h, uint64_t nq);
 // modes: optional device uint8 per read (z | max_gaps << 4), overriding sp->z and
 // sp->max_gaps read by read (serving batches that mix search modes)
 int run_inexact(fm_index *h, const uint8_t *reads, const uint32_t *offs, uint32_t n_reads,
@@ -258,6 +263,21 @@ __device__ __forceinline__ uint32_t ldg32_na(const uint32_t *p) {
     if constexpr (kGatherNoL1) asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
     else v = __ldg(p);
     return v;
+}
+
+// The two sectors of a 64-byte pair block (its count word, its bit planes) are read by two loads;
+// with the L2 prefetch size of the line, the first miss brings both sectors from DRAM in one
+// access instead of two (measured on the headline search: 28% fewer DRAM bytes, same time).
+__device__ __forceinline__ uint32_t ldg32_na_line64(const uint32_t *p) {
+    uint32_t v;
+    asm("ld.global.nc.L1::no_allocate.L2::64B.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void ldg256_na_line64(const void *p, uint4 &a, uint4 &b) {
+    asm("ld.global.nc.L1::no_allocate.L2::64B.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+        : "l"(p));
 }
 
 __device__ __forceinline__ uint2 ldg64_na(const uint2 *p) {
@@ -360,8 +380,8 @@ struct PairBlk {
 
 __device__ __forceinline__ void load_pair_block(const IndexView &ix, uint32_t j, uint32_t c, PairBlk &B) {
     const uint8_t *p = ix.pblk + (size_t)j * 64;
-    B.cw = ldg32_na((const uint32_t *)p + (c >> 1));
-    ldg256_na(p + 32, B.s0, B.s1);
+    B.cw = ldg32_na_line64((const uint32_t *)p + (c >> 1));
+    ldg256_na_line64(p + 32, B.s0, B.s1);
 }
 
 // Rows among the 32 of one half block whose pair code is c: a row matches where every bit

@@ -34,9 +34,9 @@ IndexView view_fwd(const fm_index *h) {
 IndexView view_rev(const fm_index *h) {
     IndexView v = view_fwd(h);
     v.blocks = h->d_rev;
-    v.kt = nullptr;
-    v.kbits = nullptr;
-    v.kdepth = 0;
+    v.kt = h->d_kt_rev;
+    v.kbits = h->d_kbits_rev;
+    v.kdepth = h->d_kt_rev ? h->kt_depth : 0u;
     v.pblk = nullptr;
     v.psb = nullptr;
     v.pc2 = nullptr;
@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(128) k_dcalc(IndexView rv, const uint8_t *__re
                                                uint32_t defmode, uint8_t *__restrict__ D_out,
                                                uint32_t *__restrict__ err) {
     const uint32_t nq = nr * strands;
+    const uint32_t L = rv.kdepth;   // interval tables of reverse(R) (0: none)
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
         const uint32_t r = strands == 2 ? q >> 1 : q;
         const uint32_t strand = strands == 2 ? (q & 1u) : 0u;
@@ -219,25 +220,79 @@ __global__ void __launch_bounds__(128) k_dcalc(IndexView rv, const uint8_t *__re
         uint32_t bp_lo = 0xffffffffu, bp_hi = 0xffffffffu;
         bool bad = m > (uint32_t)kMaxReadLen;
         if (bad) atomicOr(err, kErrReadLen);
-        uint32_t k = 0, l = rv.n, z = 0;
         uint8_t *Dq = D_out ? D_out + (size_t)strands * s + (size_t)strand * m : nullptr;
         uint32_t *Wq = (qmeta && stride == kStageU4) ? (uint32_t *)(qmeta + (size_t)q * stride + 1) : nullptr;
-        uint32_t wacc = 0;   // symbols of the current 16-symbol word of W
-        for (uint32_t i = 0; i < m && !bad; ++i) {
-            uint32_t b = strand ? reads[s + m - 1 - i] : reads[s + i];
-            if (b > 3u) {
-                atomicOr(err, kErrDomain);
-                bad = true;
-                break;
-            }
-            if (strand) b = 3u - b;
-            if (Wq) {
-                wacc |= b << (2u * (i & 15u));
-                if ((i & 15u) == 15u || i + 1u == m) {
-                    Wq[i >> 4] = wacc;
-                    wacc = 0;
+        // W[i], oriented for the strand
+        auto wsym = [&](uint32_t i) -> uint32_t {
+            const uint32_t c = strand ? reads[s + m - 1 - i] : reads[s + i];
+            return strand ? 3u - c : c;
+        };
+        // the codes are checked (and, for staging, packed 16 to a word) before the D bound
+        {
+            uint32_t wacc = 0;
+            for (uint32_t i = 0; i < m && !bad; ++i) {
+                const uint32_t c = strand ? reads[s + m - 1 - i] : reads[s + i];
+                if (c > 3u) {
+                    atomicOr(err, kErrDomain);
+                    bad = true;
+                    break;
+                }
+                if (Wq) {
+                    wacc |= (strand ? 3u - c : c) << (2u * (i & 15u));
+                    if ((i & 15u) == 15u || i + 1u == m) {
+                        Wq[i >> 4] = wacc;
+                        wacc = 0;
+                    }
                 }
             }
+        }
+        // a window W[j..i] that does not occur closes at i: the next breakpoint is i
+        uint32_t z = 0;
+        auto close_at = [&](uint32_t i) {
+            if (z < 4) bp_lo = (bp_lo & ~(0xffu << (8 * z))) | (i << (8 * z));
+            else if (z < 8) bp_hi = (bp_hi & ~(0xffu << (8 * (z - 4)))) | (i << (8 * (z - 4)));
+            ++z;
+        };
+        uint32_t k = 0, l = rv.n;
+        bool fresh = true;   // a window starts at i ([k, l] = [0, n])
+        for (uint32_t i = 0; i < m && !bad;) {
+            if (L && fresh) {
+                // The window's first dmax symbols from the tables of reverse(R): a window
+                // W[i..i+d-1] occurs in R exactly when its reverse occurs in reverse(R), the
+                // string whose code is P >> 2(L - d) with P holding W[i] in its highest symbol.
+                // Prefixes of an occurring string occur, so the longest occurring d is found by
+                // testing dmax first and else by bisection over the occurrence bits.
+                const uint32_t dmax = m - i < L ? m - i : L;
+                uint32_t P = 0;
+                for (uint32_t t = 0; t < dmax; ++t) P = (P << 2) | wsym(i + t);
+                P <<= 2u * (L - dmax);
+                auto occurs = [&](uint32_t d) { return kt_occ1(rv, d, P >> (2u * (L - d))) != 0u; };
+                uint32_t d = dmax;
+                if (!occurs(dmax)) {
+                    uint32_t lo = 0, hi = dmax - 1;   // occurs(lo), and d <= hi
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi + 1) / 2;
+                        if (occurs(mid)) lo = mid; else hi = mid - 1;
+                    }
+                    d = lo;
+                }
+                if (Dq)
+                    for (uint32_t t = 0; t < d; ++t) Dq[i + t] = (uint8_t)(z > 255 ? 255 : z);
+                if (d < dmax) {   // W[i..i+d] does not occur: the window closes at i + d
+                    close_at(i + d);
+                    if (Dq) Dq[i + d] = (uint8_t)(z > 255 ? 255 : z);
+                    i += d + 1;
+                    continue;
+                }
+                i += dmax;
+                if (i == m) break;
+                const uint2 kl = kt_get(rv, L, P);   // dmax = L: continue from the table entry
+                k = kl.x;
+                l = kl.y;
+                fresh = false;
+                continue;
+            }
+            const uint32_t b = wsym(i);
             const uint32_t pk = k, pl = l + 1u;
             const uint32_t jk = pk / I, jl = pl / I;
             Blk<I> Bk, Bl;
@@ -253,16 +308,16 @@ __global__ void __launch_bounds__(128) k_dcalc(IndexView rv, const uint8_t *__re
             const uint32_t k2 = cb + rank1_in<I>(Bk, jk, pk, rv.dollar, b) + 1u;
             const uint32_t l2 = cb + rank1_in<I>(Bl, jl, pl, rv.dollar, b);
             if (k2 > l2) {   // W[j..i] does not occur: close the window, restart after i
-                if (z < 4) bp_lo = (bp_lo & ~(0xffu << (8 * z))) | (i << (8 * z));
-                else if (z < 8) bp_hi = (bp_hi & ~(0xffu << (8 * (z - 4)))) | (i << (8 * (z - 4)));
-                ++z;
+                close_at(i);
                 k = 0;
                 l = rv.n;
+                fresh = true;
             } else {
                 k = k2;
                 l = l2;
             }
             if (Dq) Dq[i] = (uint8_t)(z > 255 ? 255 : z);
+            ++i;
         }
         if (qmeta) {
             uint4 mt;
@@ -507,38 +562,55 @@ int ensure_kmer(fm_index *h, cudaStream_t st) {
     const uint32_t L = kmer_depth_for(h);
     if (L == h->kt_depth) return FM_OK;
     FM_CUDA_TRY(h, cudaStreamSynchronize(st));   // no kernel of this stream reads the old tables
-    cudaFree(h->d_kt);
-    cudaFree(h->d_kbits);
-    h->d_kt = nullptr;
-    h->d_kbits = nullptr;
+    uint2 **kts[2] = {&h->d_kt, &h->d_kt_rev};
+    uint32_t **kbs[2] = {&h->d_kbits, &h->d_kbits_rev};
+    for (int v = 0; v < 2; ++v) {
+        cudaFree(*kts[v]);
+        cudaFree(*kbs[v]);
+        *kts[v] = nullptr;
+        *kbs[v] = nullptr;
+    }
     h->kt_depth = 0;
     if (L == 0) return FM_OK;
     const uint64_t entries = 2ull << (2 * L);
     const uint64_t nwords = (entries + 31) / 32;
-    if (cudaMalloc(&h->d_kt, entries * sizeof(uint2)) != cudaSuccess ||
-        cudaMalloc(&h->d_kbits, nwords * sizeof(uint32_t)) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(h->d_kt);
-        h->d_kt = nullptr;
-        h->d_kbits = nullptr;
-        return set_error(h, FM_ENOMEM, "interval tables: out of device memory");
-    }
-    const uint2 root = make_uint2(0u, (uint32_t)h->n);   // the empty string: [0, n]
-    FM_CUDA_TRY(h, cudaMemcpyAsync(h->d_kt + 1, &root, sizeof(root), cudaMemcpyHostToDevice, st));
-    IndexView ix = view_fwd(h);
-    for (uint32_t j = 0; j < L; ++j) {
-        const int block = 256;
-        const int grid = grid_occ(h, 1ull << (2 * j), block);
-        switch (h->interval) {
-            case 32: k_kmer_level<32><<<grid, block, 0, st>>>(ix, h->d_kt, j); break;
-            case 64: k_kmer_level<64><<<grid, block, 0, st>>>(ix, h->d_kt, j); break;
-            case 128: k_kmer_level<128><<<grid, block, 0, st>>>(ix, h->d_kt, j); break;
-            default: k_kmer_level<256><<<grid, block, 0, st>>>(ix, h->d_kt, j); break;
+    // the forward index's tables (search) and, with the index of reverse(R), that index's own
+    // (the D bound: windows of a query are looked up as strings of reverse(R))
+    for (int v = 0; v < (h->has_rev ? 2 : 1); ++v) {
+        if (cudaMalloc(kts[v], entries * sizeof(uint2)) != cudaSuccess ||
+            cudaMalloc(kbs[v], nwords * sizeof(uint32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            for (int u = 0; u < 2; ++u) {
+                cudaFree(*kts[u]);
+                cudaFree(*kbs[u]);
+                *kts[u] = nullptr;
+                *kbs[u] = nullptr;
+            }
+            return set_error(h, FM_ENOMEM, "interval tables: out of device memory");
         }
+        const uint2 root = make_uint2(0u, (uint32_t)h->n);   // the empty string: [0, n]
+        FM_CUDA_TRY(h, cudaMemcpyAsync(*kts[v] + 1, &root, sizeof(root), cudaMemcpyHostToDevice, st));
+        IndexView ix = view_fwd(h);
+        if (v == 1) {
+            ix = view_rev(h);
+            ix.kt = nullptr;   // the steps below read checkpoint blocks only
+            ix.kbits = nullptr;
+            ix.kdepth = 0;
+        }
+        for (uint32_t j = 0; j < L; ++j) {
+            const int block = 256;
+            const int grid = grid_occ(h, 1ull << (2 * j), block);
+            switch (h->interval) {
+                case 32: k_kmer_level<32><<<grid, block, 0, st>>>(ix, *kts[v], j); break;
+                case 64: k_kmer_level<64><<<grid, block, 0, st>>>(ix, *kts[v], j); break;
+                case 128: k_kmer_level<128><<<grid, block, 0, st>>>(ix, *kts[v], j); break;
+                default: k_kmer_level<256><<<grid, block, 0, st>>>(ix, *kts[v], j); break;
+            }
+            FM_CUDA_TRY(h, cudaGetLastError());
+        }
+        k_kmer_bits<<<grid_occ(h, nwords, 256), 256, 0, st>>>(*kts[v], *kbs[v], (uint32_t)nwords, L);
         FM_CUDA_TRY(h, cudaGetLastError());
     }
-    k_kmer_bits<<<grid_occ(h, nwords, 256), 256, 0, st>>>(h->d_kt, h->d_kbits, (uint32_t)nwords, L);
-    FM_CUDA_TRY(h, cudaGetLastError());
     FM_CUDA_TRY(h, cudaStreamSynchronize(st));
     h->kt_depth = L;
     return FM_OK;

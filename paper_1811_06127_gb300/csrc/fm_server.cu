@@ -253,6 +253,14 @@ int fm_server_start(fm_index *h, const fm_server_params *p, fm_server **out) {
         }
         w->ctx->scratch_budget = s->budget_per_worker;
         w->ctx->use_graphs = false;   // batch sizes change from one batch to the next
+        // scratch for a full batch now: a regrowth during serving would free the old buffer,
+        // and cudaFree waits for the whole device, the other workers' batches included (best
+        // effort: a budget too small for it leaves the growth to the batches)
+        {
+            uint64_t nq = (uint64_t)q.max_batch_reads * q.strands;
+            while (nq > 1024 && scratch_model(*w, nq) > s->budget_per_worker) nq /= 2;
+            if (reserve_search_scratch(w->ctx, nq) != FM_OK) w->ctx->err.clear();
+        }
         e = cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
             free_search_context(w->ctx);

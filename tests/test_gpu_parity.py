@@ -227,13 +227,21 @@ def test_dcalc_matches_oracle(fm, interval):
     reads = synth.sample_reads(9, R, 1500, 1, 255, sub_rate=0.03, indel_rate=0.01,
                                both_strands=True, random_frac=0.1)
     codes, offs = fm.to_device_reads(reads)
-    D = fm.fm_dcalc(h, codes, offs, strands=2).cpu().numpy()
-    for r in range(len(reads)):
-        W = reads.read(r)
-        m = W.size
-        s = 2 * int(reads.offs[r])
-        assert np.array_equal(D[s:s + m], ix.dcalc(W)), r
-        assert np.array_equal(D[s + m:s + 2 * m], ix.dcalc(synth.revcomp(W))), r
+    want = [(ix.dcalc(reads.read(r)), ix.dcalc(synth.revcomp(reads.read(r))))
+            for r in range(len(reads))]
+    # without interval tables, then with tables of reverse(R) at several depths (a search
+    # builds them; the D bound then takes each window's first symbols from them)
+    ek, eo = fm.to_device_reads(reads.subset(np.arange(4)))
+    for depth in (None, 1, 2, 7, fm.KMER_AUTO):
+        if depth is not None:
+            fm.fm_set_tuning(h, kmer_depth=depth)
+            fm.fm_exact(h, ek, eo)
+        D = fm.fm_dcalc(h, codes, offs, strands=2).cpu().numpy()
+        for r in range(len(reads)):
+            m = int(reads.offs[r + 1] - reads.offs[r])
+            s = 2 * int(reads.offs[r])
+            assert np.array_equal(D[s:s + m], want[r][0]), (depth, r)
+            assert np.array_equal(D[s + m:s + 2 * m], want[r][1]), (depth, r)
     h.close()
 
 
