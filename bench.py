@@ -715,13 +715,23 @@ def gather_ceiling(torch, fmocc, dev, footprint, flush):
 
 def bench_occ8(args, torch, fmocc, synth, dev, hbm_peak, peak_kind, flush, barrier,
                max_over_ranks, world):
-    t0 = time.time()
+    """Config 2 at the main checkpoint interval, and beside it at the other intervals of
+    {64, 128, 256} (each with its own index and the query mix drawn for its block size)."""
     R = synth.gc_text(SEED_OCC, args.occ_n, 0.41)
-    h = fmocc.fm_build(R, interval=args.interval, device=dev.index, forward_only=True)
-    del R
+    main = occ8_at(args, args.interval, R, torch, fmocc, synth, dev, hbm_peak, peak_kind, flush,
+                   barrier, max_over_ranks, world)
+    main["other_intervals"] = [
+        occ8_at(args, I, R, torch, fmocc, synth, dev, hbm_peak, peak_kind, flush, barrier,
+                max_over_ranks, world) for I in (64, 128, 256) if I != args.interval]
+    return main
+
+
+def occ8_at(args, I, R, torch, fmocc, synth, dev, hbm_peak, peak_kind, flush, barrier,
+            max_over_ranks, world):
+    t0 = time.time()
+    h = fmocc.fm_build(R, interval=I, device=dev.index, forward_only=True)
     n = args.occ_n
-    k, l = synth.occ_queries_mixed(SEED_OCC, n, args.occ_queries, args.interval)
-    I = args.interval
+    k, l = synth.occ_queries_mixed(SEED_OCC, n, args.occ_queries, I)
     same = (k // I) == ((l.astype(np.int64) + 1) // I)
     blocks = float(np.where(same, 1, 2).sum())
     kd = torch.from_numpy(k.view(np.int32)).to(dev)
