@@ -331,48 +331,70 @@ __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, cons
 // i = 0), or the branch ends (empty interval).  The child needs no D test: every node is
 // created with z >= D(i), D never decreases with i, so here D(i-1) <= D(i) = 0.  Only the
 // query's symbols are used.
+//
+// A shallow node (its string X shorter than the table depth L) runs all of its steps inside the
+// tables at once: the symbols it will prepend are W[i], W[i-1], ..., so after t steps its
+// string is W[i-t+1..i] X, of code code(X) 4^t + sum_s W[i-s] 4^(t-1-s).  With
+// tmax = min(L - d, i + 1) steps left in the tables, the string after tmax steps is tested
+// first (one occurrence bit); otherwise the longest occurring prefix length t is found by
+// bisection (longer strings occur only if their shorter suffixes do, and the code after t steps
+// is the code after tmax steps shifted right by 2 (tmax - t)).  The chain then ends after t + 1
+// steps, or after tmax steps becomes a result (i reaches -1) or an interval node at depth L.
+// nn counts the steps, as the one-step walk would count its nodes.
 template <int I, class Q>
 __device__ __forceinline__ void exact_step(const SearchCfg &c, const uint4 &nd, const Q &qv,
                                            uint4 &out, bool &survive, bool &is_leaf,
-                                           uint32_t &nblocks) {
+                                           uint32_t &nblocks, uint32_t &nn) {
     const uint32_t i = nd.y & 255u;
-    const uint32_t b = qv.w(i);
     const uint32_t k = nd.z, l = nd.w;
-    uint32_t k2 = 0u, l2 = 0u, ybits = nd.y & (0xf000u | kSlotBits);   // z = 0, created by a match
-    bool alive;
+    const uint32_t ybits = nd.y & (0xf000u | kSlotBits);   // z = 0, created by a match
     if (nd.y & kShallow) {
-        const uint32_t d = (nd.y >> 20) & 15u, code = 4u * k + b;
+        const uint32_t d = (nd.y >> 20) & 15u;
+        const uint32_t left = c.ix.kdepth - d;
+        const uint32_t tmax = left < i + 1u ? left : i + 1u;
+        uint32_t code = k;
+        for (uint32_t s = 0; s < tmax; ++s) code = 4u * code + qv.w(i - s);
         nblocks = 0;
-        alive = kt_occ1(c.ix, d + 1u, code) != 0u;
-        if (d + 1u < c.ix.kdepth && i > 0u) {
-            k2 = code;
-            ybits |= kShallow | ((d + 1u) << 20);
-        } else if (alive) {   // the table depth, or a result (its interval)
-            const uint2 kl = kt_get(c.ix, d + 1u, code);
-            k2 = kl.x;
-            l2 = kl.y;
-            nblocks = kTabRead;
+        if (!kt_occ1(c.ix, d + tmax, code)) {
+            uint32_t lo = 0, hi = tmax - 1u;   // X itself occurs (the node exists)
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1u) >> 1;
+                if (kt_occ1(c.ix, d + mid, code >> (2u * (tmax - mid)))) lo = mid; else hi = mid - 1u;
+            }
+            nn = lo + 1u;
+            survive = false;
+            is_leaf = false;
+            out = nd;
+            return;
         }
-    } else {
-        const uint32_t pk = k, pl = l + 1u;
-        const uint32_t jk = pk / I, jl = pl / I;
-        const uint32_t ok = pk - jk * I, ol = pl - jl * I;
-        // C[b] by select: a runtime index into the parameter struct would copy it to local memory
-        const uint32_t cb = b == 0 ? c.ix.C[0] : (b == 1 ? c.ix.C[1] : (b == 2 ? c.ix.C[2] : c.ix.C[3]));
-        Blk<I> Bk, Bl;
-        if (jk == jl) {
-            load_block<I>(c.ix.blocks, jk, ok > ol ? ok : ol, Bk);
-            Bl = Bk;
-            nblocks = 1;
-        } else {
-            load_block<I>(c.ix.blocks, jk, ok, Bk);
-            load_block<I>(c.ix.blocks, jl, ol, Bl);
-            nblocks = 2;
-        }
-        k2 = cb + rank1_in<I>(Bk, jk, pk, c.ix.dollar, b) + 1u;
-        l2 = cb + rank1_in<I>(Bl, jl, pl, c.ix.dollar, b);
-        alive = k2 <= l2;
+        const uint2 kl = kt_get(c.ix, d + tmax, code);
+        nblocks = kTabRead;
+        nn = tmax;
+        is_leaf = tmax == i + 1u;
+        survive = !is_leaf;
+        out = make_uint4(nd.x, (i - tmax) | ybits, kl.x, kl.y);
+        return;
     }
+    const uint32_t b = qv.w(i);
+    const uint32_t pk = k, pl = l + 1u;
+    const uint32_t jk = pk / I, jl = pl / I;
+    const uint32_t ok = pk - jk * I, ol = pl - jl * I;
+    // C[b] by select: a runtime index into the parameter struct would copy it to local memory
+    const uint32_t cb = b == 0 ? c.ix.C[0] : (b == 1 ? c.ix.C[1] : (b == 2 ? c.ix.C[2] : c.ix.C[3]));
+    Blk<I> Bk, Bl;
+    if (jk == jl) {
+        load_block<I>(c.ix.blocks, jk, ok > ol ? ok : ol, Bk);
+        Bl = Bk;
+        nblocks = 1;
+    } else {
+        load_block<I>(c.ix.blocks, jk, ok, Bk);
+        load_block<I>(c.ix.blocks, jl, ol, Bl);
+        nblocks = 2;
+    }
+    const uint32_t k2 = cb + rank1_in<I>(Bk, jk, pk, c.ix.dollar, b) + 1u;
+    const uint32_t l2 = cb + rank1_in<I>(Bl, jl, pl, c.ix.dollar, b);
+    const bool alive = k2 <= l2;
+    nn = 1u;
     is_leaf = alive && i == 0u;
     survive = alive && i > 0u;
     out = make_uint4(nd.x, (i - 1u) | ybits, k2, l2);
@@ -414,8 +436,7 @@ __device__ __forceinline__ void chain_step(const SearchCfg &c, const uint4 &nd, 
     if (c.ix.pairs && !(nd.y & kShallow) && (nd.y & 255u) >= 1u) {
         pair_step<I>(c, nd, qv, out, survive, is_leaf, nblocks, nn);
     } else {
-        exact_step<I>(c, nd, qv, out, survive, is_leaf, nblocks);
-        nn = 1u;
+        exact_step<I>(c, nd, qv, out, survive, is_leaf, nblocks, nn);
     }
 }
 
