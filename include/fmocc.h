@@ -390,11 +390,12 @@ typedef struct fm_tuning {
                                    is shorter than depth are expanded from the tables, with no
                                    checkpoint-block read; exact search starts depth steps in.
                                    Results, and node counts, are unchanged; stats[1] counts
-                                   only checkpoint blocks.  Values: 1..14 the depth
+                                   only checkpoint blocks.  Values: 1..15 the depth
                                    (2 x 4^depth x 8 bytes of device memory, built on the first
                                    search that needs them); FM_KMER_AUTO (default) the depth
-                                   floor(log4(n + 1)) - 2, clamped to [0, 14] (13 at n = 2e9,
-                                   1.07 GB);
+                                   floor(log4(n + 1)) - 1, clamped to [0, 15] (14 at n = 2e9:
+                                   4.3 GB, and as much again for the index of reverse(R),
+                                   whose tables the D bound reads);
                                    FM_KMER_OFF none.  fm_get_tuning reports the depth in effect
                                    (FM_KMER_OFF for none) */
     uint32_t pair_steps;        /* 1 (default): searches advance exact continuations two symbols
@@ -407,7 +408,7 @@ typedef struct fm_tuning {
                                    branch.  2: one symbol per step (stats exactly as described) */
     uint32_t refill;            /* persistent kernel: a warp takes more queries from the work
                                    queue when its node pools hold fewer nodes than this
-                                   (1..288; default 48) */
+                                   (1..288; default 40) */
     uint32_t chain2_min;        /* persistent kernel: each lane holds up to two exact chains;
                                    the warp steps the second ones only while at least this many
                                    lanes hold one, else they wait for a first place (1..32;

@@ -43,15 +43,15 @@ TABLE_SPACE = {
 
 def auto_kmer_depth(n: int) -> int:
     """The library's automatic interval-table depth for a reference of n symbols:
-    floor(log4(n+1)) - 2, at most 14 (0: no tables)."""
+    floor(log4(n+1)) - 1, at most 15 (0: no tables)."""
     lg = 0
     while 4 ** (lg + 1) <= n + 1:
         lg += 1
-    return min(14, lg - 2) if lg > 2 else 0
+    return min(15, lg - 1) if lg > 1 else 0
 
 
 def kmer_depth_of(n: int, offset: int) -> int:
-    return max(1, min(14, auto_kmer_depth(n) + offset))
+    return max(1, min(15, auto_kmer_depth(n) + offset))
 
 
 def points(n: int, space: dict | None = None, table_space: dict | None = None):

@@ -561,7 +561,7 @@ int fm_set_tuning(fm_index *h, const fm_tuning *t) {
     if (t->canonical > 2) return set_error(h, FM_EINVAL, "canonical must be 0, 1 or 2");
     if (t->pair_steps > 2) return set_error(h, FM_EINVAL, "pair_steps must be 0, 1 or 2");
     if (t->kmer_depth > fm::kMaxKmerDepth && t->kmer_depth != FM_KMER_AUTO && t->kmer_depth != FM_KMER_OFF)
-        return set_error(h, FM_EINVAL, "kmer_depth must be 0, 1..14, FM_KMER_AUTO or FM_KMER_OFF");
+        return set_error(h, FM_EINVAL, "kmer_depth must be 0, 1..15, FM_KMER_AUTO or FM_KMER_OFF");
     if (t->refill > 288) return set_error(h, FM_EINVAL, "refill must be 0..288");
     if (t->chain2_min > 32) return set_error(h, FM_EINVAL, "chain2_min must be 0..32");
     if (t->stage > 2) return set_error(h, FM_EINVAL, "stage must be 0, 1 or 2");

@@ -97,10 +97,10 @@ struct Tuning {
     uint32_t plain_block = 128;
     uint32_t occ_q = 2;
     uint32_t canon = 1;      // inexact search enumerates canonical alignments only
-    uint32_t kmer = FM_KMER_AUTO;   // interval-table depth setting (FM_KMER_AUTO, FM_KMER_OFF, 1..14)
+    uint32_t kmer = FM_KMER_AUTO;   // interval-table depth setting (FM_KMER_AUTO, FM_KMER_OFF, 1..15)
     uint32_t pairs = 1;             // exact continuations two symbols per step from the pair table
     uint32_t l2_fetch = 0;   // 0: leave the context's limit alone
-    uint32_t refill = 48;    // a warp takes more queries when its pools hold fewer nodes
+    uint32_t refill = 40;    // a warp takes more queries when its pools hold fewer nodes
     uint32_t chain2_min = 12; // lanes whose second exact chain is live for the warp to step it
     uint32_t stage = 0;      // persistent kernel stages its queries in shared memory
 };
@@ -197,7 +197,7 @@ int ensure_kmer(fm_index *h, cudaStream_t st);
 // pair table: built on first use when the tuning asks for pair steps
 int ensure_pairs(fm_index *h, cudaStream_t st);
 constexpr uint32_t kPairRows = 64, kPairSuper = 32768;
-constexpr uint32_t kMaxKmerDepth = 14;
+constexpr uint32_t kMaxKmerDepth = 15;   // 2 x 4^15 entries: 32-bit table indices
 // D lower bound per query; qmeta (one uint4 per query, or with stride kStageU4 the staging
 // record of the persistent search: that uint4, then the query as 2-bit symbols) and/or D_out
 // (uint8 per position)

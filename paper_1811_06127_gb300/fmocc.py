@@ -441,7 +441,7 @@ def fm_inexact_fetch(h: Index, pairs: torch.Tensor, stream=None):
 def fm_set_tuning(h: Index, warps_per_block=0, blocks_per_sm=0, chunk=0, plain_block=0,
                   graphs=0, occ_per_thread=0, l2_fetch_bytes=0, canonical=0, kmer_depth=0,
                   pair_steps=0, refill=0, chain2_min=0, stage=0):
-    """Zero keeps a knob; graphs, canonical and pair_steps: 1 on, 2 off; kmer_depth: 1..14,
+    """Zero keeps a knob; graphs, canonical and pair_steps: 1 on, 2 off; kmer_depth: 1..15,
     KMER_AUTO or KMER_OFF.  Speed and memory only, never results (the tables and pair steps
     answer the cache-locality question of Sec. 4.2; the rest have no counterpart in the
     paper)."""

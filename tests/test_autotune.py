@@ -27,15 +27,15 @@ def test_autotune_table_stage_prefers_less_memory_within_noise():
 
 def test_autotune_points_cover_both_stages():
     from paper_1811_06127_gb300 import autotune
-    # the library's automatic depth: floor(log4(n+1)) - 2
-    assert autotune.auto_kmer_depth(2_000_000_000) == 13
-    assert autotune.auto_kmer_depth(256_000_000) == 11
-    assert autotune.auto_kmer_depth(8_000_000) == 9
+    # the library's automatic depth: floor(log4(n+1)) - 1
+    assert autotune.auto_kmer_depth(2_000_000_000) == 14
+    assert autotune.auto_kmer_depth(256_000_000) == 12
+    assert autotune.auto_kmer_depth(8_000_000) == 10
     assert autotune.auto_kmer_depth(10) == 0
     assert autotune.kmer_depth_of(10, 1) == 1
     pts = autotune.points(2_000_000_000)
     assert len(pts) == 3 * 2 * 3 * 3 * 3 * 2
-    assert {p["kmer_depth"] for p in pts} == {12, 13, 14}
+    assert {p["kmer_depth"] for p in pts} == {13, 14, 15}
     assert {p["pair_steps"] for p in pts} == {1, 2}
     assert {(p["interval"], p["chunk"]) for p in pts} == {(i, c) for i in (32, 64, 128)
                                                           for c in (8, 16, 32)}

@@ -3,8 +3,8 @@
 The oracle's SA-IS takes over ten minutes at 2 Gbp, so the headline read model (50-250 bp,
 1% substitutions + 0.05% single-base indels, both strands, z = 2 with at most one gap) is
 checked against Listing 2 on a 256 Mbp reference from the same repeat generator, with the code
-paths of the 2 Gbp index forced on: interval tables of depth 13 (the automatic depth at
-2 Gbp; at 256 Mbp it would be 11), pair steps, and the scheduler point the autotuner picks at
+paths of the 2 Gbp index forced on: interval tables of depth 14 (the automatic depth at
+2 Gbp; at 256 Mbp it would be 12), pair steps, and the scheduler point the autotuner picks at
 full size (I = 64, 8 warps per CTA, as many CTAs per SM as fit, chunk 8).  Every other point
 the autotuner can return is run on a smaller reference.  The occ8 micro-benchmark's query mix
 is checked value by value against the oracle's sorted sweep over its own BWT at 256 Mbp for
@@ -72,16 +72,16 @@ def _same(got, want, what):
 
 def test_headline_read_model_256mbp_vs_listing2(fm, texts, oracle_ix):
     """10^5 reads of the headline read model (2 x 10^5 queries), z = 2 with one gap, at the
-    tuned scheduler point with depth-13 tables and pair steps: intervals (graph replay and the
+    tuned scheduler point with depth-14 tables and pair steps: intervals (graph replay and the
     eager path) and per-interval costs against every call of the oracle's Listing 2."""
     R = texts["head"]
     reads = synth.sample_reads(SEED_SEARCH + 17, R, 100_000, 50, 250, sub_rate=0.01,
                                indel_rate=0.0005, both_strands=True)
     h = fm.fm_build(R, interval=64)
-    fm.fm_set_tuning(h, warps_per_block=8, blocks_per_sm=32, chunk=8, kmer_depth=13,
+    fm.fm_set_tuning(h, warps_per_block=8, blocks_per_sm=32, chunk=8, kmer_depth=14,
                      pair_steps=1, canonical=1, graphs=1)
     t = fm.fm_get_tuning(h)
-    assert (t["kmer_depth"], t["pair_steps"], t["chunk"]) == (13, 1, 8)
+    assert (t["kmer_depth"], t["pair_steps"], t["chunk"]) == (14, 1, 8)
     codes, offs = fm.to_device_reads(reads)
     stats = torch.zeros(4, dtype=torch.int64, device="cuda")
     first = fm.fm_inexact(h, codes, offs, 2, 1, strands=2)               # eager, sizes scratch

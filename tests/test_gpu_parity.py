@@ -479,7 +479,7 @@ def test_inexact_end_restriction(fm, z, gaps, e):
     h.close()
 
 
-@pytest.mark.parametrize("depth", [1, 3, 7, 10, 13, 14])
+@pytest.mark.parametrize("depth", [1, 3, 7, 10, 13, 14, 15])
 def test_inexact_interval_table_depths(fm, depth):
     """Tables of every depth, up to deeper than the strings of the search's first steps on this
     text: same intervals and nodes as the oracle, and no more checkpoint blocks."""
