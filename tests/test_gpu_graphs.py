@@ -119,7 +119,7 @@ def test_rejected_tuning_changes_nothing(fm):
     before = fm.fm_get_tuning(h)
     for bad in ({"warps_per_block": 4, "graphs": 3}, {"chunk": 8, "occ_per_thread": 3},
                 {"blocks_per_sm": 2, "l2_fetch_bytes": 48}, {"warps_per_block": 9},
-                {"chunk": 4, "kmer_depth": 15}, {"canonical": 2, "kmer_depth": 0x80}):
+                {"chunk": 4, "kmer_depth": 16}, {"canonical": 2, "kmer_depth": 0x80}):
         with pytest.raises(fm.FmError) as ei:
             fm.fm_set_tuning(h, **bad)
         assert ei.value.code == fm.FM_EINVAL
