@@ -800,7 +800,7 @@ def bench_locate(args, torch, fmocc, h, dev, flush):
 def bench_e2e_serving_abi(args, fmocc, h, reads, world):
     """The main batch end to end through the host-buffer serving ABI: the 10^7 reads submitted
     from host memory as requests of the server's maximum batch (fm_server_submit copies them),
-    searched by the server's workers (two batches in flight), and every result read back to host
+    searched by the server's workers (three batches in flight), and every result read back to host
     memory (fm_server_poll); timed from the first submission to the last result."""
     chunk = 262_144
     nr = len(reads)

@@ -303,7 +303,7 @@ typedef struct fm_server_params {
                                  that growth and the batch is split in two (a single request
                                  that does not fit finishes with FM_ENOMEM) */
     uint32_t kernel;          /* FM_KERNEL_* */
-    uint32_t inflight;        /* batches in flight, one worker thread each (0: 2; at most 4) */
+    uint32_t inflight;        /* batches in flight, one worker thread each (0: 3; at most 4) */
 } fm_server_params;
 
 /* Result of one request, owned by the server until fm_server_release. */
