@@ -182,6 +182,13 @@ def test_server_errors(fm):
     with fm.Server(h, strands=2) as srv:
         with pytest.raises(fm.FmError):
             srv.submit(np.array([0, 9], np.uint8), np.array([0, 2], np.uint32), 1)
+        # one bad code deep inside a request of several reads, whatever its high bits
+        for bad in (4, 128, 255):
+            codes = np.zeros(1000, np.uint8)
+            codes[777] = bad
+            with pytest.raises(fm.FmError) as ei:
+                srv.submit(codes, np.arange(0, 1001, 200, dtype=np.uint32), 1)
+            assert ei.value.code == fm.FM_EINVAL
         with pytest.raises(fm.FmError):
             srv.poll(123456)
         t = srv.submit(np.zeros(0, np.uint8), np.array([0], np.uint32), 1)
