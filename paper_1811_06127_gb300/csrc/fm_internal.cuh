@@ -48,18 +48,15 @@ struct IndexView {
     uint32_t kdepth;
     // Pair table (0 when absent): for every row i, the two symbols before suffix SA[i],
     // BWT[LF(i)] and BWT[i], as one 4-bit code 4 b1 + b2, so that one rank over pairs moves an
-    // interval back two symbols.  64-row blocks of 64 bytes: uint16 cnt[16] (pairs in the
-    // rows of its superblock of 32768 rows before the block, special rows excluded), then the
-    // 64 rows' 4-bit pair codes as bit planes: 32-bit word 4h + p holds bit p of the codes of
-    // rows 32h .. 32h+31 (row 32h + r at bit r), so one uint4 holds all four planes of a half
-    // block.  psb[s][c]: pairs c in
-    // the rows before superblock s; pc2[c]: rows whose suffix sorts before every string
-    // starting with pair c.  The $ row and the row whose LF is the $ row have no pair: stored
-    // as pair 0 and excluded from the counts (prow_a, prow_b).
-    const uint8_t *pblk;
-    const uint32_t *psb;
+    // interval back two symbols.  One 16-byte record per (pair code c, 64-row block j), at
+    // prec[c * pnblk + j]: x = rows before block j holding pair c, y and z = which rows of
+    // the block hold pair c (rows 0-31 at bits 0-31 of y, rows 32-63 of z), w = 0.  A rank of
+    // one pair is one record: one 16-byte load.  The $ row and the row whose LF is the $ row
+    // have no pair and are in no record's rows.  pc2[c]: rows whose suffix sorts before every
+    // string starting with pair c.
+    const uint4 *prec;
     const uint32_t *pc2;
-    uint32_t prow_a, prow_b;
+    uint32_t pnblk;
     uint32_t pairs;
 };
 
@@ -129,9 +126,8 @@ struct fm_index {
     uint32_t kt_depth = 0;           // levels built (0: none)
     uint2 *d_kt_rev = nullptr;       // the same tables of the index of reverse(R) (D bound)
     uint32_t *d_kbits_rev = nullptr;
-    uint8_t *d_pblk = nullptr;       // pair table (see IndexView)
-    uint32_t *d_psb = nullptr;       // its superblock counts, then pc2[16]
-    uint32_t prow_a = 0, prow_b = 0;
+    uint4 *d_prec = nullptr;         // pair table (see IndexView)
+    uint32_t *d_pc2 = nullptr;       // its pc2[16]
     bool pairs_built = false;
     // grow-on-demand scratch of the search calls
     fm::Scratch s_qmeta, s_raw, s_spill, s_group, s_scan, s_plain, s_misc;
@@ -196,7 +192,8 @@ uint32_t kmer_depth_for(const fm_index *h);
 int ensure_kmer(fm_index *h, cudaStream_t st);
 // pair table: built on first use when the tuning asks for pair steps
 int ensure_pairs(fm_index *h, cudaStream_t st);
-constexpr uint32_t kPairRows = 64, kPairSuper = 32768;
+constexpr uint32_t kPairRows = 64;
+constexpr uint32_t kPairScanBlocks = 512;   // blocks one thread of the pair count pass sums
 constexpr uint32_t kMaxKmerDepth = 15;   // 2 x 4^15 entries: 32-bit table indices
 // D lower bound per query; qmeta (one uint4 per query, or with stride kStageU4 the staging
 // record of the persistent search: that uint4, then the query as 2-bit symbols) and/or D_out
@@ -241,11 +238,11 @@ __device__ __forceinline__ void ldg256(const void *p, uint4 &a, uint4 &b) {
                  : "l"(p));
 }
 
-// L1 policy of the random gathers.  Checkpoint blocks, pair blocks and the interval-table
+// L1 policy of the random gathers.  Checkpoint blocks, pair records and the interval-table
 // sectors of levels >= kL1TableLevel are read once per search node at uniformly random places
 // of a table far larger than L1; they are loaded without allocating L1 lines, so that they do
-// not evict the lines that are reused (the shallow table levels, the occurrence bits, the pair
-// superblock counts), which stay in L1 across nodes, queries and warps of the SM.
+// not evict the lines that are reused (the shallow table levels, the occurrence bits, the
+// query data), which stay in L1 across nodes, queries and warps of the SM.
 constexpr bool kGatherNoL1 = true;
 constexpr uint32_t kL1TableLevel = 8;
 __device__ __forceinline__ void ldg256_na(const void *p, uint4 &a, uint4 &b) {
@@ -263,21 +260,6 @@ __device__ __forceinline__ uint32_t ldg32_na(const uint32_t *p) {
     if constexpr (kGatherNoL1) asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
     else v = __ldg(p);
     return v;
-}
-
-// The two sectors of a 64-byte pair block (its count word, its bit planes) are read by two loads;
-// with the L2 prefetch size of the line, the first miss brings both sectors from DRAM in one
-// access instead of two (measured on the headline search: 28% fewer DRAM bytes, same time).
-__device__ __forceinline__ uint32_t ldg32_na_line64(const uint32_t *p) {
-    uint32_t v;
-    asm("ld.global.nc.L1::no_allocate.L2::64B.u32 %0, [%1];" : "=r"(v) : "l"(p));
-    return v;
-}
-
-__device__ __forceinline__ void ldg256_na_line64(const void *p, uint4 &a, uint4 &b) {
-    asm("ld.global.nc.L1::no_allocate.L2::64B.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
-        : "l"(p));
 }
 
 __device__ __forceinline__ uint2 ldg64_na(const uint2 *p) {
@@ -371,45 +353,20 @@ __device__ __forceinline__ uint32_t low_mask(uint32_t width) {
     return m;
 }
 
-// The part of a pair block one rank of pair c needs: the word holding cnt[c] (two uint16 per
-// word, low half first) and the bit planes of the 64 rows (s0: rows 0-31, s1: rows 32-63).
-struct PairBlk {
-    uint32_t cw;
-    uint4 s0, s1;
-};
-
-__device__ __forceinline__ void load_pair_block(const IndexView &ix, uint32_t j, uint32_t c, PairBlk &B) {
-    const uint8_t *p = ix.pblk + (size_t)j * 64;
-    B.cw = ldg32_na_line64((const uint32_t *)p + (c >> 1));
-    ldg256_na_line64(p + 32, B.s0, B.s1);
+// One record of the pair table (a 16-byte read-only load that allocates no L1 line).
+__device__ __forceinline__ uint4 load_pair_rec(const IndexView &ix, uint32_t c, uint32_t j) {
+    const uint4 *p = ix.prec + (size_t)c * ix.pnblk + j;
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
 }
 
-// Rows among the 32 of one half block whose pair code is c: a row matches where every bit
-// plane agrees with the corresponding bit of c (planes XOR-ed with that bit spread over the
-// word are zero there).
-__device__ __forceinline__ uint32_t pair_eq32(const uint4 &pl, uint32_t c) {
-    const uint32_t s0 = 0u - (c & 1u), s1 = 0u - ((c >> 1) & 1u), s2 = 0u - ((c >> 2) & 1u),
-                   s3 = 0u - (c >> 3);
-    return ~((pl.x ^ s0) | (pl.y ^ s1) | (pl.z ^ s2) | (pl.w ^ s3));
-}
-
-// Pairs c among the first o rows (o in [0, 64]) of a pair block.
-__device__ __forceinline__ uint32_t pair_count_in(const PairBlk &B, uint32_t c, uint32_t o) {
+// Pairs c in rows [0, p), r the record of c for the block of p.
+__device__ __forceinline__ uint32_t pair_rank(const uint4 &r, uint32_t p) {
+    const uint32_t o = p % kPairRows;
     const uint32_t olo = o < 32u ? o : 32u;
-    return __popc(pair_eq32(B.s0, c) & low_mask(olo)) + __popc(pair_eq32(B.s1, c) & low_mask(o - olo));
-}
-
-// Pairs c in rows [0, p) (rows without a pair excluded), B the pair block of p loaded for c.
-__device__ __forceinline__ uint32_t pair_rank(const IndexView &ix, const PairBlk &B, uint32_t c,
-                                              uint32_t p) {
-    const uint32_t cnt = (c & 1u) ? (B.cw >> 16) : (B.cw & 0xffffu);
-    uint32_t n = __ldg(ix.psb + (size_t)(p / kPairSuper) * 16u + c) + cnt +
-                 pair_count_in(B, c, p % kPairRows);
-    if (c == 0u) {
-        const uint32_t b0 = p / kPairRows * kPairRows;   // rows without a pair are stored as 0
-        n -= (ix.prow_a >= b0 && ix.prow_a < p ? 1u : 0u) + (ix.prow_b >= b0 && ix.prow_b < p ? 1u : 0u);
-    }
-    return n;
+    return r.x + __popc(r.y & low_mask(olo)) + __popc(r.z & low_mask(o - olo));
 }
 
 // C, G and T among the first t symbols (t in [0, 32]) of one 64-bit word, in 32-bit steps:

@@ -22,11 +22,9 @@ IndexView view_fwd(const fm_index *h) {
     v.kt = h->d_kt;
     v.kbits = h->d_kbits;
     v.kdepth = h->kt_depth;
-    v.pblk = h->d_pblk;
-    v.psb = h->d_psb;
-    v.pc2 = h->d_psb ? h->d_psb + (h->n + 1) / kPairSuper * 16 + 16 : nullptr;
-    v.prow_a = h->prow_a;
-    v.prow_b = h->prow_b;
+    v.prec = h->d_prec;
+    v.pc2 = h->d_pc2;
+    v.pnblk = (uint32_t)((h->n + 1) / kPairRows + 1);
     v.pairs = h->pairs_built && h->tune.pairs ? 1u : 0u;
     return v;
 }
@@ -37,8 +35,7 @@ IndexView view_rev(const fm_index *h) {
     v.kt = h->d_kt_rev;
     v.kbits = h->d_kbits_rev;
     v.kdepth = h->d_kt_rev ? h->kt_depth : 0u;
-    v.pblk = nullptr;
-    v.psb = nullptr;
+    v.prec = nullptr;
     v.pc2 = nullptr;
     v.pairs = 0;
     v.dollar = (uint32_t)h->rev_dollar;
@@ -153,13 +150,11 @@ __global__ void __launch_bounds__(128) k_exact(IndexView ix, const uint8_t *__re
                     break;
                 }
                 const uint32_t pc = 4u * b1 + b2, pk = k, pl = l + 1u;
-                PairBlk Pk, Pl;
-                load_pair_block(ix, pk / kPairRows, pc, Pk);
-                if (pl / kPairRows == pk / kPairRows) Pl = Pk;
-                else load_pair_block(ix, pl / kPairRows, pc, Pl);
+                const uint4 Rk = load_pair_rec(ix, pc, pk / kPairRows);
+                const uint4 Rl = pl / kPairRows == pk / kPairRows ? Rk : load_pair_rec(ix, pc, pl / kPairRows);
                 const uint32_t c2 = __ldg(ix.pc2 + pc);
-                k = c2 + pair_rank(ix, Pk, pc, pk);
-                l = c2 + pair_rank(ix, Pl, pc, pl) - 1u;
+                k = c2 + pair_rank(Rk, pk);
+                l = c2 + pair_rank(Rl, pl) - 1u;
                 --i;
                 continue;
             }
@@ -421,17 +416,20 @@ __global__ void __launch_bounds__(256) k_kmer_bits(const uint2 *__restrict__ kt,
 
 // -------------------------------------------------------------------------------------------
 // Pair table.  Row i's pair is (BWT[LF(i)], BWT[i]) with LF(i) = C[b] + rank(b, i) + 1 for
-// b = BWT[i] (Eq. 4-5): the two symbols before suffix SA[i].  Thread per 32 rows (the four bit
-// planes of one half block); the $ row and the row whose LF is the $ row have none (stored as
-// 0, row b recorded).
+// b = BWT[i] (Eq. 4-5): the two symbols before suffix SA[i].  Thread per 32 rows (one half of
+// a block): the rows of each pair code among them, written into the sixteen records of the
+// block (word 1 + half).  The $ row and the row whose LF is the $ row have no pair (row b
+// recorded).
 // -------------------------------------------------------------------------------------------
 template <int I>
-__global__ void __launch_bounds__(256) k_pair_sym(IndexView ix, uint8_t *__restrict__ pblk, uint64_t N,
-                                                  uint32_t *__restrict__ row_b) {
+__global__ void __launch_bounds__(256) k_pair_sym(IndexView ix, uint4 *__restrict__ prec, uint64_t nblk,
+                                                  uint64_t N, uint32_t *__restrict__ row_b) {
     const uint64_t halves = (N + 31) / 32;
     for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < halves;
          w += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t plane[4] = {0u, 0u, 0u, 0u};
+        uint32_t rows[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) rows[c] = 0u;
         for (uint32_t t = 0; t < 32u; ++t) {
             const uint64_t i64 = 32 * w + t;
             if (i64 >= N) break;
@@ -450,46 +448,43 @@ __global__ void __launch_bounds__(256) k_pair_sym(IndexView ix, uint8_t *__restr
             const uint32_t jl = lf / I;
             Blk<I> L;
             load_block<I>(ix.blocks, jl, lf - jl * I + 1u, L);
-            const uint32_t b1 = sym_in<I>(L, jl, lf);
-            const uint32_t code = 4u * b1 + b;
+            const uint32_t code = 4u * sym_in<I>(L, jl, lf) + b;
 #pragma unroll
-            for (int p = 0; p < 4; ++p) plane[p] |= ((code >> p) & 1u) << t;
+            for (int c = 0; c < 16; ++c) rows[c] |= (code == (uint32_t)c ? 1u : 0u) << t;
         }
-        const uint64_t r0 = 32 * w;
-        uint32_t *dst = (uint32_t *)(pblk + (r0 / kPairRows) * 64 + 32 + ((r0 % kPairRows) / 32) * 16);
+        const uint64_t j = w / 2;
+        uint32_t *dst = reinterpret_cast<uint32_t *>(prec + j) + 1 + (w & 1);
 #pragma unroll
-        for (int p = 0; p < 4; ++p) dst[p] = plane[p];
+        for (int c = 0; c < 16; ++c) dst[(size_t)c * nblk * 4] = rows[c];
     }
 }
 
-// Thread per (superblock, pair): the block counts relative to the superblock (uint16, written
-// into each block), and the superblock's total; rows >= N and rows without a pair not counted.
-__global__ void __launch_bounds__(256) k_pair_counts(uint8_t *__restrict__ pblk, uint64_t N,
-                                                     uint64_t nblk, uint32_t prow_a, uint32_t prow_b,
-                                                     uint32_t *__restrict__ sbtot, uint64_t nsb) {
-    const uint32_t per = kPairSuper / kPairRows;
-    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nsb * 16;
+// Thread per (pair code c, run of kPairScanBlocks blocks): x of each record = pairs c in the
+// run's rows before its block; the run's total goes to tot.
+__global__ void __launch_bounds__(256) k_pair_counts(uint4 *__restrict__ prec, uint64_t nblk, uint64_t nrun,
+                                                     uint32_t *__restrict__ tot) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nrun * 16;
          t += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t sbi = t / 16;
-        const uint32_t c = (uint32_t)(t % 16);
+        const uint64_t c = t / nrun, run = t % nrun;
+        uint4 *rec = prec + c * nblk;
+        const uint64_t j0 = run * kPairScanBlocks;
+        const uint64_t j1 = j0 + kPairScanBlocks < nblk ? j0 + kPairScanBlocks : nblk;
         uint32_t acc = 0;
-        const uint64_t j1 = (sbi + 1) * per < nblk ? (sbi + 1) * per : nblk;
-        for (uint64_t j = sbi * per; j < j1; ++j) {
-            uint8_t *blk = pblk + j * 64;
-            *(uint16_t *)(blk + 2 * c) = (uint16_t)acc;
-            const uint4 *sw = (const uint4 *)(blk + 32);
-            const uint64_t r0 = j * kPairRows;
-            const uint32_t rows = N > r0 ? (uint32_t)(N - r0 < kPairRows ? N - r0 : kPairRows) : 0u;
-            PairBlk P;
-            P.s0 = sw[0];
-            P.s1 = sw[1];
-            uint32_t n = pair_count_in(P, c, rows);   // rows >= N hold code 0 and are not counted
-            if (c == 0u)
-                n -= (prow_a >= r0 && prow_a < r0 + rows ? 1u : 0u) +
-                     (prow_b >= r0 && prow_b < r0 + rows ? 1u : 0u);
-            acc += n;
+        for (uint64_t j = j0; j < j1; ++j) {
+            rec[j].x = acc;
+            acc += __popc(rec[j].y) + __popc(rec[j].z);
         }
-        sbtot[t] = acc;
+        tot[t] = acc;
+    }
+}
+
+// Thread per record: add the pairs c before its run (base[c * nrun + run]).
+__global__ void __launch_bounds__(256) k_pair_base(uint4 *__restrict__ prec, uint64_t nblk, uint64_t nrun,
+                                                   const uint32_t *__restrict__ base) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nblk * 16;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t c = t / nblk, j = t % nblk;
+        prec[t].x += base[c * nrun + j / kPairScanBlocks];
     }
 }
 
@@ -623,76 +618,77 @@ int ensure_pairs(fm_index *h, cudaStream_t st) {
     if (!h->tune.pairs || h->pairs_built || h->borrowed) return FM_OK;
     const uint64_t N = h->n + 1;                    // rows
     const uint64_t nblk = N / kPairRows + 1;        // rank positions 0..N
-    const uint64_t nsb = N / kPairSuper + 1;
+    const uint64_t nrun = (nblk + kPairScanBlocks - 1) / kPairScanBlocks;
     const uint32_t sentinel = 0xffffffffu;
-    uint32_t *d_rowb = nullptr, *d_sbtot = nullptr;
+    uint32_t *d_rowb = nullptr, *d_tot = nullptr;
     int rc = FM_OK;
     FM_CUDA_TRY(h, cudaStreamSynchronize(st));
-    if (cudaMalloc(&h->d_pblk, nblk * 64) != cudaSuccess ||
-        cudaMalloc(&h->d_psb, (nsb * 16 + 16) * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc(&d_sbtot, nsb * 16 * sizeof(uint32_t)) != cudaSuccess ||
+    if (cudaMalloc(&h->d_prec, nblk * 16 * sizeof(uint4)) != cudaSuccess ||
+        cudaMalloc(&h->d_pc2, 16 * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&d_tot, nrun * 16 * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&d_rowb, sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
         rc = set_error(h, FM_ENOMEM, "pair table: out of device memory");
     }
-    std::vector<uint32_t> tot, psb;
+    std::vector<uint32_t> tot, base;
     if (!rc) {
-        FM_CUDA_TRY(h, cudaMemsetAsync(h->d_pblk, 0, nblk * 64, st));
+        FM_CUDA_TRY(h, cudaMemsetAsync(h->d_prec, 0, nblk * 16 * sizeof(uint4), st));
         FM_CUDA_TRY(h, cudaMemcpyAsync(d_rowb, &sentinel, 4, cudaMemcpyHostToDevice, st));
         IndexView ix = view_fwd(h);
         const int grid = grid_occ(h, (N + 7) / 8, 256);
         switch (h->interval) {
-            case 32: k_pair_sym<32><<<grid, 256, 0, st>>>(ix, h->d_pblk, N, d_rowb); break;
-            case 64: k_pair_sym<64><<<grid, 256, 0, st>>>(ix, h->d_pblk, N, d_rowb); break;
-            case 128: k_pair_sym<128><<<grid, 256, 0, st>>>(ix, h->d_pblk, N, d_rowb); break;
-            default: k_pair_sym<256><<<grid, 256, 0, st>>>(ix, h->d_pblk, N, d_rowb); break;
+            case 32: k_pair_sym<32><<<grid, 256, 0, st>>>(ix, h->d_prec, nblk, N, d_rowb); break;
+            case 64: k_pair_sym<64><<<grid, 256, 0, st>>>(ix, h->d_prec, nblk, N, d_rowb); break;
+            case 128: k_pair_sym<128><<<grid, 256, 0, st>>>(ix, h->d_prec, nblk, N, d_rowb); break;
+            default: k_pair_sym<256><<<grid, 256, 0, st>>>(ix, h->d_prec, nblk, N, d_rowb); break;
         }
         FM_CUDA_TRY(h, cudaGetLastError());
         uint32_t rowb = sentinel;
         FM_CUDA_TRY(h, cudaMemcpyAsync(&rowb, d_rowb, 4, cudaMemcpyDeviceToHost, st));
         FM_CUDA_TRY(h, cudaStreamSynchronize(st));
         if (rowb == sentinel) rc = set_error(h, FM_ECUDA, "pair table: no row precedes the $ row");
-        h->prow_a = (uint32_t)h->dollar;
-        h->prow_b = rowb;
     }
     if (!rc) {
-        k_pair_counts<<<grid_occ(h, nsb * 16, 256), 256, 0, st>>>(h->d_pblk, N, nblk, h->prow_a,
-                                                                  h->prow_b, d_sbtot, nsb);
+        k_pair_counts<<<grid_occ(h, nrun * 16, 256), 256, 0, st>>>(h->d_prec, nblk, nrun, d_tot);
         FM_CUDA_TRY(h, cudaGetLastError());
-        tot.resize(nsb * 16);
-        FM_CUDA_TRY(h, cudaMemcpyAsync(tot.data(), d_sbtot, nsb * 16 * 4, cudaMemcpyDeviceToHost, st));
+        tot.resize(nrun * 16);
+        FM_CUDA_TRY(h, cudaMemcpyAsync(tot.data(), d_tot, nrun * 16 * 4, cudaMemcpyDeviceToHost, st));
         // the symbol of row 0 (the $ suffix) is T[n-1]: read it from the first checkpoint block
         uint8_t b0[32];
         FM_CUDA_TRY(h, cudaMemcpyAsync(b0, h->d_fwd, 32, cudaMemcpyDeviceToHost, st));
         FM_CUDA_TRY(h, cudaStreamSynchronize(st));
         const uint32_t last = b0[16] & 3u;
-        // superblock bases (exclusive scan per pair), then pc2
-        psb.assign(nsb * 16 + 16, 0u);
+        // run bases (exclusive scan per pair code), then pc2
+        base.assign(nrun * 16, 0u);
         uint64_t run[16] = {0};
-        for (uint64_t sbi = 0; sbi < nsb; ++sbi)
-            for (int c = 0; c < 16; ++c) {
-                psb[sbi * 16 + c] = (uint32_t)run[c];
-                run[c] += tot[sbi * 16 + c];
+        for (int c = 0; c < 16; ++c)
+            for (uint64_t r = 0; r < nrun; ++r) {
+                base[c * nrun + r] = (uint32_t)run[c];
+                run[c] += tot[c * nrun + r];
             }
         // rows before every string that starts with pair (b1, b2): the $ row, suffixes starting
         // with a symbol below b1, the suffix "b1 $" when R ends with b1, and suffixes starting
         // with b1 then a symbol below b2
+        uint32_t pc2[16];
         for (uint32_t b1 = 0; b1 < 4; ++b1)
             for (uint32_t b2 = 0; b2 < 4; ++b2) {
                 uint64_t v = 1 + h->C[b1] + (last == b1 ? 1 : 0);
                 for (uint32_t y = 0; y < b2; ++y) v += run[4 * b1 + y];
-                psb[nsb * 16 + 4 * b1 + b2] = (uint32_t)v;
+                pc2[4 * b1 + b2] = (uint32_t)v;
             }
-        FM_CUDA_TRY(h, cudaMemcpyAsync(h->d_psb, psb.data(), psb.size() * 4, cudaMemcpyHostToDevice, st));
+        FM_CUDA_TRY(h, cudaMemcpyAsync(d_tot, base.data(), base.size() * 4, cudaMemcpyHostToDevice, st));
+        FM_CUDA_TRY(h, cudaMemcpyAsync(h->d_pc2, pc2, sizeof(pc2), cudaMemcpyHostToDevice, st));
+        k_pair_base<<<grid_occ(h, nblk * 16, 256), 256, 0, st>>>(h->d_prec, nblk, nrun, d_tot);
+        FM_CUDA_TRY(h, cudaGetLastError());
         FM_CUDA_TRY(h, cudaStreamSynchronize(st));
     }
-    cudaFree(d_sbtot);
+    cudaFree(d_tot);
     cudaFree(d_rowb);
     if (rc) {
-        cudaFree(h->d_pblk);
-        cudaFree(h->d_psb);
-        h->d_pblk = nullptr;
-        h->d_psb = nullptr;
+        cudaFree(h->d_prec);
+        cudaFree(h->d_pc2);
+        h->d_prec = nullptr;
+        h->d_pc2 = nullptr;
         return rc;
     }
     h->pairs_built = true;
