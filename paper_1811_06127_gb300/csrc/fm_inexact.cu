@@ -336,11 +336,12 @@ __device__ __forceinline__ void expand(const SearchCfg &c, const uint4 &nd, cons
 // tables at once: the symbols it will prepend are W[i], W[i-1], ..., so after t steps its
 // string is W[i-t+1..i] X, of code code(X) 4^t + sum_s W[i-s] 4^(t-1-s).  With
 // tmax = min(L - d, i + 1) steps left in the tables, the string after tmax steps is tested
-// first (one occurrence bit); otherwise the longest occurring prefix length t is found by
-// bisection (longer strings occur only if their shorter suffixes do, and the code after t steps
-// is the code after tmax steps shifted right by 2 (tmax - t)).  The chain then ends after t + 1
-// steps, or after tmax steps becomes a result (i reaches -1) or an interval node at depth L.
-// nn counts the steps, as the one-step walk would count its nodes.
+// first: its table entry, whose k <= l says it occurs (an empty string's entry holds its
+// insertion point, k = l + 1); otherwise the longest occurring prefix length t is found by
+// bisection over occurrence bits (longer strings occur only if their shorter suffixes do, and
+// the code after t steps is the code after tmax steps shifted right by 2 (tmax - t)).  The
+// chain then ends after t + 1 steps, or after tmax steps becomes a result (i reaches -1) or an
+// interval node at depth L.  nn counts the steps, as the one-step walk would count its nodes.
 template <int I, class Q>
 __device__ __forceinline__ void exact_step(const SearchCfg &c, const uint4 &nd, const Q &qv,
                                            uint4 &out, bool &survive, bool &is_leaf,
@@ -354,8 +355,9 @@ __device__ __forceinline__ void exact_step(const SearchCfg &c, const uint4 &nd, 
         const uint32_t tmax = left < i + 1u ? left : i + 1u;
         uint32_t code = k;
         for (uint32_t s = 0; s < tmax; ++s) code = 4u * code + qv.w(i - s);
-        nblocks = 0;
-        if (!kt_occ1(c.ix, d + tmax, code)) {
+        const uint2 kl = kt_get(c.ix, d + tmax, code);
+        nblocks = kTabRead;
+        if (kl.x > kl.y) {
             uint32_t lo = 0, hi = tmax - 1u;   // X itself occurs (the node exists)
             while (lo < hi) {
                 const uint32_t mid = (lo + hi + 1u) >> 1;
@@ -367,8 +369,6 @@ __device__ __forceinline__ void exact_step(const SearchCfg &c, const uint4 &nd, 
             out = nd;
             return;
         }
-        const uint2 kl = kt_get(c.ix, d + tmax, code);
-        nblocks = kTabRead;
         nn = tmax;
         is_leaf = tmax == i + 1u;
         survive = !is_leaf;
