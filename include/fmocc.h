@@ -400,8 +400,8 @@ typedef struct fm_tuning {
                                    (FM_KMER_OFF for none) */
     uint32_t pair_steps;        /* 1 (default): searches advance exact continuations two symbols
                                    per step over a pair table (for each row, the two symbols
-                                   before its suffix; one 16-byte record per pair code and 64
-                                   rows, 256 B per 64 rows, 8 GB at n = 2e9, built from the
+                                   before its suffix; one 8-byte record per pair code and 32
+                                   rows, 4 B per row, 8 GB at n = 2e9, built from the
                                    index on the first call that needs it).  Intervals, insertion points
                                    and results are unchanged; an inexact search's stats[0] then
                                    omits the middle node of a two-symbol step that ends the

@@ -308,7 +308,7 @@ int fm_info(const fm_index *h, fm_info_t *out) {
     out->bytes_device = h->n_blocks * h->bbytes * (h->has_rev ? 2 : 1) + h->n_sa_sample * 4;
     if (h->kt_depth)   // forward tables, and the reverse index's own with it
         out->bytes_device += (h->d_kt_rev ? 2 : 1) * (2ull << (2 * h->kt_depth)) * (8 + 1.0 / 8);
-    if (h->pairs_built) out->bytes_device += ((h->n + 1) / fm::kPairRows + 1) * 16 * 16 + 64;
+    if (h->pairs_built) out->bytes_device += ((h->n + 1) / fm::kPairRows + 1) * 16 * 8 + 64;
     out->has_reverse = h->has_rev ? 1 : 0;
     out->both_strands = h->both_strands ? 1 : 0;
     out->device = h->device;

@@ -414,8 +414,8 @@ __device__ __forceinline__ void pair_step(const SearchCfg &c, const uint4 &nd, c
     const uint32_t pc = 4u * b1 + b2, pk = nd.z, pl = nd.w + 1u;
     const uint32_t jk = pk / kPairRows, jl = pl / kPairRows;
     const uint32_t c2 = __ldg(c.ix.pc2 + pc);
-    const uint4 Rk = load_pair_rec(c.ix, pc, jk);   // one record when k and l+1 share a block
-    const uint4 Rl = jl == jk ? Rk : load_pair_rec(c.ix, pc, jl);
+    const uint2 Rk = load_pair_rec(c.ix, pc, jk);   // one record when k and l+1 share a block
+    const uint2 Rl = jl == jk ? Rk : load_pair_rec(c.ix, pc, jl);
     const uint32_t k2 = c2 + pair_rank(Rk, pk);
     const uint32_t l2 = c2 + pair_rank(Rl, pl) - 1u;
     const bool alive = k2 <= l2;

@@ -48,13 +48,13 @@ struct IndexView {
     uint32_t kdepth;
     // Pair table (0 when absent): for every row i, the two symbols before suffix SA[i],
     // BWT[LF(i)] and BWT[i], as one 4-bit code 4 b1 + b2, so that one rank over pairs moves an
-    // interval back two symbols.  One 16-byte record per (pair code c, 64-row block j), at
-    // prec[c * pnblk + j]: x = rows before block j holding pair c, y and z = which rows of
-    // the block hold pair c (rows 0-31 at bits 0-31 of y, rows 32-63 of z), w = 0.  A rank of
-    // one pair is one record: one 16-byte load.  The $ row and the row whose LF is the $ row
+    // interval back two symbols.  One 8-byte record per (pair code c, 32-row block j), at
+    // uint2 entry c * pnblk + j of prec: x = rows before block j holding pair c, y = which
+    // rows of the block hold pair c (row 32 j + r at bit r).  A rank of one pair is one
+    // record: one 8-byte load.  The $ row and the row whose LF is the $ row
     // have no pair and are in no record's rows.  pc2[c]: rows whose suffix sorts before every
     // string starting with pair c.
-    const uint4 *prec;
+    const uint2 *prec;
     const uint32_t *pc2;
     uint32_t pnblk;
     uint32_t pairs;
@@ -126,7 +126,7 @@ struct fm_index {
     uint32_t kt_depth = 0;           // levels built (0: none)
     uint2 *d_kt_rev = nullptr;       // the same tables of the index of reverse(R) (D bound)
     uint32_t *d_kbits_rev = nullptr;
-    uint4 *d_prec = nullptr;         // pair table (see IndexView)
+    uint2 *d_prec = nullptr;         // pair table (see IndexView)
     uint32_t *d_pc2 = nullptr;       // its pc2[16]
     bool pairs_built = false;
     // grow-on-demand scratch of the search calls
@@ -192,7 +192,7 @@ uint32_t kmer_depth_for(const fm_index *h);
 int ensure_kmer(fm_index *h, cudaStream_t st);
 // pair table: built on first use when the tuning asks for pair steps
 int ensure_pairs(fm_index *h, cudaStream_t st);
-constexpr uint32_t kPairRows = 64;
+constexpr uint32_t kPairRows = 32;
 constexpr uint32_t kPairScanBlocks = 512;   // blocks one thread of the pair count pass sums
 constexpr uint32_t kMaxKmerDepth = 15;   // 2 x 4^15 entries: 32-bit table indices
 // D lower bound per query; qmeta (one uint4 per query, or with stride kStageU4 the staging
@@ -353,20 +353,18 @@ __device__ __forceinline__ uint32_t low_mask(uint32_t width) {
     return m;
 }
 
-// One record of the pair table (a 16-byte read-only load that allocates no L1 line).
-__device__ __forceinline__ uint4 load_pair_rec(const IndexView &ix, uint32_t c, uint32_t j) {
-    const uint4 *p = ix.prec + (size_t)c * ix.pnblk + j;
-    uint4 v;
-    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+// One record of the pair table (a read-only load that allocates no L1 line).  Measured on the
+// headline search: 8-byte records of 32 rows 518 ms, 16-byte records of 64 rows 534 ms,
+// 32-byte records of 128 rows 595 ms (the same table size).
+__device__ __forceinline__ uint2 load_pair_rec(const IndexView &ix, uint32_t c, uint32_t j) {
+    const uint2 *p = ix.prec + (size_t)c * ix.pnblk + j;
+    uint2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
     return v;
 }
-
 // Pairs c in rows [0, p), r the record of c for the block of p.
-__device__ __forceinline__ uint32_t pair_rank(const uint4 &r, uint32_t p) {
-    const uint32_t o = p % kPairRows;
-    const uint32_t olo = o < 32u ? o : 32u;
-    return r.x + __popc(r.y & low_mask(olo)) + __popc(r.z & low_mask(o - olo));
+__device__ __forceinline__ uint32_t pair_rank(const uint2 &r, uint32_t p) {
+    return r.x + __popc(r.y & low_mask(p % kPairRows));
 }
 
 // C, G and T among the first t symbols (t in [0, 32]) of one 64-bit word, in 32-bit steps:

@@ -150,8 +150,8 @@ __global__ void __launch_bounds__(128) k_exact(IndexView ix, const uint8_t *__re
                     break;
                 }
                 const uint32_t pc = 4u * b1 + b2, pk = k, pl = l + 1u;
-                const uint4 Rk = load_pair_rec(ix, pc, pk / kPairRows);
-                const uint4 Rl = pl / kPairRows == pk / kPairRows ? Rk : load_pair_rec(ix, pc, pl / kPairRows);
+                const uint2 Rk = load_pair_rec(ix, pc, pk / kPairRows);
+                const uint2 Rl = pl / kPairRows == pk / kPairRows ? Rk : load_pair_rec(ix, pc, pl / kPairRows);
                 const uint32_t c2 = __ldg(ix.pc2 + pc);
                 k = c2 + pair_rank(Rk, pk);
                 l = c2 + pair_rank(Rl, pl) - 1u;
@@ -416,13 +416,12 @@ __global__ void __launch_bounds__(256) k_kmer_bits(const uint2 *__restrict__ kt,
 
 // -------------------------------------------------------------------------------------------
 // Pair table.  Row i's pair is (BWT[LF(i)], BWT[i]) with LF(i) = C[b] + rank(b, i) + 1 for
-// b = BWT[i] (Eq. 4-5): the two symbols before suffix SA[i].  Thread per 32 rows (one half of
-// a block): the rows of each pair code among them, written into the sixteen records of the
-// block (word 1 + half).  The $ row and the row whose LF is the $ row have no pair (row b
-// recorded).
+// b = BWT[i] (Eq. 4-5): the two symbols before suffix SA[i].  Thread per 32-row block: the
+// rows of each pair code among them, written into the sixteen records of the block (word 1).
+// The $ row and the row whose LF is the $ row have no pair (row b recorded).
 // -------------------------------------------------------------------------------------------
 template <int I>
-__global__ void __launch_bounds__(256) k_pair_sym(IndexView ix, uint4 *__restrict__ prec, uint64_t nblk,
+__global__ void __launch_bounds__(256) k_pair_sym(IndexView ix, uint2 *__restrict__ prec, uint64_t nblk,
                                                   uint64_t N, uint32_t *__restrict__ row_b) {
     const uint64_t halves = (N + 31) / 32;
     for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < halves;
@@ -452,34 +451,32 @@ __global__ void __launch_bounds__(256) k_pair_sym(IndexView ix, uint4 *__restric
 #pragma unroll
             for (int c = 0; c < 16; ++c) rows[c] |= (code == (uint32_t)c ? 1u : 0u) << t;
         }
-        const uint64_t j = w / 2;
-        uint32_t *dst = reinterpret_cast<uint32_t *>(prec + j) + 1 + (w & 1);
 #pragma unroll
-        for (int c = 0; c < 16; ++c) dst[(size_t)c * nblk * 4] = rows[c];
+        for (int c = 0; c < 16; ++c) prec[(size_t)c * nblk + w].y = rows[c];
     }
 }
 
 // Thread per (pair code c, run of kPairScanBlocks blocks): x of each record = pairs c in the
 // run's rows before its block; the run's total goes to tot.
-__global__ void __launch_bounds__(256) k_pair_counts(uint4 *__restrict__ prec, uint64_t nblk, uint64_t nrun,
+__global__ void __launch_bounds__(256) k_pair_counts(uint2 *__restrict__ prec, uint64_t nblk, uint64_t nrun,
                                                      uint32_t *__restrict__ tot) {
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nrun * 16;
          t += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t c = t / nrun, run = t % nrun;
-        uint4 *rec = prec + c * nblk;
+        uint2 *rec = prec + c * nblk;
         const uint64_t j0 = run * kPairScanBlocks;
         const uint64_t j1 = j0 + kPairScanBlocks < nblk ? j0 + kPairScanBlocks : nblk;
         uint32_t acc = 0;
         for (uint64_t j = j0; j < j1; ++j) {
             rec[j].x = acc;
-            acc += __popc(rec[j].y) + __popc(rec[j].z);
+            acc += __popc(rec[j].y);
         }
         tot[t] = acc;
     }
 }
 
 // Thread per record: add the pairs c before its run (base[c * nrun + run]).
-__global__ void __launch_bounds__(256) k_pair_base(uint4 *__restrict__ prec, uint64_t nblk, uint64_t nrun,
+__global__ void __launch_bounds__(256) k_pair_base(uint2 *__restrict__ prec, uint64_t nblk, uint64_t nrun,
                                                    const uint32_t *__restrict__ base) {
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nblk * 16;
          t += (uint64_t)gridDim.x * blockDim.x) {
@@ -623,7 +620,7 @@ int ensure_pairs(fm_index *h, cudaStream_t st) {
     uint32_t *d_rowb = nullptr, *d_tot = nullptr;
     int rc = FM_OK;
     FM_CUDA_TRY(h, cudaStreamSynchronize(st));
-    if (cudaMalloc(&h->d_prec, nblk * 16 * sizeof(uint4)) != cudaSuccess ||
+    if (cudaMalloc(&h->d_prec, nblk * 16 * sizeof(uint2)) != cudaSuccess ||
         cudaMalloc(&h->d_pc2, 16 * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&d_tot, nrun * 16 * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&d_rowb, sizeof(uint32_t)) != cudaSuccess) {
@@ -632,7 +629,7 @@ int ensure_pairs(fm_index *h, cudaStream_t st) {
     }
     std::vector<uint32_t> tot, base;
     if (!rc) {
-        FM_CUDA_TRY(h, cudaMemsetAsync(h->d_prec, 0, nblk * 16 * sizeof(uint4), st));
+        FM_CUDA_TRY(h, cudaMemsetAsync(h->d_prec, 0, nblk * 16 * sizeof(uint2), st));
         FM_CUDA_TRY(h, cudaMemcpyAsync(d_rowb, &sentinel, 4, cudaMemcpyHostToDevice, st));
         IndexView ix = view_fwd(h);
         const int grid = grid_occ(h, (N + 7) / 8, 256);
