@@ -423,8 +423,8 @@ __global__ void __launch_bounds__(256) k_kmer_bits(const uint2 *__restrict__ kt,
 template <int I>
 __global__ void __launch_bounds__(256) k_pair_sym(IndexView ix, uint2 *__restrict__ prec, uint64_t nblk,
                                                   uint64_t N, uint32_t *__restrict__ row_b) {
-    const uint64_t halves = (N + 31) / 32;
-    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < halves;
+    const uint64_t nrows32 = (N + 31) / 32;   // 32-row blocks holding rows
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < nrows32;
          w += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t rows[16];
 #pragma unroll
