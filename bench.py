@@ -52,8 +52,7 @@ BLOCK_BYTES = {32: 32, 64: 32, 128: 64, 256: 96}
 # keyed by (interval, reference bp, reads, canonical enumeration on, interval-table depth, pair
 # steps on) and reported only when the run matches that configuration.  An entry is removed
 # when the kernel changes and added back from a fresh capture.
-TRAFFIC_NCU = {(64, 2_000_000_000, 10_000_000, True, 14, True): 2.094946075648e12 + 5.34521088e8,
-               (32, 2_000_000_000, 10_000_000, True, 14, True): 2.112166277888e12 + 5.31737344e8}
+TRAFFIC_NCU = {}
 
 
 def parse():
@@ -97,7 +96,7 @@ def parse():
     ap.add_argument("--chain2-min", type=int, default=0,
                     help="persistent kernel: step second exact chains when this many lanes hold "
                          "one (0: library default)")
-    ap.add_argument("--tune-reads", type=int, default=200_000)
+    ap.add_argument("--tune-reads", type=int, default=1_000_000)
     ap.add_argument("--tune-cache", default=None, help="JSON cache of tuning results")
     ap.add_argument("--cpu-sample-reads", type=int, default=200_000)
     ap.add_argument("--cpu-sample-ref", type=int, default=32_000_000)

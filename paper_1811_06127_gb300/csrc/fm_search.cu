@@ -250,7 +250,11 @@ __global__ void __launch_bounds__(128) k_dcalc(IndexView rv, const uint8_t *__re
         };
         uint32_t k = 0, l = rv.n;
         bool fresh = true;   // a window starts at i ([k, l] = [0, n])
-        for (uint32_t i = 0; i < m && !bad;) {
+        // Without a D array to fill, the pass stops once more windows have closed than the
+        // query allows differences (zq): D only prunes, and every node at a position past that
+        // breakpoint is pruned whatever the further breakpoints are.
+        const uint32_t zq = (modes ? (uint32_t)modes[r] : defmode) & 15u;
+        for (uint32_t i = 0; i < m && !bad && (Dq || z <= zq);) {
             if (L && fresh) {
                 // The window's first dmax symbols from the tables of reverse(R): a window
                 // W[i..i+d-1] occurs in R exactly when its reverse occurs in reverse(R), the
