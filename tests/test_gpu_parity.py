@@ -153,10 +153,12 @@ def test_exact_matches_oracle(fm, interval):
     h.close()
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 62, 63, 64, 65, 127, 128, 4095, 32767, 32768, 70000])
+@pytest.mark.parametrize("n", [1, 2, 3, 30, 31, 32, 62, 63, 64, 65, 127, 128, 4095, 16382,
+                               16383, 16384, 32767, 32768, 70000])
 def test_exact_pair_steps_edge_sizes(fm, n):
-    """Listing 1 two symbols per step over the pair table on texts whose row count falls on
-    and around pair-block (64) and superblock (32768) boundaries: every string of length <= 5
+    """Listing 1 two symbols per step over the pair table on texts whose row count (n + 1)
+    falls on and around pair-record (32 rows) and count-run (512 records, 16384 rows)
+    boundaries, and around the checkpoint intervals: every string of length <= 5
     and random reads, occurring or not (insertion points included), with and without pair
     steps and tables, equal the oracle's."""
     R = synth.uniform_text(900 + n, n) if n > 3 else np.array([0, 0, 1][:n], np.uint8)
