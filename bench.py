@@ -604,6 +604,12 @@ def main():
                                         "no capture of this configuration (interval, size, "
                                         "tables, pair steps)"),
                      "kernel": "k_inexact_persistent", "kernel_ms": k_ms,
+                     # the captured DRAM bytes over this run's kernel time, and that rate over
+                     # the copy peak (random reads move whole DRAM lines: traffic > algorithmic)
+                     "traffic_gb_s": (TRAFFIC_NCU[traffic_key] / (k_ms / 1000) / 1e9
+                                      if traffic_key in TRAFFIC_NCU else None),
+                     "traffic_frac": (TRAFFIC_NCU[traffic_key] / (k_ms / 1000) / 1e9 / hbm_peak
+                                      if traffic_key in TRAFFIC_NCU else None),
                      "gather_ceiling": ceil_main,
                      # every 32-byte unit the kernel gathers (checkpoint blocks and table or pair
                      # sectors) per second, over the live random 32-byte gather ceiling; above 1
@@ -615,7 +621,7 @@ def main():
                          blocks_per_step / (k_ms / 1000) / 1e9 / ceil_main["g_gathers_s"]),
                      "algorithmic_bytes": alg_bytes, "peak_kind": peak_kind,
                      "per_unit": f"{bbytes} B per checkpoint block read and 32 B per "
-                                 f"interval-table or pair-table sector read; "
+                                 f"interval-table sector or pair record read; "
                                  f"{blocks_per_step / max(nodes_per_step, 1):.3f} blocks and "
                                  f"{tables_per_step / max(nodes_per_step, 1):.3f} table sectors "
                                  f"per node, {nodes_per_step / nq:.1f} nodes per query"},
