@@ -401,8 +401,10 @@ typedef struct fm_tuning {
     uint32_t pair_steps;        /* 1 (default): searches advance exact continuations two symbols
                                    per step over a pair table (for each row, the two symbols
                                    before its suffix; one 8-byte record per pair code and 32
-                                   rows, 4 B per row, 8 GB at n = 2e9, built from the
-                                   index on the first call that needs it).  Intervals, insertion points
+                                   rows, 4 B per row, 8 GB at n = 2e9, and as much again for
+                                   the index of reverse(R), over which the D bound steps two
+                                   symbols at a time; built from the index on the first call
+                                   that needs it).  Intervals, insertion points
                                    and results are unchanged; an inexact search's stats[0] then
                                    omits the middle node of a two-symbol step that ends the
                                    branch.  2: one symbol per step (stats exactly as described) */

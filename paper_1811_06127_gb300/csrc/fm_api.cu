@@ -126,6 +126,8 @@ void release(fm_index *h) {
     cudaFree(h->d_kbits_rev);
     cudaFree(h->d_prec);
     cudaFree(h->d_pc2);
+    cudaFree(h->d_prec_rev);
+    cudaFree(h->d_pc2_rev);
     fm::Scratch *ss[] = {&h->s_qmeta, &h->s_raw, &h->s_spill, &h->s_group, &h->s_scan, &h->s_plain,
                          &h->s_misc};
     for (auto *s : ss) cudaFree(s->ptr);
@@ -308,7 +310,8 @@ int fm_info(const fm_index *h, fm_info_t *out) {
     out->bytes_device = h->n_blocks * h->bbytes * (h->has_rev ? 2 : 1) + h->n_sa_sample * 4;
     if (h->kt_depth)   // forward tables, and the reverse index's own with it
         out->bytes_device += (h->d_kt_rev ? 2 : 1) * (2ull << (2 * h->kt_depth)) * (8 + 1.0 / 8);
-    if (h->pairs_built) out->bytes_device += ((h->n + 1) / fm::kPairRows + 1) * 16 * 8 + 64;
+    if (h->pairs_built)   // forward pair table, and the reverse index's own with it
+        out->bytes_device += (h->d_prec_rev ? 2 : 1) * (((h->n + 1) / fm::kPairRows + 1) * 16 * 8 + 64);
     out->has_reverse = h->has_rev ? 1 : 0;
     out->both_strands = h->both_strands ? 1 : 0;
     out->device = h->device;

@@ -127,6 +127,8 @@ struct fm_index {
     uint2 *d_kt_rev = nullptr;       // the same tables of the index of reverse(R) (D bound)
     uint32_t *d_kbits_rev = nullptr;
     uint2 *d_prec = nullptr;         // pair table (see IndexView)
+    uint2 *d_prec_rev = nullptr;     // the pair table of the index of reverse(R) (D pass)
+    uint32_t *d_pc2_rev = nullptr;
     uint32_t *d_pc2 = nullptr;       // its pc2[16]
     bool pairs_built = false;
     // grow-on-demand scratch of the search calls

@@ -35,9 +35,9 @@ IndexView view_rev(const fm_index *h) {
     v.kt = h->d_kt_rev;
     v.kbits = h->d_kbits_rev;
     v.kdepth = h->d_kt_rev ? h->kt_depth : 0u;
-    v.prec = nullptr;
-    v.pc2 = nullptr;
-    v.pairs = 0;
+    v.prec = h->d_prec_rev;
+    v.pc2 = h->d_pc2_rev;
+    v.pairs = h->pairs_built && h->tune.pairs && h->d_prec_rev ? 1u : 0u;
     v.dollar = (uint32_t)h->rev_dollar;
     return v;
 }
@@ -292,6 +292,24 @@ __global__ void __launch_bounds__(128) k_dcalc(IndexView rv, const uint8_t *__re
                 continue;
             }
             const uint32_t b = wsym(i);
+            if (rv.pairs && i + 1u < m) {
+                // W[i] and W[i+1] at once over the pair table of reverse(R) (prepended to the
+                // reversed window in that order: pair code 4 W[i+1] + W[i]); a pair that does
+                // not occur falls back to the single step below, which finds where the window
+                // closes
+                const uint32_t pc = 4u * wsym(i + 1u) + b, pk = k, pl = l + 1u;
+                const uint2 Rk = load_pair_rec(rv, pc, pk / kPairRows);
+                const uint2 Rl = pl / kPairRows == pk / kPairRows ? Rk : load_pair_rec(rv, pc, pl / kPairRows);
+                const uint32_t c2 = __ldg(rv.pc2 + pc);
+                const uint32_t k2 = c2 + pair_rank(Rk, pk), l2 = c2 + pair_rank(Rl, pl) - 1u;
+                if (k2 <= l2) {
+                    k = k2;
+                    l = l2;
+                    if (Dq) Dq[i] = Dq[i + 1] = (uint8_t)(z > 255 ? 255 : z);
+                    i += 2;
+                    continue;
+                }
+            }
             const uint32_t pk = k, pl = l + 1u;
             const uint32_t jk = pk / I, jl = pl / I;
             Blk<I> Bk, Bl;
@@ -615,17 +633,18 @@ int ensure_kmer(fm_index *h, cudaStream_t st) {
     return FM_OK;
 }
 
-int ensure_pairs(fm_index *h, cudaStream_t st) {
-    if (!h->tune.pairs || h->pairs_built || h->borrowed) return FM_OK;
+// The pair records and pc2 of the index ix views (blocks: its checkpoint blocks, whose first
+// holds the symbol before its $ suffix, the text's last symbol).
+static int build_pair_table(fm_index *h, const IndexView &ix, const uint8_t *blocks, uint2 **prec,
+                            uint32_t **pc2_out, cudaStream_t st) {
     const uint64_t N = h->n + 1;                    // rows
     const uint64_t nblk = N / kPairRows + 1;        // rank positions 0..N
     const uint64_t nrun = (nblk + kPairScanBlocks - 1) / kPairScanBlocks;
     const uint32_t sentinel = 0xffffffffu;
     uint32_t *d_rowb = nullptr, *d_tot = nullptr;
     int rc = FM_OK;
-    FM_CUDA_TRY(h, cudaStreamSynchronize(st));
-    if (cudaMalloc(&h->d_prec, nblk * 16 * sizeof(uint2)) != cudaSuccess ||
-        cudaMalloc(&h->d_pc2, 16 * sizeof(uint32_t)) != cudaSuccess ||
+    if (cudaMalloc(prec, nblk * 16 * sizeof(uint2)) != cudaSuccess ||
+        cudaMalloc(pc2_out, 16 * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&d_tot, nrun * 16 * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&d_rowb, sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
@@ -633,15 +652,14 @@ int ensure_pairs(fm_index *h, cudaStream_t st) {
     }
     std::vector<uint32_t> tot, base;
     if (!rc) {
-        FM_CUDA_TRY(h, cudaMemsetAsync(h->d_prec, 0, nblk * 16 * sizeof(uint2), st));
+        FM_CUDA_TRY(h, cudaMemsetAsync(*prec, 0, nblk * 16 * sizeof(uint2), st));
         FM_CUDA_TRY(h, cudaMemcpyAsync(d_rowb, &sentinel, 4, cudaMemcpyHostToDevice, st));
-        IndexView ix = view_fwd(h);
         const int grid = grid_occ(h, (N + 7) / 8, 256);
         switch (h->interval) {
-            case 32: k_pair_sym<32><<<grid, 256, 0, st>>>(ix, h->d_prec, nblk, N, d_rowb); break;
-            case 64: k_pair_sym<64><<<grid, 256, 0, st>>>(ix, h->d_prec, nblk, N, d_rowb); break;
-            case 128: k_pair_sym<128><<<grid, 256, 0, st>>>(ix, h->d_prec, nblk, N, d_rowb); break;
-            default: k_pair_sym<256><<<grid, 256, 0, st>>>(ix, h->d_prec, nblk, N, d_rowb); break;
+            case 32: k_pair_sym<32><<<grid, 256, 0, st>>>(ix, *prec, nblk, N, d_rowb); break;
+            case 64: k_pair_sym<64><<<grid, 256, 0, st>>>(ix, *prec, nblk, N, d_rowb); break;
+            case 128: k_pair_sym<128><<<grid, 256, 0, st>>>(ix, *prec, nblk, N, d_rowb); break;
+            default: k_pair_sym<256><<<grid, 256, 0, st>>>(ix, *prec, nblk, N, d_rowb); break;
         }
         FM_CUDA_TRY(h, cudaGetLastError());
         uint32_t rowb = sentinel;
@@ -650,13 +668,14 @@ int ensure_pairs(fm_index *h, cudaStream_t st) {
         if (rowb == sentinel) rc = set_error(h, FM_ECUDA, "pair table: no row precedes the $ row");
     }
     if (!rc) {
-        k_pair_counts<<<grid_occ(h, nrun * 16, 256), 256, 0, st>>>(h->d_prec, nblk, nrun, d_tot);
+        k_pair_counts<<<grid_occ(h, nrun * 16, 256), 256, 0, st>>>(*prec, nblk, nrun, d_tot);
         FM_CUDA_TRY(h, cudaGetLastError());
         tot.resize(nrun * 16);
         FM_CUDA_TRY(h, cudaMemcpyAsync(tot.data(), d_tot, nrun * 16 * 4, cudaMemcpyDeviceToHost, st));
-        // the symbol of row 0 (the $ suffix) is T[n-1]: read it from the first checkpoint block
+        // the symbol of row 0 (the $ suffix) is the text's last symbol: read it from the first
+        // checkpoint block
         uint8_t b0[32];
-        FM_CUDA_TRY(h, cudaMemcpyAsync(b0, h->d_fwd, 32, cudaMemcpyDeviceToHost, st));
+        FM_CUDA_TRY(h, cudaMemcpyAsync(b0, blocks, 32, cudaMemcpyDeviceToHost, st));
         FM_CUDA_TRY(h, cudaStreamSynchronize(st));
         const uint32_t last = b0[16] & 3u;
         // run bases (exclusive scan per pair code), then pc2
@@ -668,8 +687,8 @@ int ensure_pairs(fm_index *h, cudaStream_t st) {
                 run[c] += tot[c * nrun + r];
             }
         // rows before every string that starts with pair (b1, b2): the $ row, suffixes starting
-        // with a symbol below b1, the suffix "b1 $" when R ends with b1, and suffixes starting
-        // with b1 then a symbol below b2
+        // with a symbol below b1, the suffix "b1 $" when the text ends with b1, and suffixes
+        // starting with b1 then a symbol below b2 (C is the same for R and reverse(R))
         uint32_t pc2[16];
         for (uint32_t b1 = 0; b1 < 4; ++b1)
             for (uint32_t b2 = 0; b2 < 4; ++b2) {
@@ -678,13 +697,35 @@ int ensure_pairs(fm_index *h, cudaStream_t st) {
                 pc2[4 * b1 + b2] = (uint32_t)v;
             }
         FM_CUDA_TRY(h, cudaMemcpyAsync(d_tot, base.data(), base.size() * 4, cudaMemcpyHostToDevice, st));
-        FM_CUDA_TRY(h, cudaMemcpyAsync(h->d_pc2, pc2, sizeof(pc2), cudaMemcpyHostToDevice, st));
-        k_pair_base<<<grid_occ(h, nblk * 16, 256), 256, 0, st>>>(h->d_prec, nblk, nrun, d_tot);
+        FM_CUDA_TRY(h, cudaMemcpyAsync(*pc2_out, pc2, sizeof(pc2), cudaMemcpyHostToDevice, st));
+        k_pair_base<<<grid_occ(h, nblk * 16, 256), 256, 0, st>>>(*prec, nblk, nrun, d_tot);
         FM_CUDA_TRY(h, cudaGetLastError());
         FM_CUDA_TRY(h, cudaStreamSynchronize(st));
     }
     cudaFree(d_tot);
     cudaFree(d_rowb);
+    if (rc) {
+        cudaFree(*prec);
+        cudaFree(*pc2_out);
+        *prec = nullptr;
+        *pc2_out = nullptr;
+    }
+    return rc;
+}
+
+// The pair tables: the forward index's (search steps) and, with the index of reverse(R), that
+// index's own (two-symbol steps of the D pass).
+int ensure_pairs(fm_index *h, cudaStream_t st) {
+    if (!h->tune.pairs || h->pairs_built || h->borrowed) return FM_OK;
+    FM_CUDA_TRY(h, cudaStreamSynchronize(st));
+    int rc = build_pair_table(h, view_fwd(h), h->d_fwd, &h->d_prec, &h->d_pc2, st);
+    if (!rc && h->has_rev) {
+        IndexView rv = view_rev(h);
+        rv.kt = nullptr;   // the builder's steps read checkpoint blocks only
+        rv.kbits = nullptr;
+        rv.kdepth = 0;
+        rc = build_pair_table(h, rv, h->d_rev, &h->d_prec_rev, &h->d_pc2_rev, st);
+    }
     if (rc) {
         cudaFree(h->d_prec);
         cudaFree(h->d_pc2);

@@ -231,11 +231,16 @@ def test_dcalc_matches_oracle(fm, interval):
     codes, offs = fm.to_device_reads(reads)
     want = [(ix.dcalc(reads.read(r)), ix.dcalc(synth.revcomp(reads.read(r))))
             for r in range(len(reads))]
-    # without interval tables, then with tables of reverse(R) at several depths (a search
-    # builds them; the D bound then takes each window's first symbols from them)
+    # without interval or pair tables, then with tables of reverse(R) at several depths (a
+    # search builds them; the D bound then takes each window's first symbols from them and its
+    # further symbols two at a time from the pair table of reverse(R)), then pairs without
+    # interval tables, then interval tables without pair steps
     ek, eo = fm.to_device_reads(reads.subset(np.arange(4)))
-    for depth in (None, 1, 2, 7, fm.KMER_AUTO):
-        if depth is not None:
+    for depth in (None, 1, 2, 7, fm.KMER_AUTO, fm.KMER_OFF, "no pairs"):
+        if depth == "no pairs":
+            fm.fm_set_tuning(h, kmer_depth=fm.KMER_AUTO, pair_steps=2)
+            fm.fm_exact(h, ek, eo)
+        elif depth is not None:
             fm.fm_set_tuning(h, kmer_depth=depth)
             fm.fm_exact(h, ek, eo)
         D = fm.fm_dcalc(h, codes, offs, strands=2).cpu().numpy()
